@@ -1,0 +1,190 @@
+"""Pins of the oracle's Fox / LazyFox iteration: hand-derived runs, recount
+invariants after every queue, brute-force candidate enumeration, the
+equivalence of LazyFox and Fox when a queue's nodes cannot interact, and the
+stopping criterion.
+
+Paper passages: Node Changes (Joining / Leaving a Community, Algorithm 1),
+Parallelism on Node Change Computations (Algorithm 2), Stopping Criteria,
+Post-processing.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2210_03211_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.mark.parametrize("name", ["bowtie", "k4_pendant", "path5"])
+def test_golden_runs(oracle_lib, name):
+    fx = json.load(open(os.path.join(GOLDEN, name + ".json")))
+    el = W.from_pairs(fx["edges"])
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    r = g.run(fx["queue_size"], fx["threshold"], fx["max_iters"])
+    assert r["T0"] == pytest.approx(float(Fraction(fx["T0"])), rel=1e-14, abs=1e-300)
+    assert r["iterations"] == fx["iterations"]
+    assert r["converged"]
+    for got, want in zip(r["T"], fx["T"]):
+        assert got == pytest.approx(float(Fraction(want)), rel=1e-14, abs=1e-300)
+    assert r["joins"].tolist() == fx["joins"]
+    assert r["leaves"].tolist() == fx["leaves"]
+    comms = [c.tolist() for c in g.communities()]
+    assert comms == fx["final_communities"]
+
+
+def test_disjoint_cliques_converge_without_moves(oracle_lib):
+    """Every node of a disjoint union of cliques has CC = 1, so cc = 1 and each
+    membership scores 1: WCC-hat(P) = total size.  Leaving lowers the score and
+    no other community is adjacent, so Fox makes no move and stops after one
+    iteration."""
+    sizes = [5, 4, 7, 3]
+    pairs, off = [], 0
+    for s in sizes:
+        pairs += W.clique(s, off)
+        off += s + 2
+    el = W.from_pairs(pairs)
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    r = g.run(1, 0.01, 50)
+    assert r["T0"] == sum(sizes)
+    assert r["iterations"] == 1 and r["joins"][0] == 0 and r["leaves"][0] == 0
+    assert r["T"][0] == sum(sizes)
+
+
+def recount(g, st):
+    off, adj, _ = g.csr()
+    k = len(st["n"])
+    n = np.zeros(k, np.int64)
+    m2 = np.zeros(k, np.int64)
+    vol = np.zeros(k, np.int64)
+    mem = [set(st["mem_ids"][st["mem_off"][x]:st["mem_off"][x + 1]].tolist()) for x in range(g.n)]
+    for x in range(g.n):
+        row = st["mem_ids"][st["mem_off"][x]:st["mem_off"][x + 1]]
+        assert np.all(np.diff(row) > 0)
+        for c in mem[x]:
+            n[c] += 1
+            vol[c] += off[x + 1] - off[x]
+            m2[c] += sum(1 for y in adj[off[x]:off[x + 1]] if c in mem[y])
+    return n, m2 // 2, vol
+
+
+@pytest.mark.parametrize("q", [1, 3, 64, 1000])
+def test_aggregates_equal_recounts_after_every_queue(oracle_lib, q):
+    el = W.eu_core_like()
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    g.set_check_invariants(True)
+    g.run(q, 0.01, 2)
+    assert g.invariant_failures() == 0
+    # and the python recount of the final state agrees
+    st = g.state()
+    n, m, vol = recount(g, st)
+    live = st["n"] > 0
+    assert np.array_equal(n, st["n"]) and np.array_equal(m, st["m"]) and np.array_equal(vol, st["vol"])
+    assert np.all(st["n"][live] >= 2)
+
+
+def test_candidates_and_choice_by_brute_force(oracle_lib):
+    """For nodes of a mid-run state: the join target is a community some
+    neighbour is in and the node is not, with k = |N(x) & C| counted by brute
+    force; the leave target is one of the node's communities; no candidate has
+    a strictly larger gain (or an equal gain and a lower id)."""
+    el = W.eu_core_like()
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    g.run(16, 0.01, 1, max_batches=30)
+    st = g.state()
+    off, adj, _ = g.csr()
+    cc = g.cc
+    mem = [set(st["mem_ids"][st["mem_off"][x]:st["mem_off"][x + 1]].tolist()) for x in range(g.n)]
+    for x in range(0, g.n, 7):
+        nbrs = adj[off[x]:off[x + 1]].tolist()
+        d = len(nbrs)
+        cand = set().union(*[mem[y] for y in nbrs]) | mem[x]
+        k = {c: sum(1 for y in nbrs if c in mem[y]) for c in cand}
+        gains_join, gains_leave = {}, {}
+        for c in cand:
+            before = oracle_lib.community_score(st["n"][c], st["m"][c], st["vol"][c], cc)
+            if c in mem[x]:
+                gains_leave[c] = oracle_lib.community_score(st["n"][c] - 1, st["m"][c] - k[c], st["vol"][c] - d, cc) - before
+            else:
+                gains_join[c] = oracle_lib.community_score(st["n"][c] + 1, st["m"][c] + k[c], st["vol"][c] + d, cc) - before
+        a = g.evaluate(x)
+
+        def best(gains):
+            pos = [(gv, -c) for c, gv in gains.items() if gv > 0]
+            return -max(pos)[1] if pos else -1
+
+        assert a["join"] == best(gains_join)
+        assert a["leave"] == best(gains_leave)
+        if a["join"] >= 0:
+            assert a["kjoin"] == k[a["join"]] and a["join"] not in mem[x]
+        if a["leave"] >= 0:
+            assert a["kleave"] == k[a["leave"]] and a["leave"] in mem[x]
+
+
+def interleaved_components(copies: int, pairs):
+    """`copies` disjoint copies of a small graph with ids interleaved (copy j of
+    node i gets id i*copies + j), so nodes in the same role of different copies
+    sit next to each other in the node order."""
+    out = []
+    for j in range(copies):
+        out += [(a * copies + j, b * copies + j) for a, b in pairs]
+    return W.from_pairs(out)
+
+
+def test_lazyfox_equals_fox_when_queue_nodes_cannot_interact(oracle_lib):
+    """If no two nodes of a queue share a neighbouring or own community, the
+    bulk apply of Algorithm 2 changes nothing against Algorithm 1: with the
+    queue size equal to the number of identical, disjoint, interleaved copies,
+    each queue holds one node per copy, so LazyFox(q) must equal Fox."""
+    base = W.eu_core_like(seed=5)
+    bg = oracle_lib.OracleGraph(base.src, base.dst, prepare=False)
+    off, adj, _ = bg.csr()
+    pairs = [(x, int(y)) for x in range(bg.n) for y in adj[off[x]:off[x + 1]] if y > x]
+    copies = 4
+    el = interleaved_components(copies, pairs)
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    lazy = g.run(copies, 0.01, 6)
+    lazy_comms = [c.tolist() for c in g.communities()]
+    fox = g.run(1, 0.01, 6)
+    fox_comms = [c.tolist() for c in g.communities()]
+    assert lazy["iterations"] == fox["iterations"]
+    assert np.array_equal(lazy["T"], fox["T"])
+    assert lazy_comms == fox_comms
+    # and the copies are identical to each other: each result is the base result
+    single = oracle_lib.OracleGraph(base.src, base.dst)
+    sr = single.run(1, 0.01, 6)
+    assert np.allclose(fox["T"], copies * sr["T"], rtol=1e-12)
+
+
+def test_stopping_criterion(oracle_lib):
+    el = W.eu_core_like()
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    r = g.run(8, -math.inf, 5)
+    assert r["iterations"] == 5 and not r["converged"]
+    r = g.run(8, math.inf, 5)
+    assert r["iterations"] == 1 and r["converged"]
+    r = g.run(8, 0.01, 0)
+    assert r["iterations"] == 0
+    # the stop decision follows the relative change of the totals
+    r = g.run(8, 0.05, 50)
+    prev = r["T0"]
+    for i, T in enumerate(r["T"]):
+        rel = (T - prev) / prev
+        if i < r["iterations"] - 1:
+            assert rel >= 0.05
+        else:
+            assert rel < 0.05
+        prev = T
+
+
+def test_membership_counts_grow_at_most_one_per_iteration(oracle_lib):
+    el = W.eu_core_like()
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    for it in range(1, 6):
+        g.run(32, -math.inf, it)
+        st = g.state()
+        assert np.max(np.diff(st["mem_off"])) <= 1 + it
