@@ -1,0 +1,224 @@
+/*
+ * lazyfox.h -- C ABI of the GB300 (sm_103a) implementation of Fox / LazyFox
+ * overlapping community detection (Garrels, Khodabakhsh, Renard, Baum,
+ * "LazyFox: Fast and parallelized overlapping community detection in large
+ * graphs", arXiv 2210.03211).
+ *
+ * Every step of the method runs in this library's own CUDA kernels on one
+ * GPU; there is no CPU fallback.  Plain C types only.  No exception crosses
+ * the boundary: every call returns an lf_status and, on failure, leaves a
+ * message for lf_last_error() (thread-local).
+ *
+ * Conventions
+ *  - Pointers marked "host" are read or written by the call before it returns;
+ *    the library keeps no reference to them.  Pointers marked "device" are
+ *    CUDA device pointers, used in order on the graph's stream.
+ *  - A graph handle owns all device state of one graph.  One handle must not
+ *    be used by two threads at the same time; distinct handles are
+ *    independent.
+ *  - All work of a handle is ordered on one CUDA stream (lf_options.stream,
+ *    or a stream the library creates).  Calls that return host data
+ *    synchronise that stream.
+ *  - Node ids in the input are non-negative int32; the library relabels them
+ *    densely (0..n-1, increasing with the original id) and reports results in
+ *    original ids.
+ *  - Community ids are assigned by the initial clustering (0, 1, 2, ... in
+ *    the order the communities are opened) and never reused during a run.
+ */
+#ifndef LAZYFOX_H
+#define LAZYFOX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LF_OK = 0,
+    LF_ERR_INVALID = 1,   /* bad argument or malformed input */
+    LF_ERR_OOM = 2,       /* an allocation failed (device or callback) */
+    LF_ERR_CUDA = 3,      /* a CUDA runtime call or a kernel failed */
+    LF_ERR_CAPACITY = 4,  /* a size exceeds a documented limit, or an output buffer is too small */
+    LF_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    LF_ERR_STATE = 6      /* call out of order (e.g. results before any run) */
+} lf_status;
+
+typedef struct lf_graph lf_graph;   /* opaque; owns all device state of one graph */
+
+/* Device memory callbacks: alloc returns a device pointer (NULL on failure)
+ * usable on `stream`; free releases it.  Used instead of cudaMallocAsync when
+ * set, e.g. to route the library's memory through PyTorch's caching
+ * allocator. */
+typedef void *(*lf_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*lf_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+
+typedef struct lf_options {
+    void *stream;            /* cudaStream_t to run on; NULL: the library creates one */
+    lf_alloc_fn alloc;       /* NULL: cudaMallocAsync on the stream */
+    lf_free_fn free;
+    void *alloc_ctx;
+    int32_t edges_on_device; /* 1: src/dst of lf_graph_create are device pointers */
+    int32_t member_slots;    /* initial per-node membership capacity (0: default 4); grows as needed */
+    int32_t warp_max_degree; /* 0: default; smaller values send more nodes to the block-wide
+                                kernels (tuning and tests) */
+    int32_t use_graphs;      /* 0: default (capture each iteration in a CUDA graph);
+                                -1: launch kernels directly */
+} lf_options;
+
+/* Per-run statistics.  The history pointers are optional caller buffers with
+ * `history_cap` entries each (NULL to skip). */
+typedef struct lf_run_stats {
+    int32_t iterations;      /* iterations completed */
+    int32_t converged;       /* 1 if the relative-change test stopped the run */
+    int64_t num_batches;     /* queues processed in total */
+    double wcc_initial;      /* WCC-hat(P) of the initial clustering */
+    int64_t num_communities; /* live communities after the run */
+    int64_t num_memberships; /* (node, community) pairs after the run */
+    double ms_total;         /* wall time of the call */
+    double ms_init;          /* initial clustering and its total (device time) */
+    double ms_iterations;    /* all iterations (device time) */
+    int32_t history_cap;
+    double *wcc_history;     /* WCC-hat(P) after iterations 1..iterations */
+    int64_t *joins_history;  /* join actions applied per iteration */
+    int64_t *leaves_history; /* leave actions applied per iteration */
+} lf_run_stats;
+
+/* Device times of the phases of lf_graph_create. */
+typedef struct lf_create_stats {
+    int64_t num_nodes;
+    int64_t num_edges;       /* undirected simple edges m */
+    int64_t num_triangles;
+    double ms_csr;           /* self-loop/duplicate removal, relabel, symmetric CSR */
+    double ms_orient;        /* degree-ordered orientation */
+    double ms_triangles;     /* triangle kernels: t(x,V) and the edge marks */
+    double ms_vt;            /* vt(x,V) */
+    double ms_order;         /* local CC, node order, global cc */
+    int64_t merge_bytes;     /* sum over oriented edges u->v of 4*(d+(u) + d+(v)) */
+} lf_create_stats;
+
+/*
+ * lf_graph_create -- build a graph from an undirected, unweighted edge list
+ * (Methods, Input Data) and run the one-time preprocessing (Methods,
+ * Preprocessing; Methods, WCC; Heuristic Counting of Triangles):
+ *   - remove self-loops and repeated pairs ("Remove Multi-Edges");
+ *   - relabel endpoint ids densely in increasing order ("Dense Node Labels");
+ *     the nodes are the endpoints of the remaining edges;
+ *   - build the symmetric CSR (ascending rows) and the degree-ordered
+ *     orientation N+(u) = {v in N(u) : (deg v, v) > (deg u, u)};
+ *   - count t(x,V), the triangles containing x, and vt(x,V), the neighbours
+ *     of x that share at least one triangle with x;
+ *   - compute the local clustering coefficients CC(i) = t_i / C(d_i,2)
+ *     (0 if d_i <= 1), the node order (CC descending, compared exactly as
+ *     rationals; then degree descending; then dense id ascending) and the
+ *     global cc: the correctly rounded sum of the rounded local CCs over all
+ *     n nodes, divided by n ("Node Order"; global cc).
+ * src, dst : num_edges ids each; host memory, or device memory if
+ *            opt->edges_on_device.  Ids must be >= 0 (else LF_ERR_INVALID).
+ * num_edges: >= 0; 0 gives an empty graph (n = 0).
+ * opt      : may be NULL (defaults).  Copied; its stream and callbacks must
+ *            stay valid until lf_graph_destroy.
+ * out      : receives the new handle (NULL on failure).
+ * Limits   : fewer than 2^31 simple edges (LF_ERR_CAPACITY).
+ */
+lf_status lf_graph_create(const int32_t *src, const int32_t *dst, int64_t num_edges,
+                          const lf_options *opt, lf_graph **out);
+
+/*
+ * lf_run -- Fox / LazyFox community detection (Methods: Initial Clustering,
+ * Node Changes with Algorithm 1, Parallelism on Node Change Computations
+ * with Algorithm 2, Stopping Criteria, Post-processing).  Always restarts
+ * from the initial clustering:
+ *   - initial clustering: walk the node order; a node not yet in a community
+ *     opens a new one and its unassigned neighbours join it;
+ *   - each iteration walks the node order in queues of queue_size nodes (the
+ *     last may be shorter).  Every queued node x is evaluated against the
+ *     partition as it stood when the queue was filled: for each community C
+ *     adjacent to x (x not in C) the gain of joining, for each community of x
+ *     the gain of leaving, both as the change of the community's mean-field
+ *     WCC-hat score; the best strictly positive gain of each kind is chosen
+ *     (lowest community id on ties).  Then all chosen actions of the queue are
+ *     applied (leave before join).  queue_size 1 is Fox;
+ *   - after each iteration, communities with fewer than two members are
+ *     removed and WCC-hat(P), the sum of WCC-hat(x,C) over all memberships, is
+ *     taken; the run stops when (T_it - T_prev) / T_prev < wcc_threshold (if
+ *     T_prev == 0: when T_it == 0) or after max_iters iterations.
+ * queue_size   : >= 1 (else LF_ERR_INVALID).
+ * wcc_threshold: relative-change threshold; -INFINITY never stops early.
+ * max_iters    : >= 0 (0 runs only the initial clustering).
+ * stats        : optional (NULL); filled on return.
+ * Errors       : LF_ERR_CAPACITY if a queue of queue_size nodes cannot be
+ *                held (queue_size is clamped to n internally, so this only
+ *                happens when device memory runs out), LF_ERR_CUDA, LF_ERR_OOM.
+ */
+lf_status lf_run(lf_graph *g, int32_t queue_size, double wcc_threshold, int32_t max_iters,
+                 lf_run_stats *stats);
+
+/*
+ * lf_get_communities -- the communities of the last run: live communities in
+ * ascending id, members ascending, as original node ids (Post-processing: no
+ * post-processing beyond removing degenerate communities).  After a run with
+ * max_iters = 0 the initial clustering is returned (singletons included).
+ * offsets: host, num_communities + 1 entries (member ranges).
+ * members: host, num_members entries.
+ * Passing NULL buffers (or caps that are too small) only reports the sizes in
+ * *num_communities and *num_members; too-small non-NULL buffers also return
+ * LF_ERR_CAPACITY.  LF_ERR_STATE before the first lf_run.
+ */
+lf_status lf_get_communities(lf_graph *g, int64_t *offsets, int64_t offsets_cap,
+                             int32_t *members, int64_t members_cap,
+                             int64_t *num_communities, int64_t *num_members);
+
+/*
+ * lf_get_node_stats -- per-node triangle counts t(x,V) (int64, n entries),
+ * vt(x,V) (int32, n entries) and the global cc (Methods, WCC; Heuristic
+ * Counting of Triangles), indexed by dense id.  Any pointer may be NULL.
+ * Host buffers.
+ */
+lf_status lf_get_node_stats(lf_graph *g, int64_t *t, int32_t *vt, double *cc_global);
+
+/* Sizes of the graph: nodes n, undirected simple edges m. */
+lf_status lf_get_sizes(lf_graph *g, int64_t *num_nodes, int64_t *num_edges);
+
+/* Device times of lf_graph_create's phases (see lf_create_stats). */
+lf_status lf_get_create_stats(lf_graph *g, lf_create_stats *stats);
+
+/*
+ * Inspection hooks (host buffers, dense ids).  They expose intermediate
+ * results of the preprocessing and of a run for parity tests and tooling.
+ *  lf_get_csr      : offsets (n+1), neighbours (2m), labels (n: dense -> original id).
+ *  lf_get_oriented : offsets (n+1) and out-neighbours (m) of the orientation.
+ *  lf_get_order    : the node order (n dense ids).
+ *  lf_get_state    : memberships as CSR over dense ids (mem_offsets n+1,
+ *                    mem_ids as counted by *num_memberships, each row
+ *                    ascending) and, for every community id ever used
+ *                    (*num_comm_ids of them), members n_C, internal edges m_C
+ *                    and the sum of member degrees vol_C.  NULL buffers: sizes
+ *                    only.  LF_ERR_STATE before the first run.
+ */
+lf_status lf_get_csr(lf_graph *g, int64_t *offsets, int32_t *neighbours, int32_t *labels);
+lf_status lf_get_oriented(lf_graph *g, int64_t *offsets, int32_t *out_neighbours);
+lf_status lf_get_order(lf_graph *g, int32_t *order);
+lf_status lf_get_state(lf_graph *g, int64_t *mem_offsets, int32_t *mem_ids,
+                       int64_t *comm_n, int64_t *comm_m, int64_t *comm_vol,
+                       int64_t *num_memberships, int64_t *num_comm_ids);
+
+/*
+ * lf_run_partial -- lf_run that stops after max_batches queues in total
+ * (iteration ends run only for completed iterations), for per-queue parity
+ * checks.  max_batches < 0 behaves like lf_run.
+ */
+lf_status lf_run_partial(lf_graph *g, int32_t queue_size, double wcc_threshold, int32_t max_iters,
+                         int64_t max_batches, lf_run_stats *stats);
+
+/* Release every device buffer and the handle (NULL is a no-op). */
+void lf_graph_destroy(lf_graph *g);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *lf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

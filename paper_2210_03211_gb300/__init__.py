@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) implementation of Fox / LazyFox overlapping community
+detection (Garrels et al., arXiv 2210.03211): hand-written CUDA kernels behind
+the C ABI of ``include/lazyfox.h``, with a thin Python binding.
+
+The CUDA library is loaded on first use (``lazyfox.load_library``); without it
+every call raises -- there is no CPU fallback.
+"""
+from .lazyfox import (ABI_FUNCTIONS, Graph, LazyFoxError, RunStats, load_library,  # noqa: F401
+                      run_lazyfox)
+
+__all__ = ["Graph", "LazyFoxError", "RunStats", "load_library", "run_lazyfox", "ABI_FUNCTIONS"]

@@ -1,0 +1,398 @@
+// C ABI entry points, error plumbing, device memory, and result extraction.
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "lf_internal.cuh"
+
+namespace lf {
+
+void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E, bool on_device);
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(lf_status st, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    (void)st;
+    g_last_error = buf;
+}
+
+[[noreturn]] void fail(lf_status st, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    throw Error{st};
+}
+
+void *dalloc(lf_graph *g, size_t bytes) {
+    void *p = nullptr;
+    if (g->alloc_cb) {
+        p = g->alloc_cb(bytes, (void *)g->stream, g->alloc_ctx);
+        if (!p) fail(LF_ERR_OOM, "device allocation of %zu bytes failed (callback)", bytes);
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, g->stream);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            fail(LF_ERR_OOM, "cudaMallocAsync of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    g->live.emplace_back(p, bytes);
+    return p;
+}
+
+void dfree(lf_graph *g, void *p) {
+    if (!p) return;
+    size_t bytes = 0;
+    for (size_t i = 0; i < g->live.size(); ++i)
+        if (g->live[i].first == p) {
+            bytes = g->live[i].second;
+            g->live[i] = g->live.back();
+            g->live.pop_back();
+            break;
+        }
+    if (g->free_cb) g->free_cb(p, bytes, (void *)g->stream, g->alloc_ctx);
+    else cudaFreeAsync(p, g->stream);
+}
+
+namespace {
+
+struct CommKeyArgs {
+    const int32_t *mem;
+    const int32_t *nmem;
+    int32_t K;
+};
+
+__global__ void k_member_counts(const int32_t *nmem, int64_t n, int64_t *cnt) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        cnt[x] = nmem[x];
+}
+
+__global__ void k_member_keys(CommKeyArgs a, int64_t n, const int64_t *moff, unsigned long long *keys) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = a.nmem[x];
+        for (int32_t s = 0; s < c; ++s)
+            keys[moff[x] + s] = ((unsigned long long)(uint32_t)a.mem[x * a.K + s] << 32) | (uint32_t)x;
+    }
+}
+
+__global__ void k_live_flags(const CommRec *comm, int64_t ncomm, uint32_t *flag) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncomm; c += (int64_t)gridDim.x * blockDim.x)
+        flag[c] = comm[c].n >= 1 ? 1u : 0u;
+}
+
+__global__ void k_comm_output(const unsigned long long *keys, int64_t M, const uint32_t *rank, const int32_t *labels,
+                              int64_t *offsets, int32_t *members, int64_t L) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        const uint32_t C = (uint32_t)(k >> 32);
+        members[i] = labels[(uint32_t)(k & 0xffffffffull)];
+        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != C) offsets[rank[C]] = i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) offsets[L] = M;
+}
+
+template <typename T>
+void d2h(lf_graph *g, T *host, const T *dev, int64_t count) {
+    if (count <= 0 || !host) return;
+    LF_CUDA(cudaMemcpyAsync(host, dev, (size_t)count * sizeof(T), cudaMemcpyDeviceToHost, g->stream));
+}
+
+}  // namespace
+}  // namespace lf
+
+using namespace lf;
+
+namespace {
+
+template <typename F>
+lf_status call_guarded(F &&fn) {
+    try {
+        fn();
+        return LF_OK;
+    } catch (const lf::Error &e) {
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        lf::set_error(LF_ERR_OOM, "host allocation failed");
+        return LF_ERR_OOM;
+    } catch (...) {
+        lf::set_error(LF_ERR_CUDA, "unexpected internal error");
+        return LF_ERR_CUDA;
+    }
+}
+
+void release_all(lf_graph *g) {
+    if (!g) return;
+    free_run_state(g);
+    while (!g->live.empty()) dfree(g, g->live.back().first);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->rb) cudaFreeHost(g->rb);
+    g->rb = nullptr;
+    if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+    g->stream = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lf_last_error(void) {
+    static thread_local std::string copy;
+    copy = lf::g_last_error;
+    return copy.c_str();
+}
+
+lf_status lf_graph_create(const int32_t *src, const int32_t *dst, int64_t num_edges, const lf_options *opt,
+                          lf_graph **out) {
+    if (!out) {
+        set_error(LF_ERR_INVALID, "out is NULL");
+        return LF_ERR_INVALID;
+    }
+    *out = nullptr;
+    lf_graph *g = nullptr;
+    lf_status st = call_guarded([&] {
+        if (num_edges < 0) fail(LF_ERR_INVALID, "num_edges < 0");
+        if (num_edges > 0 && (!src || !dst)) fail(LF_ERR_INVALID, "src/dst is NULL");
+        if (num_edges >= (1ll << 31)) fail(LF_ERR_CAPACITY, "more than 2^31-1 input edges");
+        g = new lf_graph();
+        if (opt) {
+            g->stream = static_cast<cudaStream_t>(opt->stream);
+            g->alloc_cb = opt->alloc;
+            g->free_cb = opt->free;
+            g->alloc_ctx = opt->alloc_ctx;
+            if (opt->member_slots > 0) g->member_slots = opt->member_slots;
+            g->warp_max_degree = opt->warp_max_degree;
+            g->use_graphs = opt->use_graphs < 0 ? 0 : 1;
+            if ((g->alloc_cb == nullptr) != (g->free_cb == nullptr))
+                fail(LF_ERR_INVALID, "alloc and free callbacks must be set together");
+        }
+        int dev_count = 0;
+        if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+            cudaGetLastError();
+            fail(LF_ERR_CUDA, "no CUDA device available");
+        }
+        if (!g->stream) {
+            LF_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+            g->own_stream = true;
+        }
+        LF_CUDA(cudaMallocHost(&g->rb, sizeof(lf::Readback)));
+        std::memset(g->rb, 0, sizeof(lf::Readback));
+        g->ds = static_cast<lf::DevScalars *>(dalloc(g, sizeof(lf::DevScalars) + sizeof(lf::Readback)));
+        LF_CUDA(cudaMemsetAsync(g->ds, 0, sizeof(lf::DevScalars) + sizeof(lf::Readback), g->stream));
+        build_graph(g, src, dst, num_edges, opt && opt->edges_on_device);
+    });
+    if (st != LF_OK) {
+        if (g) {
+            try { release_all(g); } catch (...) {}
+            delete g;
+        }
+        return st;
+    }
+    *out = g;
+    return LF_OK;
+}
+
+void lf_graph_destroy(lf_graph *g) {
+    if (!g) return;
+    try {
+        release_all(g);
+    } catch (...) {
+    }
+    delete g;
+}
+
+lf_status lf_run(lf_graph *g, int32_t queue_size, double wcc_threshold, int32_t max_iters, lf_run_stats *stats) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    return call_guarded([&] { run_impl(g, queue_size, wcc_threshold, max_iters, -1, stats); });
+}
+
+lf_status lf_run_partial(lf_graph *g, int32_t queue_size, double wcc_threshold, int32_t max_iters,
+                         int64_t max_batches, lf_run_stats *stats) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    return call_guarded([&] { run_impl(g, queue_size, wcc_threshold, max_iters, max_batches, stats); });
+}
+
+lf_status lf_get_sizes(lf_graph *g, int64_t *num_nodes, int64_t *num_edges) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    if (num_nodes) *num_nodes = g->n;
+    if (num_edges) *num_edges = g->m;
+    return LF_OK;
+}
+
+lf_status lf_get_create_stats(lf_graph *g, lf_create_stats *stats) {
+    if (!g || !stats) {
+        set_error(LF_ERR_INVALID, "NULL argument");
+        return LF_ERR_INVALID;
+    }
+    *stats = g->cstats;
+    return LF_OK;
+}
+
+lf_status lf_get_node_stats(lf_graph *g, int64_t *t, int32_t *vt, double *cc_global) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    return call_guarded([&] {
+        d2h(g, reinterpret_cast<long long *>(t), g->tri, g->n);
+        d2h(g, vt, g->vt, g->n);
+        LF_CUDA(cudaStreamSynchronize(g->stream));
+        if (cc_global) *cc_global = g->cc;
+    });
+}
+
+lf_status lf_get_csr(lf_graph *g, int64_t *offsets, int32_t *neighbours, int32_t *labels) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    return call_guarded([&] {
+        d2h(g, offsets, g->off, g->n + 1);
+        d2h(g, neighbours, g->adj, 2 * g->m);
+        d2h(g, labels, g->labels, g->n);
+        LF_CUDA(cudaStreamSynchronize(g->stream));
+    });
+}
+
+lf_status lf_get_oriented(lf_graph *g, int64_t *offsets, int32_t *out_neighbours) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    return call_guarded([&] {
+        d2h(g, offsets, g->ooff, g->n + 1);
+        d2h(g, out_neighbours, g->oadj, g->m);
+        LF_CUDA(cudaStreamSynchronize(g->stream));
+    });
+}
+
+lf_status lf_get_order(lf_graph *g, int32_t *order) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    return call_guarded([&] {
+        d2h(g, order, g->order, g->n);
+        LF_CUDA(cudaStreamSynchronize(g->stream));
+    });
+}
+
+lf_status lf_get_state(lf_graph *g, int64_t *mem_offsets, int32_t *mem_ids, int64_t *comm_n, int64_t *comm_m,
+                       int64_t *comm_vol, int64_t *num_memberships, int64_t *num_comm_ids) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    if (!g->ran) {
+        set_error(LF_ERR_STATE, "no run yet");
+        return LF_ERR_STATE;
+    }
+    return call_guarded([&] {
+        const int64_t n = g->n;
+        std::vector<int32_t> cnt((size_t)n);
+        std::vector<int32_t> rows((size_t)(n * g->K));
+        std::vector<lf::CommRec> rec((size_t)g->ncomm);
+        d2h(g, cnt.data(), g->nmem, n);
+        d2h(g, rows.data(), g->mem, n * g->K);
+        d2h(g, rec.data(), g->comm, g->ncomm);
+        LF_CUDA(cudaStreamSynchronize(g->stream));
+        int64_t total = 0;
+        for (int64_t x = 0; x < n; ++x) {
+            if (mem_offsets) mem_offsets[x] = total;
+            for (int32_t s = 0; s < cnt[x]; ++s) {
+                if (mem_ids) mem_ids[total] = rows[(size_t)(x * g->K + s)];
+                ++total;
+            }
+        }
+        if (mem_offsets) mem_offsets[n] = total;
+        for (int64_t c = 0; c < g->ncomm; ++c) {
+            if (comm_n) comm_n[c] = rec[c].n;
+            if (comm_m) comm_m[c] = rec[c].m2 / 2;
+            if (comm_vol) comm_vol[c] = rec[c].vol;
+        }
+        if (num_memberships) *num_memberships = total;
+        if (num_comm_ids) *num_comm_ids = g->ncomm;
+    });
+}
+
+lf_status lf_get_communities(lf_graph *g, int64_t *offsets, int64_t offsets_cap, int32_t *members,
+                             int64_t members_cap, int64_t *num_communities, int64_t *num_members) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    if (!g->ran) {
+        set_error(LF_ERR_STATE, "no run yet");
+        return LF_ERR_STATE;
+    }
+    return call_guarded([&] {
+        cudaStream_t st = g->stream;
+        const int64_t n = g->n, nc = g->ncomm;
+        // memberships as (community << 32 | node), sorted: communities ascending, members ascending
+        int64_t *moff = dalloc_n<int64_t>(g, n + 1);
+        k_member_counts<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(g->nmem, n, moff);
+        LF_LAUNCHED();
+        scan_exclusive<int64_t>(g, moff, moff, n, moff + n);
+        uint32_t *rank = dalloc_n<uint32_t>(g, nc + 1);
+        k_live_flags<<<grid_for(nc, 256, 1 << 16), 256, 0, st>>>(g->comm, nc, rank);
+        LF_LAUNCHED();
+        scan_exclusive<uint32_t>(g, rank, rank, nc, rank + nc);
+        int64_t M = 0;
+        uint32_t L = 0;
+        LF_CUDA(cudaMemcpyAsync(&M, moff + n, 8, cudaMemcpyDeviceToHost, st));
+        LF_CUDA(cudaMemcpyAsync(&L, rank + nc, 4, cudaMemcpyDeviceToHost, st));
+        LF_CUDA(cudaStreamSynchronize(st));
+        if (num_communities) *num_communities = (int64_t)L;
+        if (num_members) *num_members = M;
+        const bool want = offsets && members;
+        if (want && (offsets_cap < (int64_t)L + 1 || members_cap < M)) {
+            dfree(g, rank);
+            dfree(g, moff);
+            fail(LF_ERR_CAPACITY, "output buffers too small: need %lld offsets and %lld members",
+                 (long long)L + 1, (long long)M);
+        }
+        if (want) {
+            unsigned long long *keys = dalloc_n<unsigned long long>(g, M);
+            CommKeyArgs ka{g->mem, g->nmem, g->K};
+            k_member_keys<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(ka, n, moff, keys);
+            LF_LAUNCHED();
+            std::vector<int> sh;
+            const int bx = bits_for((unsigned long long)(n > 0 ? n - 1 : 0));
+            const int bc = bits_for((unsigned long long)(nc > 0 ? nc - 1 : 0));
+            for (int s = 0; s < bx; s += 8) sh.push_back(s);
+            for (int s = 0; s < bc; s += 8) sh.push_back(32 + s);
+            radix_sort(g, keys, nullptr, M, sh);
+            int64_t *d_off = dalloc_n<int64_t>(g, (int64_t)L + 1);
+            int32_t *d_mem = dalloc_n<int32_t>(g, M);
+            k_comm_output<<<grid_for(M, 256, 1 << 16), 256, 0, st>>>(keys, M, rank, g->labels, d_off, d_mem, L);
+            LF_LAUNCHED();
+            d2h(g, offsets, d_off, (int64_t)L + 1);
+            d2h(g, members, d_mem, M);
+            LF_CUDA(cudaStreamSynchronize(st));
+            dfree(g, d_mem);
+            dfree(g, d_off);
+            dfree(g, keys);
+        }
+        dfree(g, rank);
+        dfree(g, moff);
+    });
+}
+
+}  // extern "C"

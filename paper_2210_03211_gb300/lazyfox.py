@@ -1,0 +1,316 @@
+"""Python binding of the LazyFox C ABI (``include/lazyfox.h``).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``lib/liblazyfox.so``.  PyTorch supplies the device memory (its caching
+allocator, through the ABI's allocation callbacks) and the CUDA stream.  There
+is no fallback: if the library or a GPU is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "liblazyfox.so")
+
+LF_OK, LF_ERR_INVALID, LF_ERR_OOM, LF_ERR_CUDA, LF_ERR_CAPACITY, LF_ERR_TIMEOUT, LF_ERR_STATE = range(7)
+_STATUS = {1: "LF_ERR_INVALID", 2: "LF_ERR_OOM", 3: "LF_ERR_CUDA", 4: "LF_ERR_CAPACITY",
+           5: "LF_ERR_TIMEOUT", 6: "LF_ERR_STATE"}
+
+ABI_FUNCTIONS = ("lf_graph_create", "lf_run", "lf_run_partial", "lf_get_communities",
+                 "lf_get_node_stats", "lf_get_sizes", "lf_get_create_stats", "lf_get_csr",
+                 "lf_get_oriented", "lf_get_order", "lf_get_state", "lf_graph_destroy",
+                 "lf_last_error")
+
+
+class LazyFoxError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Options(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN),
+                ("alloc_ctx", C.c_void_p), ("edges_on_device", C.c_int32),
+                ("member_slots", C.c_int32), ("warp_max_degree", C.c_int32),
+                ("use_graphs", C.c_int32)]
+
+
+class RunStatsC(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("num_batches", C.c_int64),
+                ("wcc_initial", C.c_double), ("num_communities", C.c_int64),
+                ("num_memberships", C.c_int64), ("ms_total", C.c_double), ("ms_init", C.c_double),
+                ("ms_iterations", C.c_double), ("history_cap", C.c_int32),
+                ("wcc_history", C.POINTER(C.c_double)), ("joins_history", C.POINTER(C.c_int64)),
+                ("leaves_history", C.POINTER(C.c_int64))]
+
+
+class CreateStatsC(C.Structure):
+    _fields_ = [("num_nodes", C.c_int64), ("num_edges", C.c_int64), ("num_triangles", C.c_int64),
+                ("ms_csr", C.c_double), ("ms_orient", C.c_double), ("ms_triangles", C.c_double),
+                ("ms_vt", C.c_double), ("ms_order", C.c_double), ("merge_bytes", C.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> C.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise LazyFoxError(LF_ERR_STATE, f"CUDA library not built: {p} (run paper_2210_03211_gb300.build)")
+    L = C.CDLL(p)
+    P = C.c_void_p
+    i64p, i32p, f64p = C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_double)
+    sig = {
+        "lf_graph_create": (C.c_int, [P, P, C.c_int64, C.POINTER(Options), C.POINTER(P)]),
+        "lf_run": (C.c_int, [P, C.c_int32, C.c_double, C.c_int32, C.POINTER(RunStatsC)]),
+        "lf_run_partial": (C.c_int, [P, C.c_int32, C.c_double, C.c_int32, C.c_int64, C.POINTER(RunStatsC)]),
+        "lf_get_communities": (C.c_int, [P, i64p, C.c_int64, i32p, C.c_int64, i64p, i64p]),
+        "lf_get_node_stats": (C.c_int, [P, i64p, i32p, f64p]),
+        "lf_get_sizes": (C.c_int, [P, i64p, i64p]),
+        "lf_get_create_stats": (C.c_int, [P, C.POINTER(CreateStatsC)]),
+        "lf_get_csr": (C.c_int, [P, i64p, i32p, i32p]),
+        "lf_get_oriented": (C.c_int, [P, i64p, i32p]),
+        "lf_get_order": (C.c_int, [P, i32p]),
+        "lf_get_state": (C.c_int, [P, i64p, i32p, i64p, i64p, i64p, i64p, i64p]),
+        "lf_graph_destroy": (None, [P]),
+        "lf_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(L, status: int):
+    if status != LF_OK:
+        raise LazyFoxError(status, L.lf_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through torch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self._torch = torch
+        self._device = device
+        self.alloc = _ALLOC_FN(self._alloc)
+        self.free = _FREE_FN(self._free)
+
+    def _alloc(self, nbytes, stream, ctx):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes), self._device, stream)
+        except Exception:  # noqa: BLE001 - an allocation failure is reported to the library as NULL
+            return None
+
+    def _free(self, ptr, nbytes, stream, ctx):
+        if ptr:
+            self._torch.cuda.caching_allocator_delete(ptr)
+
+
+@dataclasses.dataclass
+class RunStats:
+    iterations: int
+    converged: bool
+    num_batches: int
+    wcc_initial: float
+    wcc_history: np.ndarray
+    joins: np.ndarray
+    leaves: np.ndarray
+    num_communities: int
+    num_memberships: int
+    ms_total: float
+    ms_init: float
+    ms_iterations: float
+
+
+class Graph:
+    """One graph on the GPU: ``lf_graph_create`` plus the run and result calls.
+
+    ``src``/``dst``: numpy int32 arrays (host) or int32 CUDA tensors (device).
+    ``stream``: a ``torch.cuda.Stream`` (default: torch's current stream).
+    ``allocator``: "torch" (caching allocator) or "cuda" (cudaMallocAsync).
+    """
+
+    def __init__(self, src, dst, *, stream=None, allocator: str = "torch", member_slots: int = 0,
+                 warp_max_degree: int = 0, use_graphs: bool = True, device=None):
+        import torch
+        self._L = load_library()
+        self._h = C.c_void_p()
+        if not torch.cuda.is_available():
+            raise LazyFoxError(LF_ERR_CUDA, "no CUDA device available")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        if stream is None:
+            # a stream of our own, ordered after the caller's current stream (which
+            # produced any device-resident edge list)
+            stream = torch.cuda.Stream(self.device)
+            stream.wait_stream(torch.cuda.current_stream(self.device))
+        self.stream = stream
+        opt = Options()
+        opt.stream = C.c_void_p(self.stream.cuda_stream)
+        self._allocator = None
+        if allocator == "torch":
+            self._allocator = _TorchAllocator(self.device)
+            opt.alloc = self._allocator.alloc
+            opt.free = self._allocator.free
+        elif allocator != "cuda":
+            raise ValueError(allocator)
+        opt.member_slots = int(member_slots)
+        opt.warp_max_degree = int(warp_max_degree)
+        opt.use_graphs = 0 if use_graphs else -1
+        if isinstance(src, torch.Tensor):
+            if src.dtype != torch.int32 or dst.dtype != torch.int32 or not src.is_cuda:
+                raise TypeError("device edge lists must be int32 CUDA tensors")
+            src = src.contiguous()
+            dst = dst.contiguous()
+            opt.edges_on_device = 1
+            E = src.numel()
+            ps, pd = C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr())
+            keep = (src, dst)
+        else:
+            src = np.ascontiguousarray(src, dtype=np.int32)
+            dst = np.ascontiguousarray(dst, dtype=np.int32)
+            if src.shape != dst.shape:
+                raise ValueError("src and dst differ in length")
+            opt.edges_on_device = 0
+            E = src.shape[0]
+            ps, pd = C.c_void_p(src.ctypes.data), C.c_void_p(dst.ctypes.data)
+            keep = (src, dst)
+        self._opt = opt
+        _check(self._L, self._L.lf_graph_create(ps, pd, E, C.byref(opt), C.byref(self._h)))
+        del keep
+        n, m = C.c_int64(), C.c_int64()
+        _check(self._L, self._L.lf_get_sizes(self._h, C.byref(n), C.byref(m)))
+        self.n, self.m = n.value, m.value
+
+    # -- lifetime -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.lf_graph_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the method -----------------------------------------------------------
+    def run(self, queue_size: int, wcc_threshold: float = 0.01, max_iters: int = 50,
+            max_batches: int | None = None) -> RunStats:
+        cap = max(1, max_iters)
+        T = np.zeros(cap, np.float64)
+        J = np.zeros(cap, np.int64)
+        Lv = np.zeros(cap, np.int64)
+        st = RunStatsC()
+        st.history_cap = cap
+        st.wcc_history = _ptr(T, C.c_double)
+        st.joins_history = _ptr(J, C.c_int64)
+        st.leaves_history = _ptr(Lv, C.c_int64)
+        if max_batches is None:
+            s = self._L.lf_run(self._h, int(queue_size), float(wcc_threshold), int(max_iters), C.byref(st))
+        else:
+            s = self._L.lf_run_partial(self._h, int(queue_size), float(wcc_threshold), int(max_iters),
+                                       int(max_batches), C.byref(st))
+        _check(self._L, s)
+        k = st.iterations
+        return RunStats(k, bool(st.converged), st.num_batches, st.wcc_initial, T[:k].copy(), J[:k].copy(),
+                        Lv[:k].copy(), st.num_communities, st.num_memberships, st.ms_total, st.ms_init,
+                        st.ms_iterations)
+
+    def communities(self):
+        """(offsets int64[k+1], members int32[...]) in original node ids."""
+        nc, nm = C.c_int64(), C.c_int64()
+        _check(self._L, self._L.lf_get_communities(self._h, None, 0, None, 0, C.byref(nc), C.byref(nm)))
+        off = np.zeros(nc.value + 1, np.int64)
+        mem = np.zeros(max(1, nm.value), np.int32)
+        _check(self._L, self._L.lf_get_communities(self._h, _ptr(off, C.c_int64), off.shape[0],
+                                                   _ptr(mem, C.c_int32), mem.shape[0],
+                                                   C.byref(nc), C.byref(nm)))
+        return off, mem[:nm.value]
+
+    def community_list(self):
+        off, mem = self.communities()
+        return [mem[off[i]:off[i + 1]] for i in range(off.shape[0] - 1)]
+
+    # -- inspection -------------------------------------------------------------
+    def node_stats(self):
+        t = np.zeros(max(1, self.n), np.int64)
+        vt = np.zeros(max(1, self.n), np.int32)
+        cc = C.c_double()
+        _check(self._L, self._L.lf_get_node_stats(self._h, _ptr(t, C.c_int64), _ptr(vt, C.c_int32), C.byref(cc)))
+        return t[:self.n], vt[:self.n], cc.value
+
+    def csr(self):
+        off = np.zeros(self.n + 1, np.int64)
+        adj = np.zeros(max(1, 2 * self.m), np.int32)
+        labels = np.zeros(max(1, self.n), np.int32)
+        _check(self._L, self._L.lf_get_csr(self._h, _ptr(off, C.c_int64), _ptr(adj, C.c_int32),
+                                           _ptr(labels, C.c_int32)))
+        return off, adj[:2 * self.m], labels[:self.n]
+
+    def oriented(self):
+        off = np.zeros(self.n + 1, np.int64)
+        adj = np.zeros(max(1, self.m), np.int32)
+        _check(self._L, self._L.lf_get_oriented(self._h, _ptr(off, C.c_int64), _ptr(adj, C.c_int32)))
+        return off, adj[:self.m]
+
+    def order(self):
+        o = np.zeros(max(1, self.n), np.int32)
+        _check(self._L, self._L.lf_get_order(self._h, _ptr(o, C.c_int32)))
+        return o[:self.n]
+
+    def state(self):
+        nm, nc = C.c_int64(), C.c_int64()
+        _check(self._L, self._L.lf_get_state(self._h, None, None, None, None, None, C.byref(nm), C.byref(nc)))
+        mem_off = np.zeros(self.n + 1, np.int64)
+        mem_ids = np.zeros(max(1, nm.value), np.int32)
+        cn = np.zeros(max(1, nc.value), np.int64)
+        cm = np.zeros(max(1, nc.value), np.int64)
+        cv = np.zeros(max(1, nc.value), np.int64)
+        _check(self._L, self._L.lf_get_state(self._h, _ptr(mem_off, C.c_int64), _ptr(mem_ids, C.c_int32),
+                                             _ptr(cn, C.c_int64), _ptr(cm, C.c_int64), _ptr(cv, C.c_int64),
+                                             C.byref(nm), C.byref(nc)))
+        k = nc.value
+        return dict(mem_off=mem_off, mem_ids=mem_ids[:nm.value], n=cn[:k], m=cm[:k], vol=cv[:k])
+
+    def create_stats(self) -> dict:
+        s = CreateStatsC()
+        _check(self._L, self._L.lf_get_create_stats(self._h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in CreateStatsC._fields_}
+
+
+def run_lazyfox(src, dst, queue_size: int, wcc_threshold: float = 0.01, max_iters: int = 50, **kw):
+    """One call end to end: build, run, return (communities, stats)."""
+    with Graph(src, dst, **kw) as g:
+        st = g.run(queue_size, wcc_threshold, max_iters)
+        return g.community_list(), st
+
+
+def infinity_threshold() -> float:
+    return -math.inf

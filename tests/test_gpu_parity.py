@@ -1,0 +1,225 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer and index results must be bit-exact: CSR, labels, orientation,
+t(x,V), vt(x,V), node order, initial clustering, per-queue and per-iteration
+memberships and community aggregates, community output.  Floating point:
+the global cc and every WCC-hat(P) total are compared bit for bit (both sides
+round the same expressions operation by operation and use correctly rounded
+sums); the stated contract is 1e-9 relative, asserted as well.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2210_03211_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+T_REL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def lf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2210_03211_gb300 import build
+    build.build()
+    from paper_2210_03211_gb300 import lazyfox
+    lazyfox.load_library()
+    return lazyfox
+
+
+def small_cases():
+    cases = [W.from_pairs(W.clique(5) + W.clique(4, 10) + [(3, 10)], "two_cliques"),
+             W.from_pairs([(0, 1), (0, 2), (1, 2), (2, 3), (2, 4), (3, 4)], "bowtie"),
+             W.from_pairs(W.clique(4) + [(0, 4)], "k4_pendant"),
+             W.from_pairs(W.path(5), "path5"),
+             W.from_pairs(W.star(40), "star40"),
+             W.from_pairs(W.cycle(3) + W.cycle(7, 10), "cycles")]
+    for seed in range(4):
+        cases.append(W.random_graph(n=60 + 20 * seed, m=400 + 100 * seed, seed=seed, self_loops=5, duplicates=20))
+    cases.append(W.random_graph(n=300, m=1500, seed=11, hubs=3, hub_degree=250))
+    cases.append(W.random_graph(n=3000, m=9000, seed=12, hubs=2, hub_degree=2600))
+    cases.append(W.eu_core_like())
+    cases.append(W.dblp_like(seed=3, scale=0.03))
+    return cases
+
+
+CASES = small_cases()
+IDS = [c.name for c in CASES]
+
+
+def compare_preprocessing(g, og):
+    off, adj, labels = g.csr()
+    ooff, oadj, olabels = og.csr()
+    assert np.array_equal(labels, olabels)
+    assert np.array_equal(off, ooff)
+    assert np.array_equal(adj, oadj)
+    # orientation: N+(u) = neighbours with higher (degree, id), ascending ids
+    deg = np.diff(off)
+    uoff, uadj = g.oriented()
+    assert uoff[-1] == og.m
+    for u in range(0, g.n, max(1, g.n // 500)):
+        row = adj[off[u]:off[u + 1]]
+        keep = row[(deg[row] > deg[u]) | ((deg[row] == deg[u]) & (row > u))]
+        assert np.array_equal(uadj[uoff[u]:uoff[u + 1]], keep)
+    t, vt, cc = g.node_stats()
+    ot, ovt, occ = og.node_stats()
+    assert np.array_equal(t, ot)
+    assert np.array_equal(vt, ovt)
+    assert cc == occ
+    assert np.array_equal(g.order(), og.order())
+
+
+def compare_state(g, og):
+    s, o = g.state(), og.state()
+    assert np.array_equal(s["mem_off"], o["mem_off"])
+    assert np.array_equal(s["mem_ids"], o["mem_ids"])
+    assert np.array_equal(s["n"], o["n"])
+    assert np.array_equal(s["m"], o["m"])
+    assert np.array_equal(s["vol"], o["vol"])
+
+
+def compare_run(st, ref):
+    assert st.iterations == ref["iterations"]
+    assert st.converged == ref["converged"]
+    assert st.wcc_initial == ref["T0"]
+    assert np.array_equal(st.joins, ref["joins"])
+    assert np.array_equal(st.leaves, ref["leaves"])
+    for a, b in zip(st.wcc_history, ref["T"]):
+        assert a == pytest.approx(b, rel=T_REL, abs=0)
+        assert a == b
+
+
+@pytest.mark.parametrize("el", CASES, ids=IDS)
+def test_preprocessing_parity(lf, oracle_lib, el):
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    with lf.Graph(el.src, el.dst) as g:
+        assert (g.n, g.m) == (og.n, og.m)
+        compare_preprocessing(g, og)
+
+
+@pytest.mark.parametrize("el", CASES, ids=IDS)
+@pytest.mark.parametrize("q", [1, 2, 64, 1024, 1 << 30])
+def test_run_parity(lf, oracle_lib, el, q):
+    if q == 1 and el.num_edges > 20000:
+        pytest.skip("queue size 1 is exercised on the smaller graphs")
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(q, 0.01, 50)
+    with lf.Graph(el.src, el.dst) as g:
+        st = g.run(q, 0.01, 50)
+        compare_run(st, ref)
+        compare_state(g, og)
+        got = [c.tolist() for c in g.community_list()]
+        want = [c.tolist() for c in og.communities()]
+        assert got == want
+
+
+@pytest.mark.parametrize("el", [CASES[-2], CASES[-4], CASES[-5]], ids=[IDS[-2], IDS[-4], IDS[-5]])
+@pytest.mark.parametrize("q", [1, 7, 64])
+def test_per_queue_parity(lf, oracle_lib, el, q):
+    """State after an arbitrary number of queues, iteration ends included."""
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    nb = -(-og.n // q)
+    points = sorted({1, 2, 3, nb - 1, nb, nb + 1, 2 * nb + 5} - {0})
+    with lf.Graph(el.src, el.dst) as g:
+        for b in points:
+            og.run(q, -math.inf, 3, max_batches=b)
+            g.run(q, -math.inf, 3, max_batches=b)
+            compare_state(g, og)
+
+
+@pytest.mark.parametrize("el", [CASES[-2], CASES[-4], CASES[-5], CASES[0]], ids=[IDS[-2], IDS[-4], IDS[-5], IDS[0]])
+def test_block_tier_and_row_growth(lf, oracle_lib, el):
+    """Force every node onto the block-wide evaluation path and start from a
+    membership capacity of 2 so that the rows must grow."""
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(16, -math.inf, 6)
+    with lf.Graph(el.src, el.dst, warp_max_degree=1, member_slots=2) as g:
+        st = g.run(16, -math.inf, 6)
+        compare_run(st, ref)
+        compare_state(g, og)
+
+
+def test_graph_replay_equals_direct_launches_and_reruns(lf, oracle_lib):
+    el = W.eu_core_like(seed=2)
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(32, 0.01, 50)
+    with lf.Graph(el.src, el.dst, use_graphs=False) as g1, lf.Graph(el.src, el.dst) as g2:
+        a = g1.run(32, 0.01, 50)
+        b = g2.run(32, 0.01, 50)
+        c = g2.run(32, 0.01, 50)    # same handle again: restarts from the initial clustering
+        for st in (a, b, c):
+            compare_run(st, ref)
+        compare_state(g2, og)
+
+
+def test_device_edge_input_equals_host_input(lf, oracle_lib):
+    import torch
+    el = W.eu_core_like(seed=4)
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(8, 0.01, 50)
+    s = torch.from_numpy(el.src).cuda()
+    d = torch.from_numpy(el.dst).cuda()
+    with lf.Graph(s, d) as g:
+        compare_preprocessing(g, og)
+        compare_run(g.run(8, 0.01, 50), ref)
+    with lf.Graph(el.src, el.dst, allocator="cuda") as g:
+        compare_run(g.run(8, 0.01, 50), ref)
+
+
+def test_edge_cases(lf, oracle_lib):
+    # empty edge list
+    with lf.Graph(np.zeros(0, np.int32), np.zeros(0, np.int32)) as g:
+        assert (g.n, g.m) == (0, 0)
+        st = g.run(4, 0.01, 5)
+        assert st.iterations == 1 and st.wcc_initial == 0.0
+        off, mem = g.communities()
+        assert off.tolist() == [0] and mem.shape[0] == 0
+    # only self-loops and duplicates of one edge; ids near the int32 limit
+    big = 2**31 - 1
+    src = np.array([5, 5, big, big - 7, big], np.int32)
+    dst = np.array([5, 5, big - 7, big, big - 7], np.int32)
+    og = oracle_lib.OracleGraph(src, dst)
+    with lf.Graph(src, dst) as g:
+        assert (g.n, g.m) == (2, 1)
+        compare_preprocessing(g, og)
+        compare_run(g.run(1, 0.01, 10), og.run(1, 0.01, 10))
+    # max_iters = 0: the initial clustering is the result (singletons kept)
+    el = W.from_pairs(W.clique(4) + [(0, 4)])
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(1, 0.01, 0)
+    with lf.Graph(el.src, el.dst) as g:
+        st = g.run(1, 0.01, 0)
+        assert st.iterations == 0 and st.wcc_initial == ref["T0"]
+        assert [c.tolist() for c in g.community_list()] == [[0, 1, 2, 3], [4]]
+    # invalid arguments
+    with pytest.raises(lf.LazyFoxError):
+        lf.Graph(np.array([0, -3], np.int32), np.array([1, 2], np.int32))
+    with lf.Graph(el.src, el.dst) as g:
+        with pytest.raises(lf.LazyFoxError):
+            g.run(0, 0.01, 5)
+        with pytest.raises(lf.LazyFoxError):
+            g.run(4, 0.01, -1)
+        with pytest.raises(lf.LazyFoxError):
+            g.communities()   # before any run
+
+
+@pytest.mark.parametrize("q", [64, 1024])
+def test_full_size_335k_parity(lf, oracle_lib, q):
+    """The 335k-node / ~0.93M-edge workload at full size, in the configuration
+    the benchmark times: every output compared with the oracle."""
+    el = W.dblp_like()
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(q, 0.01, 50)
+    with lf.Graph(el.src, el.dst) as g:
+        compare_preprocessing(g, og)
+        st = g.run(q, 0.01, 50)
+        compare_run(st, ref)
+        compare_state(g, og)
+        off, mem = g.communities()
+        want = og.communities()
+        assert off.shape[0] - 1 == len(want)
+        assert np.array_equal(mem, np.concatenate(want))
