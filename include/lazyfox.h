@@ -65,6 +65,8 @@ typedef struct lf_options {
                                 kernels (tuning and tests) */
     int32_t use_graphs;      /* 0: default (capture each iteration in a CUDA graph);
                                 -1: launch kernels directly */
+    int32_t profile;         /* 1: time every move-evaluation launch with CUDA events and
+                                count its algorithmic bytes (lf_run_stats.prof_*) */
 } lf_options;
 
 /* Per-run statistics.  The history pointers are optional caller buffers with
@@ -83,6 +85,12 @@ typedef struct lf_run_stats {
     double *wcc_history;     /* WCC-hat(P) after iterations 1..iterations */
     int64_t *joins_history;  /* join actions applied per iteration */
     int64_t *leaves_history; /* leave actions applied per iteration */
+    int64_t num_launches;    /* kernels launched by the call */
+    int64_t prof_eval_launches; /* profile mode: move-evaluation launches timed */
+    double prof_eval_ms;     /* profile mode: their summed device time */
+    int64_t prof_eval_bytes; /* profile mode: their algorithmic bytes: per node 28 + 4|M(x)|,
+                                per neighbour y 8 + 4|M(y)|, 16 per distinct candidate
+                                community, 16 for the actions written */
 } lf_run_stats;
 
 /* Device times of the phases of lf_graph_create. */
@@ -96,6 +104,7 @@ typedef struct lf_create_stats {
     double ms_vt;            /* vt(x,V) */
     double ms_order;         /* local CC, node order, global cc */
     int64_t merge_bytes;     /* sum over oriented edges u->v of 4*(d+(u) + d+(v)) */
+    int64_t num_launches;    /* kernels launched by lf_graph_create */
 } lf_create_stats;
 
 /*

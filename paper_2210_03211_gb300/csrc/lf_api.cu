@@ -171,6 +171,7 @@ lf_status lf_graph_create(const int32_t *src, const int32_t *dst, int64_t num_ed
             if (opt->member_slots > 0) g->member_slots = opt->member_slots;
             g->warp_max_degree = opt->warp_max_degree;
             g->use_graphs = opt->use_graphs < 0 ? 0 : 1;
+            g->profile = opt->profile == 1 ? 1 : 0;
             if ((g->alloc_cb == nullptr) != (g->free_cb == nullptr))
                 fail(LF_ERR_INVALID, "alloc and free callbacks must be set together");
         }
@@ -347,11 +348,11 @@ lf_status lf_get_communities(lf_graph *g, int64_t *offsets, int64_t offsets_cap,
         const int64_t n = g->n, nc = g->ncomm;
         // memberships as (community << 32 | node), sorted: communities ascending, members ascending
         int64_t *moff = dalloc_n<int64_t>(g, n + 1);
-        k_member_counts<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(g->nmem, n, moff);
+        k_member_counts<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(g->nmem, n, moff); ++g->launches;
         LF_LAUNCHED();
         scan_exclusive<int64_t>(g, moff, moff, n, moff + n);
         uint32_t *rank = dalloc_n<uint32_t>(g, nc + 1);
-        k_live_flags<<<grid_for(nc, 256, 1 << 16), 256, 0, st>>>(g->comm, nc, rank);
+        k_live_flags<<<grid_for(nc, 256, 1 << 16), 256, 0, st>>>(g->comm, nc, rank); ++g->launches;
         LF_LAUNCHED();
         scan_exclusive<uint32_t>(g, rank, rank, nc, rank + nc);
         int64_t M = 0;
@@ -371,7 +372,7 @@ lf_status lf_get_communities(lf_graph *g, int64_t *offsets, int64_t offsets_cap,
         if (want) {
             unsigned long long *keys = dalloc_n<unsigned long long>(g, M);
             CommKeyArgs ka{g->mem, g->nmem, g->K};
-            k_member_keys<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(ka, n, moff, keys);
+            k_member_keys<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(ka, n, moff, keys); ++g->launches;
             LF_LAUNCHED();
             std::vector<int> sh;
             const int bx = bits_for((unsigned long long)(n > 0 ? n - 1 : 0));
@@ -381,7 +382,7 @@ lf_status lf_get_communities(lf_graph *g, int64_t *offsets, int64_t offsets_cap,
             radix_sort(g, keys, nullptr, M, sh);
             int64_t *d_off = dalloc_n<int64_t>(g, (int64_t)L + 1);
             int32_t *d_mem = dalloc_n<int32_t>(g, M);
-            k_comm_output<<<grid_for(M, 256, 1 << 16), 256, 0, st>>>(keys, M, rank, g->labels, d_off, d_mem, L);
+            k_comm_output<<<grid_for(M, 256, 1 << 16), 256, 0, st>>>(keys, M, rank, g->labels, d_off, d_mem, L); ++g->launches;
             LF_LAUNCHED();
             d2h(g, offsets, d_off, (int64_t)L + 1);
             d2h(g, members, d_mem, M);

@@ -526,7 +526,7 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
     unsigned long long nonloops = 0;
     int32_t max_id = -1, neg = 0;
     if (E > 0) {
-        k_id_range<<<grid_for(E, 256, 4096), 256, 0, st>>>(dsrc, ddst, E, ds, tmp64);
+        k_id_range<<<grid_for(E, 256, 4096), 256, 0, st>>>(dsrc, ddst, E, ds, tmp64); ++g->launches;
         LF_LAUNCHED();
         nonloops = read_scalar(g, tmp64);
         max_id = read_scalar(g, &ds->max_id);
@@ -542,21 +542,21 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
         uint32_t *bm = dalloc_n<uint32_t>(g, nwords);
         uint32_t *wb = dalloc_n<uint32_t>(g, nwords + 1);
         LF_CUDA(cudaMemsetAsync(bm, 0, (size_t)nwords * 4, st));
-        k_mark_ids<<<grid_for(E, 256, 4096), 256, 0, st>>>(dsrc, ddst, E, bm);
+        k_mark_ids<<<grid_for(E, 256, 4096), 256, 0, st>>>(dsrc, ddst, E, bm); ++g->launches;
         LF_LAUNCHED();
-        k_word_popc<<<grid_for(nwords, 256, 4096), 256, 0, st>>>(bm, nwords, wb);
+        k_word_popc<<<grid_for(nwords, 256, 4096), 256, 0, st>>>(bm, nwords, wb); ++g->launches;
         LF_LAUNCHED();
         scan_exclusive<uint32_t>(g, wb, wb, nwords, wb + nwords);
         n = read_scalar(g, wb + nwords);
         g->n = n;
         g->labels = dalloc_n<int32_t>(g, n);
-        k_labels<<<grid_for(nwords, 256, 4096), 256, 0, st>>>(bm, wb, nwords, g->labels);
+        k_labels<<<grid_for(nwords, 256, 4096), 256, 0, st>>>(bm, wb, nwords, g->labels); ++g->launches;
         LF_LAUNCHED();
         // both directions of every pair, sorted by (row, col), duplicates dropped
         int64_t nkeys = 2 * (int64_t)nonloops;
         unsigned long long *keys = dalloc_n<unsigned long long>(g, nkeys);
         LF_CUDA(cudaMemsetAsync(tmp64, 0, sizeof(unsigned long long), st));
-        k_make_keys<<<grid_for(E, 256, 4096), 256, 0, st>>>(dsrc, ddst, E, bm, wb, keys, tmp64);
+        k_make_keys<<<grid_for(E, 256, 4096), 256, 0, st>>>(dsrc, ddst, E, bm, wb, keys, tmp64); ++g->launches;
         LF_LAUNCHED();
         dfree(g, wb);
         dfree(g, bm);
@@ -568,21 +568,21 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
         radix_sort(g, keys, nullptr, nkeys, shifts);
         uint32_t *flag = dalloc_n<uint32_t>(g, nkeys + 1);
         uint32_t *idx = dalloc_n<uint32_t>(g, nkeys + 1);
-        k_unique_flags<<<grid_for(nkeys, 256, 8192), 256, 0, st>>>(keys, nkeys, flag);
+        k_unique_flags<<<grid_for(nkeys, 256, 8192), 256, 0, st>>>(keys, nkeys, flag); ++g->launches;
         LF_LAUNCHED();
         scan_exclusive<uint32_t>(g, flag, idx, nkeys, idx + nkeys);
         two_m = read_scalar(g, idx + nkeys);
         g->m = two_m / 2;
         g->adj = dalloc_n<int32_t>(g, two_m);
         g->off = dalloc_n<int64_t>(g, n + 1);
-        k_unique_compact<<<grid_for(nkeys, 256, 8192), 256, 0, st>>>(keys, nkeys, flag, idx, g->adj, g->off);
+        k_unique_compact<<<grid_for(nkeys, 256, 8192), 256, 0, st>>>(keys, nkeys, flag, idx, g->adj, g->off); ++g->launches;
         LF_LAUNCHED();
         dfree(g, idx);
         dfree(g, flag);
         dfree(g, keys);
         g->deg = dalloc_n<int32_t>(g, n);
         LF_CUDA(cudaMemsetAsync(&ds->count32, 0, sizeof(int32_t), st));
-        k_degrees<<<grid_for(n, 256, 8192), 256, 0, st>>>(g->off, n, two_m, g->off + n, g->deg, ds);
+        k_degrees<<<grid_for(n, 256, 8192), 256, 0, st>>>(g->off, n, two_m, g->off + n, g->deg, ds); ++g->launches;
         LF_LAUNCHED();
         g->max_deg = read_scalar(g, &ds->count32);
     } else {
@@ -603,11 +603,11 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
     g->oadj = dalloc_n<int32_t>(g, m);
     if (n > 0) {
         int64_t *odeg = dalloc_n<int64_t>(g, n);
-        k_out_degree<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->off, g->adj, g->deg, n, odeg);
+        k_out_degree<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->off, g->adj, g->deg, n, odeg); ++g->launches;
         LF_LAUNCHED();
         scan_exclusive<int64_t>(g, odeg, g->ooff, n, g->ooff + n);
         dfree(g, odeg);
-        k_orient_fill<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->off, g->adj, g->deg, n, g->ooff, g->oadj);
+        k_orient_fill<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->off, g->adj, g->deg, n, g->ooff, g->oadj); ++g->launches;
         LF_LAUNCHED();
     } else {
         LF_CUDA(cudaMemsetAsync(g->ooff, 0, sizeof(int64_t), st));
@@ -626,19 +626,19 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
         int32_t *hubs = dalloc_n<int32_t>(g, n);
         uint32_t *nh = reinterpret_cast<uint32_t *>(tmp64);
         LF_CUDA(cudaMemsetAsync(nh, 0, sizeof(uint32_t), st));
-        k_select_hubs<<<grid_for(n, 256, 8192), 256, 0, st>>>(g->ooff, n, hubs, nh);
+        k_select_hubs<<<grid_for(n, 256, 8192), 256, 0, st>>>(g->ooff, n, hubs, nh); ++g->launches;
         LF_LAUNCHED();
-        k_tri_warp<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->ooff, g->oadj, n, utri, sup, ds);
+        k_tri_warp<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->ooff, g->oadj, n, utri, sup, ds); ++g->launches;
         LF_LAUNCHED();
         const size_t smem = (size_t)TRI_BLOCK_LIST * 9;
         LF_CUDA(cudaFuncSetAttribute(k_tri_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_tri_block<<<304, TRI_BLOCK_THREADS, smem, st>>>(g->ooff, g->oadj, hubs, nh, utri, sup, ds);
+        k_tri_block<<<304, TRI_BLOCK_THREADS, smem, st>>>(g->ooff, g->oadj, hubs, nh, utri, sup, ds); ++g->launches;
         LF_LAUNCHED();
         dfree(g, hubs);
     }
     pt.mark();   // 3
     if (n > 0) {
-        k_vt<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->ooff, g->oadj, sup, n, g->vt, ds);
+        k_vt<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->ooff, g->oadj, sup, n, g->vt, ds); ++g->launches;
         LF_LAUNCHED();
     }
     dfree(g, sup);
@@ -650,31 +650,31 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
     if (n > 0) {
         unsigned long long *keys = dalloc_n<unsigned long long>(g, n);
         uint32_t *vals = dalloc_n<uint32_t>(g, n);
-        k_order_keys_deg<<<grid_for(n, 256, 8192), 256, 0, st>>>(g->deg, n, g->max_deg, keys, vals);
+        k_order_keys_deg<<<grid_for(n, 256, 8192), 256, 0, st>>>(g->deg, n, g->max_deg, keys, vals); ++g->launches;
         LF_LAUNCHED();
         std::vector<int> sh;
         for (int s = 0; s < bits_for((unsigned long long)g->max_deg); s += 8) sh.push_back(s);
         radix_sort(g, keys, vals, n, sh);
-        k_order_keys_cc<<<grid_for(n, 256, 8192), 256, 0, st>>>(utri, g->deg, n, vals, keys);
+        k_order_keys_cc<<<grid_for(n, 256, 8192), 256, 0, st>>>(utri, g->deg, n, vals, keys); ++g->launches;
         LF_LAUNCHED();
         sh.clear();
         for (int s = 0; s < 62; s += 8) sh.push_back(s);
         radix_sort(g, keys, vals, n, sh);
         LF_CUDA(cudaMemsetAsync(&ds->bad_runs, 0, sizeof(int32_t), st));
-        k_order_check<<<grid_for(n, 256, 8192), 256, 0, st>>>(keys, vals, utri, g->deg, n, ds);
+        k_order_check<<<grid_for(n, 256, 8192), 256, 0, st>>>(keys, vals, utri, g->deg, n, ds); ++g->launches;
         LF_LAUNCHED();
         if (read_scalar(g, &ds->bad_runs) > 0) {
-            k_order_fix<<<1, 1, 0, st>>>(keys, vals, utri, g->deg, n);
+            k_order_fix<<<1, 1, 0, st>>>(keys, vals, utri, g->deg, n); ++g->launches;
             LF_LAUNCHED();
         }
-        k_positions<<<grid_for(n, 256, 8192), 256, 0, st>>>(vals, n, g->order, g->pos);
+        k_positions<<<grid_for(n, 256, 8192), 256, 0, st>>>(vals, n, g->order, g->pos); ++g->launches;
         LF_LAUNCHED();
         dfree(g, vals);
         dfree(g, keys);
-        k_cc_sum<<<grid_for(n, 256, 1024), 256, 0, st>>>(utri, g->deg, n, ds);
+        k_cc_sum<<<grid_for(n, 256, 1024), 256, 0, st>>>(utri, g->deg, n, ds); ++g->launches;
         LF_LAUNCHED();
     }
-    k_cc_final<<<1, 32, 0, st>>>(ds, n);
+    k_cc_final<<<1, 32, 0, st>>>(ds, n); ++g->launches;
     LF_LAUNCHED();
     pt.mark();   // 5
     dfree(g, tmp64);
@@ -690,6 +690,7 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
     cs.ms_triangles = pt.ms(2, 3);
     cs.ms_vt = pt.ms(3, 4);
     cs.ms_order = pt.ms(4, 5);
+    cs.num_launches = (int64_t)g->launches;
 }
 
 }  // namespace lf

@@ -60,6 +60,7 @@ struct DevScalars {
     unsigned long long merge_bytes;         // triangle merge-stream bytes
     unsigned long long live_comms;          // communities with n >= 2 after pruning
     unsigned long long memberships;         // sum of row counts after pruning
+    unsigned long long prof_bytes;          // profile mode: move-evaluation algorithmic bytes
     int32_t maxcnt;                         // max memberships of a node (after pruning)
     int32_t kb;                             // bound on memberships during an iteration
     int32_t err;                            // DERR_* bits
@@ -94,6 +95,8 @@ struct lf_graph {
     int32_t member_slots = 4;
     int32_t warp_max_degree = 0;
     int32_t use_graphs = 1;
+    int32_t profile = 0;
+    unsigned long long launches = 0;               // kernels launched (host count)
     std::vector<std::pair<void *, size_t>> live;   // outstanding allocations
 
     // graph
@@ -127,6 +130,8 @@ struct lf_graph {
     int32_t *act = nullptr;       // 4*qcap: join, leave, kjoin, kleave
     cudaGraphExec_t iter_exec = nullptr;
     int32_t graph_q = 0, graph_K = 0;
+    unsigned long long graph_kernels = 0;          // kernel nodes of iter_exec
+    std::vector<cudaEvent_t> prof_ev;              // profile mode: 2 per queue
 };
 
 namespace lf {

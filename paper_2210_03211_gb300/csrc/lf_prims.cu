@@ -88,6 +88,7 @@ void scan_exclusive(lf_graph *g, const T *in, T *out, int64_t count, T *d_total)
     if (nb == 1) {
         k_scan_down<T><<<1, SCAN_THREADS, 0, g->stream>>>(in, out, count, nullptr, d_total);
         LF_LAUNCHED();
+        g->launches += 1;
         return;
     }
     T *sums = dalloc_n<T>(g, nb);
@@ -96,6 +97,7 @@ void scan_exclusive(lf_graph *g, const T *in, T *out, int64_t count, T *d_total)
     scan_exclusive<T>(g, sums, sums, nb, nullptr);
     k_scan_down<T><<<(unsigned)nb, SCAN_THREADS, 0, g->stream>>>(in, out, count, sums, d_total);
     LF_LAUNCHED();
+    g->launches += 2;
     dfree(g, sums);
 }
 
@@ -210,6 +212,7 @@ void radix_sort(lf_graph *g, unsigned long long *keys, uint32_t *vals, int64_t c
         scan_exclusive<uint32_t>(g, counts, counts, (int64_t)256 * nb, nullptr);
         k_rs_scatter<<<nb, RS_THREADS, 0, g->stream>>>(ka, va, kb, vb, count, shift, counts, nb);
         LF_LAUNCHED();
+        g->launches += 2;
         std::swap(ka, kb);
         std::swap(va, vb);
     }

@@ -39,6 +39,7 @@ struct RunArgs {
     double cc;
     int64_t nbatches;
     int32_t warp_max_deg;
+    int32_t profile;   // count algorithmic bytes of the move evaluation
 };
 
 // ---------------------------------------------------------------------------
@@ -240,12 +241,14 @@ __device__ void eval_warp(const RunArgs &a, int i, int32_t x, int32_t d, int64_t
     for (int j = lane; j < cx; j += 32) ht_insert(keys, vals, hm, rowx[j], 0u, true);
     __syncwarp();
     const int64_t beg = a.off[x], end = a.off[x + 1];
+    unsigned long long pb = 0;
     for (int64_t p0 = beg; p0 < end; p0 += 32) {
         const int64_t p = p0 + lane;
         int32_t y = 0, cy = 0;
         if (p < end) {
             y = a.adj[p];
             cy = a.nmem[y];
+            pb += 8ull + 4ull * (unsigned long long)cy;
         }
         const int32_t cmax = __reduce_max_sync(FULL, cy);
         const int32_t *rowy = a.mem + (int64_t)y * a.K;
@@ -259,10 +262,18 @@ __device__ void eval_warp(const RunArgs &a, int i, int32_t x, int32_t d, int64_t
     Best bj{0.0, -1, 0}, bl{0.0, -1, 0};
     for (uint32_t s = lane; s < H; s += 32) {
         int32_t C = keys[s];
-        if (C != EMPTY_KEY) eval_candidate(a, C, vals[s], d, bj, bl);
+        if (C != EMPTY_KEY) {
+            eval_candidate(a, C, vals[s], d, bj, bl);
+            pb += 16ull;
+        }
     }
     warp_best(bj);
     warp_best(bl);
+    if (a.profile) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pb += __shfl_down_sync(FULL, pb, o);
+        if (lane == 0) atomicAdd(&a.ds->prof_bytes, pb + 44ull + 4ull * (unsigned long long)cx);
+    }
     if (lane == 0) write_action(a, i, bj, bl, serial);
     __syncwarp();
 }
@@ -289,9 +300,11 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
     const int64_t beg = a.off[x], end = a.off[x + 1];
     int P = bound <= HB / 2 ? 1 : (int)((bound + HB / 4 - 1) / (HB / 4));
     Best bj, bl;
+    unsigned long long pb = 0;
     for (;;) {
         bj = Best{0.0, -1, 0};
         bl = Best{0.0, -1, 0};
+        pb = 0;
         uint32_t H = HB;
         if (P == 1) {
             H = 32;
@@ -318,6 +331,7 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
                 if (p < end) {
                     y = a.adj[p];
                     cy = a.nmem[y];
+                    if (part == 0) pb += 8ull + 4ull * (unsigned long long)cy;
                 }
                 const int32_t cmax = __reduce_max_sync(FULL, cy);
                 const int32_t *rowy = a.mem + (int64_t)y * a.K;
@@ -338,7 +352,10 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
             }
             for (uint32_t s = threadIdx.x; s < H; s += EV_THREADS) {
                 int32_t C = keys[s];
-                if (C != EMPTY_KEY) eval_candidate(a, C, vals[s], d, bj, bl);
+                if (C != EMPTY_KEY) {
+                    eval_candidate(a, C, vals[s], d, bj, bl);
+                    pb += 16ull;
+                }
             }
             __syncthreads();
         }
@@ -351,6 +368,11 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
     }
     warp_best(bj);
     warp_best(bl);
+    if (a.profile) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pb += __shfl_down_sync(FULL, pb, o);
+        if (lane == 0) atomicAdd(&a.ds->prof_bytes, pb + (w == 0 ? 44ull + 4ull * (unsigned long long)cx : 0ull));
+    }
     if (lane == 0) {
         bs.gj[w] = bj.g; bs.cj[w] = bj.c; bs.kj[w] = bj.k;
         bs.gl[w] = bl.g; bs.cl[w] = bl.c; bs.kl[w] = bl.k;
@@ -623,6 +645,7 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.cc = g->cc;
     a.nbatches = 0;
     a.warp_max_deg = g->warp_max_degree > 0 ? g->warp_max_degree : 0x7fffffff;
+    a.profile = g->profile;
     return a;
 }
 
@@ -632,20 +655,23 @@ Readback *device_readback(lf_graph *g) {
 }
 
 void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int64_t count) {
+    const bool prof = g->profile && (int64_t)g->prof_ev.size() >= 2 * (first + count);
     for (int64_t b = first; b < first + count; ++b) {
         const int64_t bstart = b * q;
         const int32_t blen = (int32_t)std::min<int64_t>(q, g->n - bstart);
-        k_eval<<<(unsigned)((blen + EV_WARPS - 1) / EV_WARPS), EV_THREADS, 0, g->stream>>>(a, bstart, blen, b);
-        k_apply<<<grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30), AP_THREADS, 0, g->stream>>>(a, bstart, blen, b);
+        if (prof) LF_CUDA(cudaEventRecord(g->prof_ev[2 * b], g->stream));
+        k_eval<<<(unsigned)((blen + EV_WARPS - 1) / EV_WARPS), EV_THREADS, 0, g->stream>>>(a, bstart, blen, b); ++g->launches;
+        if (prof) LF_CUDA(cudaEventRecord(g->prof_ev[2 * b + 1], g->stream));
+        k_apply<<<grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30), AP_THREADS, 0, g->stream>>>(a, bstart, blen, b); ++g->launches;
     }
     LF_LAUNCHED();
 }
 
 void launch_iteration_end(lf_graph *g, const RunArgs &a) {
     const int64_t n = g->n;
-    k_prune<<<grid_for(n + g->ncomm, 256, 1 << 16), 256, 0, g->stream>>>(a, n, g->ncomm);
-    k_total<<<grid_for(n * 32, 256, 1 << 16), 256, 0, g->stream>>>(a, n);
-    k_finalize<<<1, 32, 0, g->stream>>>(g->ds, device_readback(g), 1);
+    k_prune<<<grid_for(n + g->ncomm, 256, 1 << 16), 256, 0, g->stream>>>(a, n, g->ncomm); ++g->launches;
+    k_total<<<grid_for(n * 32, 256, 1 << 16), 256, 0, g->stream>>>(a, n); ++g->launches;
+    k_finalize<<<1, 32, 0, g->stream>>>(g->ds, device_readback(g), 1); ++g->launches;
     LF_LAUNCHED();
     LF_CUDA(cudaMemcpyAsync(g->rb, device_readback(g), sizeof(Readback), cudaMemcpyDeviceToHost, g->stream));
 }
@@ -679,7 +705,7 @@ void grow_rows(lf_graph *g, int32_t need) {
     while (K2 < need) K2 *= 2;
     if (K2 == g->K) return;
     int32_t *mem2 = dalloc_n<int32_t>(g, g->n * K2);
-    k_regrow<<<grid_for(g->n, 256, 1 << 16), 256, 0, g->stream>>>(g->mem, g->nmem, g->n, g->K, mem2, K2);
+    k_regrow<<<grid_for(g->n, 256, 1 << 16), 256, 0, g->stream>>>(g->mem, g->nmem, g->n, g->K, mem2, K2); ++g->launches;
     LF_LAUNCHED();
     dfree(g, g->mem);
     g->mem = mem2;
@@ -697,6 +723,8 @@ double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
 
 void free_run_state(lf_graph *g) {
     drop_graph(g);
+    for (auto e : g->prof_ev) cudaEventDestroy(e);
+    g->prof_ev.clear();
     if (g->act) dfree(g, g->act);
     if (g->mem) dfree(g, g->mem);
     if (g->nmem) dfree(g, g->nmem);
@@ -741,6 +769,18 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         LF_CUDA(cudaStreamSynchronize(st));
     }
     RunArgs a = make_args(g, device_readback(g));
+    const unsigned long long launches0 = g->launches;
+    const int64_t nb_all = n > 0 ? (n + q - 1) / q : 0;
+    if (g->profile && (int64_t)g->prof_ev.size() < 2 * nb_all) {
+        drop_graph(g);   // a captured graph would not record the new events
+        while ((int64_t)g->prof_ev.size() < 2 * nb_all) {
+            cudaEvent_t e;
+            LF_CUDA(cudaEventCreate(&e));
+            g->prof_ev.push_back(e);
+        }
+    }
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
 
     // ---- a6: initial clustering
     int64_t k0 = 0;
@@ -750,7 +790,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         LF_CUDA(cudaMemsetAsync(state, 0, (size_t)n * 4, st));
         for (int round = 0;; ++round) {
             LF_CUDA(cudaMemsetAsync(und, 0, 4, st));
-            k_mis_round<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->off, g->adj, g->pos, n, state, und);
+            k_mis_round<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->off, g->adj, g->pos, n, state, und); ++g->launches;
             LF_LAUNCHED();
             int32_t left = 0;
             LF_CUDA(cudaMemcpyAsync(&left, und, 4, cudaMemcpyDeviceToHost, st));
@@ -759,15 +799,15 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             if (round > n + 2) fail(LF_ERR_CUDA, "initial clustering did not converge");
         }
         uint32_t *flag = dalloc_n<uint32_t>(g, n + 1);
-        k_seed_flags<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(g->order, state, n, flag);
+        k_seed_flags<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(g->order, state, n, flag); ++g->launches;
         LF_LAUNCHED();
         scan_exclusive<uint32_t>(g, flag, flag, n, flag + n);
         uint32_t kk = 0;
         LF_CUDA(cudaMemcpyAsync(&kk, flag + n, 4, cudaMemcpyDeviceToHost, st));
         int32_t *comm_of = dalloc_n<int32_t>(g, n);
-        k_assign<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->off, g->adj, g->pos, state, flag, n, comm_of);
-        k_init_rows<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(a, comm_of, n);
-        k_init_m2<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(a, comm_of, n);
+        k_assign<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->off, g->adj, g->pos, state, flag, n, comm_of); ++g->launches;
+        k_init_rows<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(a, comm_of, n); ++g->launches;
+        k_init_m2<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(a, comm_of, n); ++g->launches;
         LF_LAUNCHED();
         LF_CUDA(cudaStreamSynchronize(st));
         k0 = kk;
@@ -777,8 +817,8 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         dfree(g, state);
     }
     g->ncomm = k0;
-    k_total<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(a, n);
-    k_finalize<<<1, 32, 0, st>>>(g->ds, device_readback(g), 0);
+    k_total<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(a, n); ++g->launches;
+    k_finalize<<<1, 32, 0, st>>>(g->ds, device_readback(g), 0); ++g->launches;
     LF_LAUNCHED();
     LF_CUDA(cudaMemcpyAsync(g->rb, device_readback(g), sizeof(Readback), cudaMemcpyDeviceToHost, st));
     LF_CUDA(cudaEventRecord(ev[1], st));
@@ -807,6 +847,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             if (!g->iter_exec || g->graph_q != q || g->graph_K != g->K) {
                 drop_graph(g);
                 cudaGraph_t graph;
+                const unsigned long long before = g->launches;
                 LF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
                 try {
                     launch_batches(g, a, q, 0, nb);
@@ -818,6 +859,8 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
                     throw;
                 }
                 LF_CUDA(cudaStreamEndCapture(st, &graph));
+                g->graph_kernels = g->launches - before;
+                g->launches = before;
                 cudaError_t e = cudaGraphInstantiate(&g->iter_exec, graph, 0);
                 cudaGraphDestroy(graph);
                 LF_CUDA(e);
@@ -825,12 +868,17 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
                 g->graph_K = g->K;
             }
             LF_CUDA(cudaGraphLaunch(g->iter_exec, st));
+            g->launches += g->graph_kernels;
         } else {
             launch_batches(g, a, q, 0, nb);
             launch_iteration_end(g, a);
         }
         batches += nb;
         LF_CUDA(cudaStreamSynchronize(st));
+        if (g->profile) {
+            for (int64_t b = 0; b < nb; ++b) prof_ms += elapsed_ms(g->prof_ev[2 * b], g->prof_ev[2 * b + 1]);
+            prof_launches += nb;
+        }
         const Readback rb = *g->rb;
         if (rb.err & DERR_CAPACITY) fail(LF_ERR_CAPACITY, "membership row overflow (internal bound violated)");
         if (rb.err & DERR_CHECK) fail(LF_ERR_CUDA, "device consistency check failed (histogram partitioning)");
@@ -865,6 +913,14 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         stats->ms_init = elapsed_ms(ev[0], ev[1]);
         stats->ms_iterations = elapsed_ms(ev[1], ev[2]);
         stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        stats->num_launches = (int64_t)(g->launches - launches0);
+        stats->prof_eval_launches = prof_launches;
+        stats->prof_eval_ms = prof_ms;
+        unsigned long long pbytes = 0;
+        if (g->profile) {
+            LF_CUDA(cudaMemcpy(&pbytes, &g->ds->prof_bytes, 8, cudaMemcpyDeviceToHost));
+        }
+        stats->prof_eval_bytes = (int64_t)pbytes;
     }
 }
 

@@ -41,7 +41,7 @@ class Options(C.Structure):
     _fields_ = [("stream", C.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("edges_on_device", C.c_int32),
                 ("member_slots", C.c_int32), ("warp_max_degree", C.c_int32),
-                ("use_graphs", C.c_int32)]
+                ("use_graphs", C.c_int32), ("profile", C.c_int32)]
 
 
 class RunStatsC(C.Structure):
@@ -50,13 +50,16 @@ class RunStatsC(C.Structure):
                 ("num_memberships", C.c_int64), ("ms_total", C.c_double), ("ms_init", C.c_double),
                 ("ms_iterations", C.c_double), ("history_cap", C.c_int32),
                 ("wcc_history", C.POINTER(C.c_double)), ("joins_history", C.POINTER(C.c_int64)),
-                ("leaves_history", C.POINTER(C.c_int64))]
+                ("leaves_history", C.POINTER(C.c_int64)), ("num_launches", C.c_int64),
+                ("prof_eval_launches", C.c_int64), ("prof_eval_ms", C.c_double),
+                ("prof_eval_bytes", C.c_int64)]
 
 
 class CreateStatsC(C.Structure):
     _fields_ = [("num_nodes", C.c_int64), ("num_edges", C.c_int64), ("num_triangles", C.c_int64),
                 ("ms_csr", C.c_double), ("ms_orient", C.c_double), ("ms_triangles", C.c_double),
-                ("ms_vt", C.c_double), ("ms_order", C.c_double), ("merge_bytes", C.c_int64)]
+                ("ms_vt", C.c_double), ("ms_order", C.c_double), ("merge_bytes", C.c_int64),
+                ("num_launches", C.c_int64)]
 
 
 _lib = None
@@ -141,6 +144,10 @@ class RunStats:
     ms_total: float
     ms_init: float
     ms_iterations: float
+    num_launches: int = 0
+    prof_eval_launches: int = 0
+    prof_eval_ms: float = 0.0
+    prof_eval_bytes: int = 0
 
 
 class Graph:
@@ -152,7 +159,7 @@ class Graph:
     """
 
     def __init__(self, src, dst, *, stream=None, allocator: str = "torch", member_slots: int = 0,
-                 warp_max_degree: int = 0, use_graphs: bool = True, device=None):
+                 warp_max_degree: int = 0, use_graphs: bool = True, profile: bool = False, device=None):
         import torch
         self._L = load_library()
         self._h = C.c_void_p()
@@ -177,6 +184,7 @@ class Graph:
         opt.member_slots = int(member_slots)
         opt.warp_max_degree = int(warp_max_degree)
         opt.use_graphs = 0 if use_graphs else -1
+        opt.profile = 1 if profile else 0
         if isinstance(src, torch.Tensor):
             if src.dtype != torch.int32 or dst.dtype != torch.int32 or not src.is_cuda:
                 raise TypeError("device edge lists must be int32 CUDA tensors")
@@ -241,7 +249,8 @@ class Graph:
         k = st.iterations
         return RunStats(k, bool(st.converged), st.num_batches, st.wcc_initial, T[:k].copy(), J[:k].copy(),
                         Lv[:k].copy(), st.num_communities, st.num_memberships, st.ms_total, st.ms_init,
-                        st.ms_iterations)
+                        st.ms_iterations, st.num_launches, st.prof_eval_launches, st.prof_eval_ms,
+                        st.prof_eval_bytes)
 
     def communities(self):
         """(offsets int64[k+1], members int32[...]) in original node ids."""
