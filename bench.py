@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Benchmark of the LazyFox hot path on one GB300 (or N replicas).
+
+One step = the whole hot path on one synthetic graph: lf_graph_create
+(self-loop/duplicate removal, relabel, CSR, orientation, triangles, vt, node
+order, cc) followed by lf_run (initial clustering, then LazyFox iterations of
+move evaluation + bulk apply per queue, pruning and the exact WCC-hat total,
+until the relative change falls below the threshold).
+
+value      = edges/s per iteration: m x iterations / step time, summed over the
+             timed steps (device-resident input, CUDA events on the library's
+             stream, L2 flushed by a 256 MiB write before every step).
+e2e        = the same metric through the public API from pinned host buffers:
+             host->device copy of the edge list, the run, and the device->host
+             read of the communities inside the timed region.
+roofline   = the move-evaluation kernel (the dominant kernel): algorithmic bytes
+             per launch / mean launch time (CUDA events around every launch in
+             the timed steps) against the measured HBM copy bandwidth.
+cpu_baseline = the sequential CPU oracle on the same workload (rank 0, N=1).
+
+--impl reference times the CPU oracle as the reference arm.
+Under torchrun every rank runs its own replica (no collective on the data
+path); value = edges x iterations of all ranks / max over ranks of the time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "edges/s per Fox iteration + triangle-count GB/s; batched graphs/s & p99 vs plain"
+UNIT = "edges/s per iteration"
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    # 335k nodes, ~0.93M edges, Chung-Lu gamma 2.5, max degree ~550, planted
+    # overlapping communities (sizes 6-2,000, 1-4 per node), seed 1
+    "dblp": dict(name="dblp_like_335k_nodes_0.93M_edges", gen=("dblp_like", {}), q=1024, q2=64,
+                 threshold=0.01, max_iters=50),
+    # 1,000 nodes, 20 planted communities, Fox (queue size 1)
+    "eu": dict(name="eu_core_like_1k_nodes_planted_er", gen=("eu_core_like", {}), q=1, q2=0,
+               threshold=0.01, max_iters=50),
+    # 3.07M nodes, Chung-Lu gamma 2.2, max degree ~33k, 20 iterations
+    "large": dict(name="large_like_3.07M_nodes", gen=("large_like", {}), q=65536, q2=1024,
+                  threshold=-math.inf, max_iters=20),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["lazyfox", "reference"], default="lazyfox")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dblp")
+    ap.add_argument("--queue-size", type=int, default=None)
+    ap.add_argument("--no-secondary", action="store_true", help="skip the second queue size")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(spec):
+    from paper_2210_03211_gb300 import workloads as W
+    fn, kw = spec["gen"]
+    return getattr(W, fn)(**kw)
+
+
+def measured_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001 - absent or unreadable: the recipe's fallback
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source has not changed since it was captured."""
+    import hashlib
+    summ = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(summ):
+        return None
+    vals = {}
+    for line in open(summ):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2210_03211_gb300", "csrc", vals.get("source", "lf_run.cu"))
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if vals.get("source_sha256_16") != sha:
+        return None
+    try:
+        return dict(bytes_per_launch=float(vals["dram_bytes_per_launch_scaled"]),
+                    workload=vals.get("captured_on", ""))
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(use_gpu_backend: bool):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if use_gpu_backend else "gloo")
+    return rank, world, local
+
+
+def reduce_max(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_oracle(el, q, threshold, max_iters):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    og = oracle.OracleGraph(el.src, el.dst)
+    r = og.run(q, threshold, max_iters)
+    dt = time.perf_counter() - t0
+    return og.m * r["iterations"], dt, r["iterations"]
+
+
+def run_reference(args, spec, q):
+    rank, world, _ = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
+    if rank != 0:
+        return 0
+    el = make_workload(spec)
+    for _ in range(args.warmup):
+        time_oracle(el, q, spec["threshold"], spec["max_iters"])
+    units, secs, iters = 0.0, 0.0, []
+    for _ in range(args.steps):
+        u, dt, it = time_oracle(el, q, spec["threshold"], spec["max_iters"])
+        units += u
+        secs += dt
+        iters.append(it)
+    value = units / secs
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": spec["name"], "queue_size": q, "threshold": spec["threshold"],
+                   "max_iters": spec["max_iters"], "iterations": iters},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full runs (preprocessing + all iterations) of the workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    spec = WORKLOADS[args.workload]
+    q = args.queue_size or spec["q"]
+    if args.impl == "reference":
+        return run_reference(args, spec, q)
+
+    import numpy as np
+    import torch
+
+    from paper_2210_03211_gb300 import lazyfox
+    from paper_2210_03211_gb300 import build as lf_build
+
+    rank, world, local = dist_setup(torch.cuda.is_available())
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU: the library has no CPU path")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        lf_build.build()
+    barrier(world)
+    lazyfox.load_library()
+    el = make_workload(spec)
+    src_d = torch.from_numpy(el.src).to(dev)
+    dst_d = torch.from_numpy(el.dst).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
+
+    def one_step(queue, profile, use_graphs=True):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g = lazyfox.Graph(src_d, dst_d, stream=stream, profile=profile, use_graphs=use_graphs)
+        st = g.run(queue, spec["threshold"], spec["max_iters"])
+        e1.record(stream)
+        cs = g.create_stats()
+        g.close()
+        stream.synchronize()
+        return e0.elapsed_time(e1), st, cs
+
+    def timed(queue, steps, warmup):
+        for _ in range(warmup):
+            one_step(queue, False)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        res = [one_step(queue, True) for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        return res
+
+    gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else str(local)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:  # noqa: BLE001 - older torch: fall back to the index
+        pass
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    res = timed(q, args.steps, args.warmup)
+    clocks = sampler.stop()
+
+    m = res[0][2]["num_edges"]
+    local_units = sum(m * r[1].iterations for r in res)
+    local_ms = sum(r[0] for r in res)
+    total_ms = reduce_max(local_ms, world, dev)
+    units = reduce_sum(local_units, world, dev)
+    value = units / (total_ms / 1e3)
+    # triangle-count throughput: merge-stream bytes / triangle kernel time
+    tri_gbs = statistics.median(r[2]["merge_bytes"] / (r[2]["ms_triangles"] / 1e3) / 1e9 for r in res
+                                if r[2]["ms_triangles"] > 0) if m > 0 else 0.0
+    launches = sum(r[2]["num_launches"] + r[1].num_launches for r in res)
+    prof = res
+    roofline_src = "timed steps (event pairs inside the captured iteration graphs)"
+    if any(math.isnan(r[1].prof_move_ms) for r in res):
+        # event timing inside graphs unavailable: time the kernel in extra steps
+        # of the same workload launched directly (kernel time does not depend
+        # on the launch mode)
+        prof = [one_step(q, True, use_graphs=False) for _ in range(max(1, min(args.steps, 2)))]
+        roofline_src = "extra steps with direct launches after the timed region"
+    ev_bytes = sum(r[1].prof_move_bytes for r in prof)
+    ev_ms = sum(r[1].prof_move_ms for r in prof)
+    ev_launches = sum(r[1].prof_move_launches for r in prof)
+    peak, peak_kind = measured_hbm()
+    achieved = (ev_bytes / (ev_ms / 1e3) / 1e9) if ev_ms > 0 else 0.0
+    traffic = ncu_traffic("k_eval")
+    roofline = {"kernel": "k_eval (move evaluation, one launch per queue)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": achieved / peak, "bytes_per_launch": ev_bytes / max(1, ev_launches),
+                "mean_launch_us": 1e3 * ev_ms / max(1, ev_launches), "launches": ev_launches,
+                "traffic": traffic["bytes_per_launch"] if traffic else None, "timed_in": roofline_src}
+
+    secondary = None
+    if spec["q2"] and not args.no_secondary:
+        res2 = timed(spec["q2"], args.steps, 1)
+        u2 = sum(m * r[1].iterations for r in res2)
+        ms2 = reduce_max(sum(r[0] for r in res2), world, dev)
+        secondary = {"queue_size": spec["q2"], "value": reduce_sum(u2, world, dev) / (ms2 / 1e3),
+                     "ms_per_step": ms2 / len(res2), "iterations": [r[1].iterations for r in res2]}
+
+    e2e = None
+    if not args.no_e2e:
+        src_h = torch.from_numpy(el.src).pin_memory()
+        dst_h = torch.from_numpy(el.dst).pin_memory()
+        src_np, dst_np = src_h.numpy(), dst_h.numpy()
+        e_units, e_secs, d2h = 0.0, 0.0, 0
+        nsteps = max(1, min(args.steps, 3))
+        for i in range(nsteps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            g = lazyfox.Graph(src_np, dst_np)
+            st = g.run(q, spec["threshold"], spec["max_iters"])
+            off, mem = g.communities()
+            t1 = time.perf_counter()
+            g.close()
+            if i == 0:
+                continue   # first call pays one-time host setup; not timed
+            e_units += g.m * st.iterations
+            e_secs += t1 - t0
+            d2h = off.nbytes + mem.nbytes + 48 * (st.iterations + 1)
+        e_secs = reduce_max(e_secs, world, dev)
+        e_units = reduce_sum(e_units, world, dev)
+        e2e = {"value": e_units / e_secs, "unit": UNIT, "h2d_bytes_per_step": int(el.src.nbytes + el.dst.nbytes),
+               "d2h_bytes_per_step": int(d2h), "steps": nsteps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        u, dt, it = time_oracle(el, q, spec["threshold"], spec["max_iters"])
+        cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full run (preprocessing + {it} iterations) of the same workload at queue size {q}",
+               "seconds": dt}
+
+    if rank == 0:
+        r0 = res[0]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
+            "config": {"workload": spec["name"], "n": r0[2]["num_nodes"], "m": m, "queue_size": q,
+                       "threshold": spec["threshold"], "max_iters": spec["max_iters"],
+                       "iterations": [r[1].iterations for r in res], "parallelism": f"replicas x{world}",
+                       "l2": "flushed before every step (256 MiB write); inputs resident in HBM"},
+            "triangle_gbs": tri_gbs,
+            "breakdown_ms": {"create": statistics.median(
+                r[2]["ms_csr"] + r[2]["ms_orient"] + r[2]["ms_triangles"] + r[2]["ms_vt"] + r[2]["ms_order"]
+                for r in res),
+                "triangles": statistics.median(r[2]["ms_triangles"] for r in res),
+                "init": statistics.median(r[1].ms_init for r in res),
+                "iterations": statistics.median(r[1].ms_iterations for r in res),
+                "eval_kernels": statistics.median(r[1].prof_move_ms for r in prof)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        if secondary:
+            line["secondary"] = secondary
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

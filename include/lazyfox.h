@@ -63,10 +63,19 @@ typedef struct lf_options {
     int32_t member_slots;    /* initial per-node membership capacity (0: default 4); grows as needed */
     int32_t warp_max_degree; /* 0: default; smaller values send more nodes to the block-wide
                                 kernels (tuning and tests) */
-    int32_t use_graphs;      /* 0: default (capture each iteration in a CUDA graph);
-                                -1: launch kernels directly */
-    int32_t profile;         /* 1: time every move-evaluation launch with CUDA events and
-                                count its algorithmic bytes (lf_run_stats.prof_*) */
+    int32_t use_graphs;      /* per-queue launch mode only: 0 (default) captures each
+                                iteration in a CUDA graph, -1 launches kernels directly */
+    int32_t profile;         /* 1: time every launch that processes queues with CUDA events
+                                and count its algorithmic bytes (lf_run_stats.prof_*) */
+    int32_t exhaustive_fp64; /* 1: evaluate every candidate gain in FP64 (no FP32 screen);
+                                the chosen actions are the same either way */
+    int32_t per_queue_launches; /* 0 (default): one persistent cooperative kernel per
+                                iteration runs every queue (evaluate, grid barrier, apply,
+                                grid barrier); 1: two kernel launches per queue */
+    int32_t barrier_timeout_ms; /* bound on one grid-barrier wait (0: 2000 ms); a wait that
+                                runs out ends the call with LF_ERR_TIMEOUT */
+    int32_t inject_barrier_stall; /* test hook: 1 makes one block of the persistent kernel
+                                skip its barriers, so that the bounded waits run out */
 } lf_options;
 
 /* Per-run statistics.  The history pointers are optional caller buffers with
@@ -86,11 +95,16 @@ typedef struct lf_run_stats {
     int64_t *joins_history;  /* join actions applied per iteration */
     int64_t *leaves_history; /* leave actions applied per iteration */
     int64_t num_launches;    /* kernels launched by the call */
-    int64_t prof_eval_launches; /* profile mode: move-evaluation launches timed */
-    double prof_eval_ms;     /* profile mode: their summed device time */
-    int64_t prof_eval_bytes; /* profile mode: their algorithmic bytes: per node 28 + 4|M(x)|,
-                                per neighbour y 8 + 4|M(y)|, 16 per distinct candidate
-                                community, 16 for the actions written */
+    int64_t prof_move_launches; /* profile mode: launches that process queues (the move
+                                evaluation kernel in per-queue mode, the persistent queue
+                                kernel otherwise) */
+    double prof_move_ms;     /* profile mode: their summed device time */
+    int64_t prof_move_bytes; /* profile mode: their algorithmic bytes.  Evaluation: per
+                                node 28 + 4|M(x)|, per neighbour y 8 + 4|M(y)|, 16 per
+                                distinct candidate community, 16 for the actions.  Apply
+                                (persistent kernel): 8 per node, and per moving node
+                                24 + 4|M(x)| + 12 per action, plus 16 per neighbour when
+                                the neighbour scan runs */
 } lf_run_stats;
 
 /* Device times of the phases of lf_graph_create. */

@@ -40,6 +40,7 @@ constexpr int SACC_CHUNKS = 68;   // 32-bit digits, bit 0 = 2^-1074
 // Device error bits (DevScalars::err).
 constexpr int32_t DERR_CAPACITY = 1;    // a membership row overflowed
 constexpr int32_t DERR_CHECK = 2;       // a consistency check failed
+constexpr int32_t DERR_TIMEOUT = 4;     // a bounded grid-barrier wait ran out
 
 // Community aggregate record: members, 2 x internal edges (sum of internal
 // degrees), sum of member degrees.  16 bytes: one vector load per candidate.
@@ -70,6 +71,8 @@ struct DevScalars {
     int32_t count32;
     int32_t max_id;
     int32_t neg_id;
+    unsigned bar_count;                     // grid barrier: arrivals
+    unsigned bar_gen;                       // grid barrier: generation
     int32_t pad;
 };
 
@@ -96,6 +99,10 @@ struct lf_graph {
     int32_t warp_max_degree = 0;
     int32_t use_graphs = 1;
     int32_t profile = 0;
+    int32_t screen = 1;                            // FP32 candidate screen in the move evaluation
+    int32_t per_queue = 0;                         // 1: kernel launches per queue instead of the persistent loop
+    int32_t barrier_timeout_ms = 2000;
+    int32_t inject_stall = 0;
     unsigned long long launches = 0;               // kernels launched (host count)
     std::vector<std::pair<void *, size_t>> live;   // outstanding allocations
 
@@ -197,10 +204,13 @@ __device__ __forceinline__ double wcchat_member(int64_t k, int64_t d, int64_t n,
 // (n copies).  The gain of a join or leave is the change of this score.
 __device__ __forceinline__ double community_score(int64_t n, int64_t m2, int64_t vol, double cc) {
     if (n < 2) return 0.0;
-    double nd = (double)n;
-    double din = __ddiv_rn((double)m2, nd);
-    double dt = __ddiv_rn((double)vol, nd);
-    double p = __ddiv_rn((double)m2, __dmul_rn(nd, __dsub_rn(nd, 1.0)));
+    // all three fit in 32 bits (n < 2^31, m2 and vol < 2^32): exact conversions
+    const double nd = __uint2double_rn((uint32_t)n);
+    const double md = __uint2double_rn((uint32_t)m2);
+    const double vd = __uint2double_rn((uint32_t)vol);
+    double din = __ddiv_rn(md, nd);
+    double dt = __ddiv_rn(vd, nd);
+    double p = __ddiv_rn(md, __dmul_rn(nd, __dsub_rn(nd, 1.0)));
     double ec = __dmul_rn(binom2(din), p);
     double ev = __dmul_rn(binom2(dt), cc);
     if (!(ev > 0.0)) return 0.0;

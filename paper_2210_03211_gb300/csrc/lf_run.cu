@@ -20,6 +20,7 @@ constexpr int EV_THREADS = EV_WARPS * 32;
 constexpr int HW = 512;              // hash slots of one warp
 constexpr int HB = EV_WARPS * HW;    // hash slots of a block (hub nodes)
 constexpr int AP_THREADS = 256;
+constexpr size_t EV_DYN_SMEM = (size_t)HB * 16;   // keys, counts, upper and lower screen bounds
 
 struct RunArgs {
     const int64_t *off;
@@ -38,8 +39,12 @@ struct RunArgs {
     Readback *rbd;
     double cc;
     int64_t nbatches;
+    int64_t nnodes;
     int32_t warp_max_deg;
     int32_t profile;   // count algorithmic bytes of the move evaluation
+    int32_t screen;    // 1: rule candidates out with the FP32 bound first
+    float cc32;        // cc rounded to float (screen)
+    float delta;       // relative error bound of the screen (see score32)
 };
 
 // ---------------------------------------------------------------------------
@@ -193,6 +198,173 @@ __device__ __forceinline__ void eval_candidate(const RunArgs &a, int32_t C, uint
     }
 }
 
+// The same mean-field score in closed form.  With din = m2/n, D = vol/n and
+// p = m2/(n(n-1)) the estimator collapses to
+//     S = m2^2 (m2 - n) / (cc (n-1) (vol - n) (n(n-1) + vol - m2)),
+// zero unless n >= 2, m2 > n (C(din,2) > 0) and vol > n (C(D,2) > 0).  Every
+// factor is a non-negative integer below 2^32, converted from 32 bits (the
+// 64-bit conversions are slow here); n(n-1) + vol - m2 is formed in float from
+// non-negative parts (three roundings, no cancellation).  In all at most 15
+// roundings: relative error < 20 x 2^-24.  It is only used to rule candidates
+// out: the gain that decides is always the FP64 one.
+__device__ __forceinline__ float score32(int64_t n, int64_t m2, int64_t vol, float cc32) {
+    if (n < 2 || m2 <= n || vol <= n) return 0.f;
+    const float a = __uint2float_rn((uint32_t)m2);
+    const float b = __uint2float_rn((uint32_t)(m2 - n));
+    const float c = __uint2float_rn((uint32_t)(n - 1));
+    const float e = __uint2float_rn((uint32_t)(vol - n));
+    const float f = __fadd_rn(__fmul_rn(__uint2float_rn((uint32_t)n), c), __uint2float_rn((uint32_t)(vol - m2)));
+    return __fdiv_rn(__fmul_rn(__fmul_rn(a, a), b), __fmul_rn(__fmul_rn(__fmul_rn(c, e), f), cc32));
+}
+
+// FP32 gain and an upper bound on |FP64 gain - FP32 gain|:
+// delta x (S_new + S_old) with delta covering the FP32 rounding, the FP64
+// rounding of the estimator (which grows with m2 and vol through C(din,2) and
+// D - din) and the two subtractions.
+__device__ __forceinline__ void screen_gain(const RunArgs &a, int32_t C, uint32_t v, int32_t d, float &g,
+                                           float &err) {
+    const bool own = (v & OWN_FLAG) != 0;
+    const int64_t k = (int64_t)(v & ~OWN_FLAG);
+    const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
+    const int64_t n = r.x, m2 = (uint32_t)r.y, vol = (uint32_t)r.z;
+    const float so = score32(n, m2, vol, a.cc32);
+    const float sn = own ? score32(n - 1, m2 - 2 * k, vol - d, a.cc32) : score32(n + 1, m2 + 2 * k, vol + d, a.cc32);
+    if (!(isfinite(sn) && isfinite(so))) {   // out of float range: keep the candidate, bound nothing
+        g = 0.f;
+        err = INFINITY;
+        return;
+    }
+    g = __fsub_rn(sn, so);
+    err = __fmul_rn(a.delta, __fadd_rn(sn, so));
+}
+
+__device__ __forceinline__ float warp_max_f(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(FULL, x, o));
+    return x;
+}
+
+// Pass 1 over table slots [lo, hi): the largest lower bound of a join gain
+// and of a leave gain (per lane); each slot's upper and lower bounds are
+// kept in ub[] and ub[HB + slot].
+__device__ __forceinline__ void screen_bounds(const RunArgs &a, const int32_t *keys, const uint32_t *vals,
+                                              float *ub, uint32_t lo, uint32_t hi, int32_t d, float &lbj,
+                                              float &lbl) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t s = lo + lane; s < hi; s += 32) {
+        const int32_t C = keys[s];
+        if (C == EMPTY_KEY) continue;
+        const uint32_t v = vals[s];
+        float g, e;
+        screen_gain(a, C, v, d, g, e);
+        const float lb = __fsub_rn(g, e);
+        ub[s] = __fadd_rn(g, e);
+        ub[HB + s] = lb;
+        if (v & OWN_FLAG) lbl = fmaxf(lbl, lb);
+        else lbj = fmaxf(lbj, lb);
+    }
+}
+
+// Survivors of the screen, per kind: their count and, when there is exactly
+// one, which.  A lone survivor whose lower bound is positive is the best
+// action of its kind without an FP64 evaluation: every other candidate's
+// FP64 gain is strictly below its own, and its own is positive.
+struct Survivors {
+    int cj, cl;
+    int32_t Cj, Cl;
+    uint32_t vj, vl;
+    float lbj, lbl;
+};
+
+__device__ __forceinline__ bool survives(float ub, uint32_t v, float lbj, float lbl) {
+    return ub > 0.f && ub >= ((v & OWN_FLAG) ? lbl : lbj);
+}
+
+__device__ void count_survivors(const int32_t *keys, const uint32_t *vals, const float *ubs, uint32_t lo,
+                                uint32_t hi, float lbj, float lbl, Survivors &sv) {
+    const int lane = threadIdx.x & 31;
+    sv = Survivors{0, 0, -1, -1, 0u, 0u, 0.f, 0.f};
+    for (uint32_t base = lo; base < hi; base += 32) {
+        const uint32_t s = base + lane;
+        bool sj = false, sl = false;
+        int32_t C = EMPTY_KEY;
+        uint32_t v = 0;
+        float lb = 0.f;
+        if (s < hi) {
+            C = keys[s];
+            if (C != EMPTY_KEY) {
+                v = vals[s];
+                if (survives(ubs[s], v, lbj, lbl)) {
+                    lb = ubs[HB + s];
+                    if (v & OWN_FLAG) sl = true; else sj = true;
+                }
+            }
+        }
+        const unsigned mj = __ballot_sync(FULL, sj), ml = __ballot_sync(FULL, sl);
+        if (mj) {
+            const int src = __ffs(mj) - 1;
+            const int32_t c1 = __shfl_sync(FULL, C, src);
+            const uint32_t v1 = __shfl_sync(FULL, v, src);
+            const float l1 = __shfl_sync(FULL, lb, src);
+            if (sv.cj == 0) { sv.Cj = c1; sv.vj = v1; sv.lbj = l1; }
+            sv.cj += __popc(mj);
+        }
+        if (ml) {
+            const int src = __ffs(ml) - 1;
+            const int32_t c1 = __shfl_sync(FULL, C, src);
+            const uint32_t v1 = __shfl_sync(FULL, v, src);
+            const float l1 = __shfl_sync(FULL, lb, src);
+            if (sv.cl == 0) { sv.Cl = c1; sv.vl = v1; sv.lbl = l1; }
+            sv.cl += __popc(ml);
+        }
+    }
+}
+
+// Pass 2 over table slots [lo, hi): candidates whose upper bound is positive
+// and not below the best lower bound of their kind may be the best action;
+// they are packed into the warp's buffer and evaluated in FP64 with full
+// lanes.  Every candidate whose FP64 gain could be maximal and positive
+// survives, so the choice equals an FP64 evaluation of all candidates.
+__device__ void eval_survivors(const RunArgs &a, const int32_t *keys, const uint32_t *vals, const float *ubs,
+                               uint32_t lo, uint32_t hi, int32_t d, float lbj, float lbl, bool do_j, bool do_l,
+                               int32_t *bkey, uint32_t *bval, Best &bj, Best &bl) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    int nbuf = 0;
+    for (uint32_t base = lo; base < hi; base += 32) {
+        const uint32_t s = base + lane;
+        bool surv = false;
+        int32_t C = EMPTY_KEY;
+        uint32_t v = 0;
+        if (s < hi) {
+            C = keys[s];
+            if (C != EMPTY_KEY) {
+                v = vals[s];
+                const bool kind_ok = (v & OWN_FLAG) ? do_l : do_j;
+                if (!kind_ok) surv = false;
+                else if (a.screen) surv = survives(ubs[s], v, lbj, lbl);
+                else surv = true;
+            }
+        }
+        const unsigned mask = __ballot_sync(FULL, surv);
+        const int cnt = __popc(mask);
+        if (nbuf + cnt > 32) {
+            if (lane < nbuf) eval_candidate(a, bkey[lane], bval[lane], d, bj, bl);
+            __syncwarp();
+            nbuf = 0;
+        }
+        if (surv) {
+            const int p = nbuf + __popc(mask & lt);
+            bkey[p] = C;
+            bval[p] = v;
+        }
+        nbuf += cnt;
+        __syncwarp();
+    }
+    if (lane < nbuf) eval_candidate(a, bkey[lane], bval[lane], d, bj, bl);
+    __syncwarp();
+}
+
 // Saturating "how many actions of this queue target C" counter, tagged with
 // the queue's serial number so that it never needs clearing.
 __device__ __forceinline__ void stamp_add(unsigned long long *w, unsigned long long serial) {
@@ -226,7 +398,7 @@ __device__ __forceinline__ void write_action(const RunArgs &a, int i, const Best
 // __match_any_sync, so each id costs one atomic per step.  `bound` (>= the
 // number of distinct ids) keeps the table at most half full.
 __device__ void eval_warp(const RunArgs &a, int i, int32_t x, int32_t d, int64_t bound, int32_t *keys,
-                          uint32_t *vals, unsigned long long serial) {
+                          uint32_t *vals, float *ubs, int32_t *bkey, uint32_t *bval, unsigned long long serial) {
     const int lane = threadIdx.x & 31;
     uint32_t H = 32;
     while ((int64_t)H < 2 * bound) H <<= 1;
@@ -236,9 +408,9 @@ __device__ void eval_warp(const RunArgs &a, int i, int32_t x, int32_t d, int64_t
         vals[s] = 0u;
     }
     __syncwarp();
-    const int32_t cx = a.nmem[x];
+    const int32_t cx = __ldcg(&a.nmem[x]);
     const int32_t *rowx = a.mem + (int64_t)x * a.K;
-    for (int j = lane; j < cx; j += 32) ht_insert(keys, vals, hm, rowx[j], 0u, true);
+    for (int j = lane; j < cx; j += 32) ht_insert(keys, vals, hm, __ldcg(&rowx[j]), 0u, true);
     __syncwarp();
     const int64_t beg = a.off[x], end = a.off[x + 1];
     unsigned long long pb = 0;
@@ -247,26 +419,40 @@ __device__ void eval_warp(const RunArgs &a, int i, int32_t x, int32_t d, int64_t
         int32_t y = 0, cy = 0;
         if (p < end) {
             y = a.adj[p];
-            cy = a.nmem[y];
+            cy = __ldcg(&a.nmem[y]);
             pb += 8ull + 4ull * (unsigned long long)cy;
         }
         const int32_t cmax = __reduce_max_sync(FULL, cy);
         const int32_t *rowy = a.mem + (int64_t)y * a.K;
         for (int s = 0; s < cmax; ++s) {
-            int32_t C = s < cy ? rowy[s] : -2 - lane;
+            int32_t C = s < cy ? __ldcg(&rowy[s]) : -2 - lane;
             unsigned mask = __match_any_sync(FULL, C);
             if (C >= 0 && lane == __ffs(mask) - 1) ht_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false);
         }
     }
     __syncwarp();
     Best bj{0.0, -1, 0}, bl{0.0, -1, 0};
-    for (uint32_t s = lane; s < H; s += 32) {
-        int32_t C = keys[s];
-        if (C != EMPTY_KEY) {
-            eval_candidate(a, C, vals[s], d, bj, bl);
-            pb += 16ull;
+    float lbj = -INFINITY, lbl = -INFINITY;
+    bool do_j = true, do_l = true;
+    if (a.screen) {
+        screen_bounds(a, keys, vals, ubs, 0, H, d, lbj, lbl);
+        lbj = warp_max_f(lbj);
+        lbl = warp_max_f(lbl);
+        __syncwarp();
+        Survivors sv;
+        count_survivors(keys, vals, ubs, 0, H, lbj, lbl, sv);
+        do_j = sv.cj > 1 || (sv.cj == 1 && !(sv.lbj > 0.f));
+        do_l = sv.cl > 1 || (sv.cl == 1 && !(sv.lbl > 0.f));
+        if (lane == 0) {
+            if (sv.cj == 1 && !do_j) bj = Best{INFINITY, sv.Cj, (int32_t)(sv.vj & ~OWN_FLAG)};
+            if (sv.cl == 1 && !do_l) bl = Best{INFINITY, sv.Cl, (int32_t)(sv.vl & ~OWN_FLAG)};
         }
+        if (sv.cj == 0) do_j = false;
+        if (sv.cl == 0) do_l = false;
     }
+    if (do_j || do_l) eval_survivors(a, keys, vals, ubs, 0, H, d, lbj, lbl, do_j, do_l, bkey, bval, bj, bl);
+    if (a.profile)
+        for (uint32_t s = lane; s < H; s += 32) pb += keys[s] != EMPTY_KEY ? 16ull : 0ull;
     warp_best(bj);
     warp_best(bl);
     if (a.profile) {
@@ -285,6 +471,7 @@ __device__ __forceinline__ uint32_t part_of(int32_t C, int P) {
 struct BlockScratch {
     double gj[EV_WARPS], gl[EV_WARPS];
     int32_t cj[EV_WARPS], cl[EV_WARPS], kj[EV_WARPS], kl[EV_WARPS];
+    float lbj[EV_WARPS], lbl[EV_WARPS];
     int overflow;
 };
 
@@ -292,10 +479,10 @@ struct BlockScratch {
 // hash and each part is counted in the block's table in its own pass; if a
 // pass overflows the table, P doubles and the evaluation restarts.
 __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, int32_t *keys, uint32_t *vals,
-                           BlockScratch &bs, unsigned long long serial) {
+                           float *ubs, int32_t *bkey, uint32_t *bval, BlockScratch &bs, unsigned long long serial) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int32_t d = a.deg[x];
-    const int32_t cx = a.nmem[x];
+    const int32_t cx = __ldcg(&a.nmem[x]);
     const int32_t *rowx = a.mem + (int64_t)x * a.K;
     const int64_t beg = a.off[x], end = a.off[x + 1];
     int P = bound <= HB / 2 ? 1 : (int)((bound + HB / 4 - 1) / (HB / 4));
@@ -305,6 +492,8 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
         bj = Best{0.0, -1, 0};
         bl = Best{0.0, -1, 0};
         pb = 0;
+        // running best lower bounds over the parts seen so far
+        float lbj = -INFINITY, lbl = -INFINITY;
         uint32_t H = HB;
         if (P == 1) {
             H = 32;
@@ -320,7 +509,7 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
             if (threadIdx.x == 0) bs.overflow = 0;
             __syncthreads();
             for (int j = threadIdx.x; j < cx; j += EV_THREADS) {
-                int32_t C = rowx[j];
+                int32_t C = __ldcg(&rowx[j]);
                 if (P == 1 || part_of(C, P) == (uint32_t)part)
                     if (!ht_insert(keys, vals, hm, C, 0u, true)) bs.overflow = 1;
             }
@@ -330,13 +519,13 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
                 int32_t y = 0, cy = 0;
                 if (p < end) {
                     y = a.adj[p];
-                    cy = a.nmem[y];
+                    cy = __ldcg(&a.nmem[y]);
                     if (part == 0) pb += 8ull + 4ull * (unsigned long long)cy;
                 }
                 const int32_t cmax = __reduce_max_sync(FULL, cy);
                 const int32_t *rowy = a.mem + (int64_t)y * a.K;
                 for (int s = 0; s < cmax; ++s) {
-                    int32_t C = s < cy ? rowy[s] : -1;
+                    int32_t C = s < cy ? __ldcg(&rowy[s]) : -1;
                     if (C >= 0 && P > 1 && part_of(C, P) != (uint32_t)part) C = -1;
                     if (C < 0) C = -2 - lane;
                     unsigned mask = __match_any_sync(FULL, C);
@@ -350,13 +539,27 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
                 __syncthreads();
                 break;
             }
-            for (uint32_t s = threadIdx.x; s < H; s += EV_THREADS) {
-                int32_t C = keys[s];
-                if (C != EMPTY_KEY) {
-                    eval_candidate(a, C, vals[s], d, bj, bl);
-                    pb += 16ull;
+            // each warp owns a contiguous slice of the table
+            const uint32_t slice = (H + EV_WARPS - 1) / EV_WARPS;
+            const uint32_t lo = min(H, (uint32_t)w * slice), hi = min(H, lo + slice);
+            if (a.screen) {
+                float wj = lbj, wl = lbl;
+                screen_bounds(a, keys, vals, ubs, lo, hi, d, wj, wl);
+                wj = warp_max_f(wj);
+                wl = warp_max_f(wl);
+                if (lane == 0) {
+                    bs.lbj[w] = wj;
+                    bs.lbl[w] = wl;
+                }
+                __syncthreads();
+                for (int ww = 0; ww < EV_WARPS; ++ww) {
+                    lbj = fmaxf(lbj, bs.lbj[ww]);
+                    lbl = fmaxf(lbl, bs.lbl[ww]);
                 }
             }
+            eval_survivors(a, keys, vals, ubs, lo, hi, d, lbj, lbl, true, true, bkey, bval, bj, bl);
+            if (a.profile)
+                for (uint32_t s = lo + lane; s < hi; s += 32) pb += keys[s] != EMPTY_KEY ? 16ull : 0ull;
             __syncthreads();
         }
         if (!overflow) break;
@@ -389,36 +592,55 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(EV_THREADS) k_eval(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx) {
-    __shared__ int32_t s_keys[HB];
-    __shared__ uint32_t s_vals[HB];
-    __shared__ int32_t s_hub[EV_WARPS];
-    __shared__ int s_nhub;
-    __shared__ BlockScratch bs;
+struct EvalShared {
+    int32_t hub[EV_WARPS];
+    int nhub;
+    BlockScratch bs;
+    int32_t bkey[EV_WARPS][32];
+    uint32_t bval[EV_WARPS][32];
+};
+
+// One block evaluates the queue's nodes base .. base+EV_WARPS-1: a warp per
+// node, then the block together for each node too large for a warp's table.
+__device__ void eval_group(const RunArgs &a, int64_t bstart, int32_t blen, int base, int32_t kb,
+                           unsigned long long serial, int32_t *s_keys, uint32_t *s_vals, float *s_ub,
+                           EvalShared &es) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_nhub = 0;
+    if (threadIdx.x == 0) es.nhub = 0;
     __syncthreads();
-    const int32_t kb = __ldcg(&a.ds->kb);
-    const unsigned long long serial = (unsigned long long)__ldcg(&a.ds->iter) * (unsigned long long)a.nbatches +
-                                      (unsigned long long)bidx + 1ull;
-    const int i = blockIdx.x * EV_WARPS + w;
+    const int i = base + w;
     if (i < blen) {
         const int32_t x = a.order[bstart + i];
         const int32_t d = a.deg[x];
         const int64_t bound = (int64_t)(d + 1) * kb;
         if (d <= a.warp_max_deg && bound <= HW / 2) {
-            eval_warp(a, i, x, d, bound, s_keys + w * HW, s_vals + w * HW, serial);
+            eval_warp(a, i, x, d, bound, s_keys + w * HW, s_vals + w * HW, s_ub + w * HW, es.bkey[w], es.bval[w],
+                      serial);
         } else if (lane == 0) {
-            s_hub[atomicAdd(&s_nhub, 1)] = i;
+            es.hub[atomicAdd(&es.nhub, 1)] = i;
         }
     }
     __syncthreads();
-    const int nh = s_nhub;
+    const int nh = es.nhub;
     for (int h = 0; h < nh; ++h) {
-        const int ih = s_hub[h];
+        const int ih = es.hub[h];
         const int32_t x = a.order[bstart + ih];
-        eval_block(a, ih, x, (int64_t)(a.deg[x] + 1) * kb, s_keys, s_vals, bs, serial);
+        eval_block(a, ih, x, (int64_t)(a.deg[x] + 1) * kb, s_keys, s_vals, s_ub, es.bkey[w], es.bval[w], es.bs,
+                   serial);
     }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long queue_serial(const RunArgs &a, int64_t bidx) {
+    return (unsigned long long)__ldcg(&a.ds->iter) * (unsigned long long)a.nbatches + (unsigned long long)bidx + 1ull;
+}
+
+__global__ void __launch_bounds__(EV_THREADS) k_eval(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx) {
+    extern __shared__ int32_t ev_dyn[];   // HB keys, HB counts, HB screen bounds
+    __shared__ EvalShared es;
+    const int32_t kb = __ldcg(&a.ds->kb);
+    eval_group(a, bstart, blen, blockIdx.x * EV_WARPS, kb, queue_serial(a, bidx), ev_dyn,
+               reinterpret_cast<uint32_t *>(ev_dyn + HB), reinterpret_cast<float *>(ev_dyn + 2 * HB), es);
 }
 
 // ---------------------------------------------------------------------------
@@ -429,84 +651,169 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval(RunArgs a, int64_t bstart, 
 // exact change of 2m_C; the neighbour scan is needed only when another action
 // of the same queue targets C.  Integer atomics: order-independent.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(AP_THREADS) k_apply(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx) {
-    __shared__ unsigned long long s_j, s_l;
+__device__ void apply_node(const RunArgs &a, int64_t bstart, int32_t blen, int64_t i, unsigned long long serial,
+                           unsigned long long &nj, unsigned long long &nl) {
     const int lane = threadIdx.x & 31;
+    const int32_t j = __ldcg(&a.act[i]), l = __ldcg(&a.act[a.qcap + i]);
+    if (j < 0 && l < 0) {
+        if (a.profile && lane == 0) atomicAdd(&a.ds->prof_bytes, 8ull);
+        return;
+    }
+    const int32_t x = a.order[bstart + i];
+    const bool need_j = j >= 0 && stamp_multi(a.stamp + j, serial);
+    const bool need_l = l >= 0 && stamp_multi(a.stamp + l, serial);
+    int jj = 0, jl = 0, ll = 0;
+    if (need_j || need_l) {
+        for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
+            const int32_t y = a.adj[p];
+            const int64_t py = a.pos[y];
+            if (py >= bstart && py < bstart + blen) {
+                const int64_t iy = py - bstart;
+                const int32_t aj = __ldcg(&a.act[iy]), al = __ldcg(&a.act[a.qcap + iy]);
+                if (need_j) {
+                    jj += aj == j;
+                    jl += al == j;
+                }
+                if (need_l) ll += al == l;
+            }
+        }
+        jj = __reduce_add_sync(FULL, jj);
+        jl = __reduce_add_sync(FULL, jl);
+        ll = __reduce_add_sync(FULL, ll);
+    }
+    if (lane == 0) {
+        const int32_t d = a.deg[x];
+        int32_t *row = a.mem + (int64_t)x * a.K;
+        int32_t c = __ldcg(&a.nmem[x]);
+        if (l >= 0) {
+            const int32_t kl = __ldcg(&a.act[3 * a.qcap + i]);
+            atomicAdd(&a.comm[l].n, -1);
+            atomicAdd(&a.comm[l].vol, (uint32_t)(-d));
+            atomicAdd(&a.comm[l].m2, (uint32_t)(-2 * kl + ll));
+            int32_t o = 0;
+            for (int32_t s = 0; s < c; ++s) {
+                const int32_t v = __ldcg(&row[s]);
+                if (v != l) row[o++] = v;
+            }
+            c = o;
+            ++nl;
+        }
+        if (j >= 0) {
+            const int32_t kj = __ldcg(&a.act[2 * a.qcap + i]);
+            atomicAdd(&a.comm[j].n, 1);
+            atomicAdd(&a.comm[j].vol, (uint32_t)d);
+            atomicAdd(&a.comm[j].m2, (uint32_t)(2 * kj + jj - 2 * jl));
+            if (c >= a.K) {
+                atomicOr(&a.ds->err, DERR_CAPACITY);
+            } else {
+                int32_t s = c;
+                while (s > 0) {
+                    const int32_t v = __ldcg(&row[s - 1]);
+                    if (v <= j) break;
+                    row[s] = v;
+                    --s;
+                }
+                row[s] = j;
+                ++c;
+            }
+            ++nj;
+        }
+        a.nmem[x] = c;
+        if (a.profile) {
+            const unsigned long long nb_scan = (need_j || need_l) ? 16ull * (unsigned long long)(a.off[x + 1] - a.off[x]) : 0ull;
+            atomicAdd(&a.ds->prof_bytes, 24ull + 4ull * (unsigned long long)c + 12ull * ((j >= 0) + (l >= 0)) + nb_scan);
+        }
+    }
+}
+
+__device__ __forceinline__ void flush_counts(const RunArgs &a, unsigned long long nj, unsigned long long nl) {
+    __shared__ unsigned long long s_j, s_l;
     if (threadIdx.x == 0) {
         s_j = 0;
         s_l = 0;
     }
     __syncthreads();
-    const unsigned long long serial = (unsigned long long)__ldcg(&a.ds->iter) * (unsigned long long)a.nbatches +
-                                      (unsigned long long)bidx + 1ull;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i < blen) {
-        const int32_t j = a.act[i], l = a.act[a.qcap + i];
-        if (j >= 0 || l >= 0) {
-            const int32_t x = a.order[bstart + i];
-            const bool nj = j >= 0 && stamp_multi(a.stamp + j, serial);
-            const bool nl = l >= 0 && stamp_multi(a.stamp + l, serial);
-            int jj = 0, jl = 0, ll = 0;
-            if (nj || nl) {
-                for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
-                    const int32_t y = a.adj[p];
-                    const int64_t py = a.pos[y];
-                    if (py >= bstart && py < bstart + blen) {
-                        const int64_t iy = py - bstart;
-                        const int32_t aj = a.act[iy], al = a.act[a.qcap + iy];
-                        if (nj) {
-                            jj += aj == j;
-                            jl += al == j;
-                        }
-                        if (nl) ll += al == l;
-                    }
-                }
-                jj = __reduce_add_sync(FULL, jj);
-                jl = __reduce_add_sync(FULL, jl);
-                ll = __reduce_add_sync(FULL, ll);
-            }
-            if (lane == 0) {
-                const int32_t d = a.deg[x];
-                int32_t *row = a.mem + (int64_t)x * a.K;
-                int32_t c = a.nmem[x];
-                if (l >= 0) {
-                    const int32_t kl = a.act[3 * a.qcap + i];
-                    atomicAdd(&a.comm[l].n, -1);
-                    atomicAdd(&a.comm[l].vol, (uint32_t)(-d));
-                    atomicAdd(&a.comm[l].m2, (uint32_t)(-2 * kl + ll));
-                    int32_t o = 0;
-                    for (int32_t s = 0; s < c; ++s)
-                        if (row[s] != l) row[o++] = row[s];
-                    c = o;
-                    atomicAdd(&s_l, 1ull);
-                }
-                if (j >= 0) {
-                    const int32_t kj = a.act[2 * a.qcap + i];
-                    atomicAdd(&a.comm[j].n, 1);
-                    atomicAdd(&a.comm[j].vol, (uint32_t)d);
-                    atomicAdd(&a.comm[j].m2, (uint32_t)(2 * kj + jj - 2 * jl));
-                    if (c >= a.K) {
-                        atomicOr(&a.ds->err, DERR_CAPACITY);
-                    } else {
-                        int32_t s = c;
-                        while (s > 0 && row[s - 1] > j) {
-                            row[s] = row[s - 1];
-                            --s;
-                        }
-                        row[s] = j;
-                        ++c;
-                    }
-                    atomicAdd(&s_j, 1ull);
-                }
-                a.nmem[x] = c;
-            }
-        }
-    }
+    if (nj) atomicAdd(&s_j, nj);
+    if (nl) atomicAdd(&s_l, nl);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (s_j) atomicAdd(&a.ds->joins, s_j);
         if (s_l) atomicAdd(&a.ds->leaves, s_l);
     }
+}
+
+__global__ void __launch_bounds__(AP_THREADS) k_apply(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx) {
+    const unsigned long long serial = queue_serial(a, bidx);
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    unsigned long long nj = 0, nl = 0;
+    if (i < blen) apply_node(a, bstart, blen, i, serial, nj, nl);
+    flush_counts(a, nj, nl);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent queue loop: one cooperative launch runs queues first ..
+// first+count-1 of an iteration: evaluate (blocks take groups of EV_WARPS
+// nodes), grid barrier, apply (warps take nodes), grid barrier.  Every
+// barrier wait is bounded; a wait that runs out sets DERR_TIMEOUT and the
+// kernel returns (the other blocks then run out at their next wait).
+// ---------------------------------------------------------------------------
+__device__ bool grid_sync(DevScalars *ds, unsigned nblocks, long long spin_limit, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *genp = &ds->bar_gen;
+        const unsigned g = *genp;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ds->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&ds->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ds->bar_gen, 1u);
+        } else {
+            long long it = 0;
+            while (*genp == g) {
+                if (++it > spin_limit) {
+                    atomicOr(&ds->err, DERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        if (*((volatile int *)&ds->err) & DERR_TIMEOUT) ok = 0;
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(EV_THREADS, 2) k_iterate(RunArgs a, int64_t q, int64_t first, int64_t count,
+                                                        long long spin_limit, int inject_stall) {
+    extern __shared__ int32_t ev_dyn[];
+    __shared__ EvalShared es;
+    __shared__ int s_ok;
+    int32_t *s_keys = ev_dyn;
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(ev_dyn + HB);
+    float *s_ub = reinterpret_cast<float *>(ev_dyn + 2 * HB);
+    const int32_t kb = __ldcg(&a.ds->kb);
+    const int64_t n = a.nnodes;
+    const unsigned nblocks = gridDim.x;
+    const int64_t warps = (int64_t)gridDim.x * EV_WARPS;
+    const int64_t gw = (int64_t)blockIdx.x * EV_WARPS + (threadIdx.x >> 5);
+    unsigned long long nj = 0, nl = 0;
+    if (inject_stall && blockIdx.x == 0) return;   // test hook: a block that never arrives
+    for (int64_t b = first; b < first + count; ++b) {
+        const int64_t bstart = b * q;
+        const int32_t blen = (int32_t)min(q, n - bstart);
+        const unsigned long long serial = queue_serial(a, b);
+        for (int64_t base = (int64_t)blockIdx.x * EV_WARPS; base < blen; base += warps)
+            eval_group(a, bstart, blen, (int)base, kb, serial, s_keys, s_vals, s_ub, es);
+        if (!grid_sync(a.ds, nblocks, spin_limit, &s_ok)) return;
+        for (int64_t i = gw; i < blen; i += warps) apply_node(a, bstart, blen, i, serial, nj, nl);
+        if (!grid_sync(a.ds, nblocks, spin_limit, &s_ok)) return;
+    }
+    flush_counts(a, nj, nl);
 }
 
 // ---------------------------------------------------------------------------
@@ -566,30 +873,72 @@ __device__ __forceinline__ bool row_has(const int32_t *row, int32_t c, int32_t C
 }
 
 // WCC-hat(P) = sum over memberships (x, C) of WCC-hat(x, C), with
-// deg(x, C) counted over x's neighbours; exact sum, so the total does not
-// depend on the order of the additions.
-__global__ void k_total(RunArgs a, int64_t n) {
+// deg(x, C) counted over x's neighbours in one pass (each neighbour's row is
+// looked up in x's own row); exact sum, so the total does not depend on the
+// order of the additions.
+constexpr int TOT_WARPS = 8;
+constexpr int TOT_ROW = 64;   // own rows up to this length are counted in one pass
+
+__global__ void __launch_bounds__(TOT_WARPS * 32) k_total(RunArgs a, int64_t n) {
     __shared__ unsigned long long acc[SACC_CHUNKS];
+    __shared__ int32_t s_row[TOT_WARPS][TOT_ROW];
+    __shared__ int32_t s_cnt[TOT_WARPS][TOT_ROW];
     for (int s = threadIdx.x; s < SACC_CHUNKS; s += blockDim.x) acc[s] = 0ull;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t *row_s = s_row[w], *cnt_s = s_cnt[w];
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
         const int32_t c = a.nmem[x];
         if (c == 0) continue;
         const int32_t d = a.deg[x];
         const int32_t *row = a.mem + x * a.K;
-        for (int32_t s = 0; s < c; ++s) {
-            const int32_t C = row[s];
-            int cnt = 0;
+        if (c <= TOT_ROW) {
+            for (int j = lane; j < c; j += 32) {
+                row_s[j] = row[j];
+                cnt_s[j] = 0;
+            }
+            __syncwarp();
+            const int32_t lo = row_s[0], hi = row_s[c - 1];
             for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
                 const int32_t y = a.adj[p];
-                cnt += row_has(a.mem + (int64_t)y * a.K, a.nmem[y], C);
+                const int32_t cy = a.nmem[y];
+                const int32_t *ry = a.mem + (int64_t)y * a.K;
+                for (int32_t s = 0; s < cy; ++s) {
+                    const int32_t C = ry[s];
+                    if (C < lo) continue;
+                    if (C > hi) break;
+                    int l = 0, h = c - 1;   // rows are ascending
+                    while (l <= h) {
+                        const int mid = (l + h) >> 1;
+                        const int32_t v = row_s[mid];
+                        if (v == C) {
+                            atomicAdd(&cnt_s[mid], 1);
+                            break;
+                        }
+                        if (v < C) l = mid + 1; else h = mid - 1;
+                    }
+                }
             }
-            cnt = __reduce_add_sync(FULL, cnt);
-            if (lane == 0) {
-                const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
-                sacc_add(acc, wcchat_member(cnt, d, r.x, (uint32_t)r.y, a.cc));
+            __syncwarp();
+            for (int j = lane; j < c; j += 32) {
+                const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[row_s[j]]));
+                sacc_add(acc, wcchat_member(cnt_s[j], d, r.x, (uint32_t)r.y, a.cc));
+            }
+            __syncwarp();
+        } else {
+            for (int32_t s = 0; s < c; ++s) {
+                const int32_t C = row[s];
+                int cnt = 0;
+                for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
+                    const int32_t y = a.adj[p];
+                    cnt += row_has(a.mem + (int64_t)y * a.K, a.nmem[y], C);
+                }
+                cnt = __reduce_add_sync(FULL, cnt);
+                if (lane == 0) {
+                    const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
+                    sacc_add(acc, wcchat_member(cnt, d, r.x, (uint32_t)r.y, a.cc));
+                }
             }
         }
     }
@@ -644,8 +993,16 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.rbd = rbd;
     a.cc = g->cc;
     a.nbatches = 0;
+    a.nnodes = g->n;
     a.warp_max_deg = g->warp_max_degree > 0 ? g->warp_max_degree : 0x7fffffff;
     a.profile = g->profile;
+    // FP32 screen: cc must be a normal float with room to spare; delta bounds
+    // 15 FP32 roundings (20 ulp) and the FP32 subtraction, the FP64 estimator's error u (m2 + 3 vol +
+    // 17) with m2, vol <= 2m, the two gain subtractions, and a 2% margin.
+    a.screen = (g->cc >= 1e-30 && g->screen) ? 1 : 0;
+    a.cc32 = (float)g->cc;
+    const double u64 = 1.1102230246251565e-16, u32 = 5.960464477539063e-08;
+    a.delta = (float)(1.02 * (21.0 * u32 + u64 * (200.0 + 8.0 * (double)g->m) + 2.0 * u64) + 1e-9);
     return a;
 }
 
@@ -654,14 +1011,23 @@ Readback *device_readback(lf_graph *g) {
     return reinterpret_cast<Readback *>(g->ds + 1);
 }
 
-void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int64_t count) {
+// Timing events: inside a stream capture they must be external event nodes,
+// otherwise the capture keeps only the ordering and records nothing.
+void record_event(lf_graph *g, cudaEvent_t e, bool capturing) {
+    if (capturing) LF_CUDA(cudaEventRecordWithFlags(e, g->stream, cudaEventRecordExternal));
+    else LF_CUDA(cudaEventRecord(e, g->stream));
+}
+
+void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int64_t count,
+                    bool capturing = false) {
+
     const bool prof = g->profile && (int64_t)g->prof_ev.size() >= 2 * (first + count);
     for (int64_t b = first; b < first + count; ++b) {
         const int64_t bstart = b * q;
         const int32_t blen = (int32_t)std::min<int64_t>(q, g->n - bstart);
-        if (prof) LF_CUDA(cudaEventRecord(g->prof_ev[2 * b], g->stream));
-        k_eval<<<(unsigned)((blen + EV_WARPS - 1) / EV_WARPS), EV_THREADS, 0, g->stream>>>(a, bstart, blen, b); ++g->launches;
-        if (prof) LF_CUDA(cudaEventRecord(g->prof_ev[2 * b + 1], g->stream));
+        if (prof) record_event(g, g->prof_ev[2 * b], capturing);
+        k_eval<<<(unsigned)((blen + EV_WARPS - 1) / EV_WARPS), EV_THREADS, EV_DYN_SMEM, g->stream>>>(a, bstart, blen, b); ++g->launches;
+        if (prof) record_event(g, g->prof_ev[2 * b + 1], capturing);
         k_apply<<<grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30), AP_THREADS, 0, g->stream>>>(a, bstart, blen, b); ++g->launches;
     }
     LF_LAUNCHED();
@@ -670,7 +1036,7 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
 void launch_iteration_end(lf_graph *g, const RunArgs &a) {
     const int64_t n = g->n;
     k_prune<<<grid_for(n + g->ncomm, 256, 1 << 16), 256, 0, g->stream>>>(a, n, g->ncomm); ++g->launches;
-    k_total<<<grid_for(n * 32, 256, 1 << 16), 256, 0, g->stream>>>(a, n); ++g->launches;
+    k_total<<<grid_for(n * 32, TOT_WARPS * 32, 1 << 16), TOT_WARPS * 32, 0, g->stream>>>(a, n); ++g->launches;
     k_finalize<<<1, 32, 0, g->stream>>>(g->ds, device_readback(g), 1); ++g->launches;
     LF_LAUNCHED();
     LF_CUDA(cudaMemcpyAsync(g->rb, device_readback(g), sizeof(Readback), cudaMemcpyDeviceToHost, g->stream));
@@ -719,6 +1085,33 @@ double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
     return (double)t;
 }
 
+// Blocks of the persistent queue kernel that can be resident at once.
+int persistent_grid_max(lf_graph *g) {
+    int dev = 0, sms = 0, per_sm = 0;
+    LF_CUDA(cudaGetDevice(&dev));
+    LF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LF_CUDA(cudaFuncSetAttribute(k_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate, EV_THREADS, EV_DYN_SMEM));
+    (void)g;
+    return std::max(1, per_sm) * std::max(1, sms);
+}
+
+// One cooperative launch runs queues first .. first+count-1.
+void launch_persistent(lf_graph *g, RunArgs a, int64_t q, int64_t first, int64_t count, int grid_max,
+                       cudaEvent_t e0, cudaEvent_t e1) {
+    if (count <= 0) return;
+    const int64_t want = (q + EV_WARPS - 1) / EV_WARPS;
+    unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, grid_max));
+    long long spin = (long long)g->barrier_timeout_ms * 10000ll;   // ~100 ns per wait step
+    int inject = g->inject_stall;
+    void *args[] = {&a, &q, &first, &count, &spin, &inject};
+    if (e0) LF_CUDA(cudaEventRecord(e0, g->stream));
+    LF_CUDA(cudaLaunchCooperativeKernel((const void *)k_iterate, dim3(grid), dim3(EV_THREADS), args, EV_DYN_SMEM,
+                                        g->stream));
+    ++g->launches;
+    if (e1) LF_CUDA(cudaEventRecord(e1, g->stream));
+}
+
 }  // namespace
 
 void free_run_state(lf_graph *g) {
@@ -746,6 +1139,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     const int64_t n = g->n;
     const int64_t q = std::max<int64_t>(1, std::min<int64_t>(q_in, std::max<int64_t>(n, 1)));
     ensure_capacity(g, q);
+    LF_CUDA(cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
     cudaEvent_t ev[3];
     for (auto &e : ev) LF_CUDA(cudaEventCreate(&e));
     struct EvGuard {
@@ -766,12 +1160,13 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         const size_t o = offsetof(DevScalars, joins);
         LF_CUDA(cudaMemcpyAsync(reinterpret_cast<char *>(g->ds) + o, reinterpret_cast<char *>(&z) + o,
                                 offsetof(DevScalars, max_id) - o, cudaMemcpyHostToDevice, st));
+        LF_CUDA(cudaMemsetAsync(&g->ds->bar_count, 0, sizeof(unsigned), st));
         LF_CUDA(cudaStreamSynchronize(st));
     }
     RunArgs a = make_args(g, device_readback(g));
     const unsigned long long launches0 = g->launches;
     const int64_t nb_all = n > 0 ? (n + q - 1) / q : 0;
-    if (g->profile && (int64_t)g->prof_ev.size() < 2 * nb_all) {
+    if (g->profile && g->per_queue && (int64_t)g->prof_ev.size() < 2 * nb_all) {
         drop_graph(g);   // a captured graph would not record the new events
         while ((int64_t)g->prof_ev.size() < 2 * nb_all) {
             cudaEvent_t e;
@@ -817,7 +1212,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         dfree(g, state);
     }
     g->ncomm = k0;
-    k_total<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(a, n); ++g->launches;
+    k_total<<<grid_for(n * 32, TOT_WARPS * 32, 1 << 16), TOT_WARPS * 32, 0, st>>>(a, n); ++g->launches;
     k_finalize<<<1, 32, 0, st>>>(g->ds, device_readback(g), 0); ++g->launches;
     LF_LAUNCHED();
     LF_CUDA(cudaMemcpyAsync(g->rb, device_readback(g), sizeof(Readback), cudaMemcpyDeviceToHost, st));
@@ -828,6 +1223,18 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     g->ran = true;
 
     const int64_t nb = n > 0 ? (n + q - 1) / q : 0;
+    const bool persistent = !g->per_queue;
+    const int grid_max = persistent ? persistent_grid_max(g) : 0;
+    cudaEvent_t pev[2] = {nullptr, nullptr};
+    if (persistent && g->profile)
+        for (auto &e : pev) LF_CUDA(cudaEventCreate(&e));
+    struct PevGuard {
+        cudaEvent_t *e;
+        ~PevGuard() {
+            for (int i = 0; i < 2; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } pg{pev};
     int32_t iters = 0, converged = 0;
     int64_t batches = 0;
     double prev = T0;
@@ -838,19 +1245,26 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         a.nbatches = nb;
         const bool partial = max_batches >= 0 && batches + nb > max_batches;
         if (partial) {
-            launch_batches(g, a, q, 0, max_batches - batches);
+            if (persistent) launch_persistent(g, a, q, 0, max_batches - batches, grid_max, nullptr, nullptr);
+            else launch_batches(g, a, q, 0, max_batches - batches);
             batches = max_batches;
             LF_CUDA(cudaStreamSynchronize(st));
+            int32_t err = 0;
+            LF_CUDA(cudaMemcpy(&err, &g->ds->err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+            if (err & DERR_TIMEOUT) fail(LF_ERR_TIMEOUT, "a grid-barrier wait ran out (limit %d ms)", g->barrier_timeout_ms);
             break;
         }
-        if (g->use_graphs > 0 && max_batches < 0) {
+        if (persistent) {
+            launch_persistent(g, a, q, 0, nb, grid_max, pev[0], pev[1]);
+            launch_iteration_end(g, a);
+        } else if (g->use_graphs > 0 && max_batches < 0) {
             if (!g->iter_exec || g->graph_q != q || g->graph_K != g->K) {
                 drop_graph(g);
                 cudaGraph_t graph;
                 const unsigned long long before = g->launches;
                 LF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
                 try {
-                    launch_batches(g, a, q, 0, nb);
+                    launch_batches(g, a, q, 0, nb, true);
                     launch_iteration_end(g, a);
                 } catch (...) {
                     cudaGraph_t tmp;
@@ -875,11 +1289,23 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         }
         batches += nb;
         LF_CUDA(cudaStreamSynchronize(st));
-        if (g->profile) {
-            for (int64_t b = 0; b < nb; ++b) prof_ms += elapsed_ms(g->prof_ev[2 * b], g->prof_ev[2 * b + 1]);
+        if (g->profile && persistent) {
+            prof_ms += elapsed_ms(pev[0], pev[1]);
+            prof_launches += 1;
+        } else if (g->profile) {
+            for (int64_t b = 0; b < nb && !std::isnan(prof_ms); ++b) {
+                float t = 0.f;
+                if (cudaEventElapsedTime(&t, g->prof_ev[2 * b], g->prof_ev[2 * b + 1]) == cudaSuccess) {
+                    prof_ms += (double)t;
+                } else {
+                    cudaGetLastError();   // timing unavailable for this launch mode: report NaN
+                    prof_ms = std::nan("");
+                }
+            }
             prof_launches += nb;
         }
         const Readback rb = *g->rb;
+        if (rb.err & DERR_TIMEOUT) fail(LF_ERR_TIMEOUT, "a grid-barrier wait ran out (limit %d ms)", g->barrier_timeout_ms);
         if (rb.err & DERR_CAPACITY) fail(LF_ERR_CAPACITY, "membership row overflow (internal bound violated)");
         if (rb.err & DERR_CHECK) fail(LF_ERR_CUDA, "device consistency check failed (histogram partitioning)");
         iters = it;
@@ -914,13 +1340,13 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         stats->ms_iterations = elapsed_ms(ev[1], ev[2]);
         stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         stats->num_launches = (int64_t)(g->launches - launches0);
-        stats->prof_eval_launches = prof_launches;
-        stats->prof_eval_ms = prof_ms;
+        stats->prof_move_launches = prof_launches;
+        stats->prof_move_ms = prof_ms;
         unsigned long long pbytes = 0;
         if (g->profile) {
             LF_CUDA(cudaMemcpy(&pbytes, &g->ds->prof_bytes, 8, cudaMemcpyDeviceToHost));
         }
-        stats->prof_eval_bytes = (int64_t)pbytes;
+        stats->prof_move_bytes = (int64_t)pbytes;
     }
 }
 

@@ -41,7 +41,9 @@ class Options(C.Structure):
     _fields_ = [("stream", C.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("edges_on_device", C.c_int32),
                 ("member_slots", C.c_int32), ("warp_max_degree", C.c_int32),
-                ("use_graphs", C.c_int32), ("profile", C.c_int32)]
+                ("use_graphs", C.c_int32), ("profile", C.c_int32), ("exhaustive_fp64", C.c_int32),
+                ("per_queue_launches", C.c_int32), ("barrier_timeout_ms", C.c_int32),
+                ("inject_barrier_stall", C.c_int32)]
 
 
 class RunStatsC(C.Structure):
@@ -51,8 +53,8 @@ class RunStatsC(C.Structure):
                 ("ms_iterations", C.c_double), ("history_cap", C.c_int32),
                 ("wcc_history", C.POINTER(C.c_double)), ("joins_history", C.POINTER(C.c_int64)),
                 ("leaves_history", C.POINTER(C.c_int64)), ("num_launches", C.c_int64),
-                ("prof_eval_launches", C.c_int64), ("prof_eval_ms", C.c_double),
-                ("prof_eval_bytes", C.c_int64)]
+                ("prof_move_launches", C.c_int64), ("prof_move_ms", C.c_double),
+                ("prof_move_bytes", C.c_int64)]
 
 
 class CreateStatsC(C.Structure):
@@ -145,9 +147,9 @@ class RunStats:
     ms_init: float
     ms_iterations: float
     num_launches: int = 0
-    prof_eval_launches: int = 0
-    prof_eval_ms: float = 0.0
-    prof_eval_bytes: int = 0
+    prof_move_launches: int = 0
+    prof_move_ms: float = 0.0
+    prof_move_bytes: int = 0
 
 
 class Graph:
@@ -159,7 +161,9 @@ class Graph:
     """
 
     def __init__(self, src, dst, *, stream=None, allocator: str = "torch", member_slots: int = 0,
-                 warp_max_degree: int = 0, use_graphs: bool = True, profile: bool = False, device=None):
+                 warp_max_degree: int = 0, use_graphs: bool = True, profile: bool = False,
+                 exhaustive_fp64: bool = False, per_queue_launches: bool = False,
+                 barrier_timeout_ms: int = 0, inject_barrier_stall: bool = False, device=None):
         import torch
         self._L = load_library()
         self._h = C.c_void_p()
@@ -185,6 +189,10 @@ class Graph:
         opt.warp_max_degree = int(warp_max_degree)
         opt.use_graphs = 0 if use_graphs else -1
         opt.profile = 1 if profile else 0
+        opt.exhaustive_fp64 = 1 if exhaustive_fp64 else 0
+        opt.per_queue_launches = 1 if per_queue_launches else 0
+        opt.barrier_timeout_ms = int(barrier_timeout_ms)
+        opt.inject_barrier_stall = 1 if inject_barrier_stall else 0
         if isinstance(src, torch.Tensor):
             if src.dtype != torch.int32 or dst.dtype != torch.int32 or not src.is_cuda:
                 raise TypeError("device edge lists must be int32 CUDA tensors")
@@ -249,8 +257,8 @@ class Graph:
         k = st.iterations
         return RunStats(k, bool(st.converged), st.num_batches, st.wcc_initial, T[:k].copy(), J[:k].copy(),
                         Lv[:k].copy(), st.num_communities, st.num_memberships, st.ms_total, st.ms_init,
-                        st.ms_iterations, st.num_launches, st.prof_eval_launches, st.prof_eval_ms,
-                        st.prof_eval_bytes)
+                        st.ms_iterations, st.num_launches, st.prof_move_launches, st.prof_move_ms,
+                        st.prof_move_bytes)
 
     def communities(self):
         """(offsets int64[k+1], members int32[...]) in original node ids."""

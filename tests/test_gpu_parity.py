@@ -147,7 +147,8 @@ def test_graph_replay_equals_direct_launches_and_reruns(lf, oracle_lib):
     el = W.eu_core_like(seed=2)
     og = oracle_lib.OracleGraph(el.src, el.dst)
     ref = og.run(32, 0.01, 50)
-    with lf.Graph(el.src, el.dst, use_graphs=False) as g1, lf.Graph(el.src, el.dst) as g2:
+    with lf.Graph(el.src, el.dst, per_queue_launches=True, use_graphs=False) as g1, \
+            lf.Graph(el.src, el.dst, per_queue_launches=True) as g2:
         a = g1.run(32, 0.01, 50)
         b = g2.run(32, 0.01, 50)
         c = g2.run(32, 0.01, 50)    # same handle again: restarts from the initial clustering
@@ -223,3 +224,47 @@ def test_full_size_335k_parity(lf, oracle_lib, q):
         want = og.communities()
         assert off.shape[0] - 1 == len(want)
         assert np.array_equal(mem, np.concatenate(want))
+
+
+@pytest.mark.parametrize("el", [CASES[-1], CASES[-2], CASES[-4]], ids=[IDS[-1], IDS[-2], IDS[-4]])
+def test_fp32_screen_changes_no_decision(lf, oracle_lib, el):
+    """The FP32 screen only rules out candidates that cannot be the best
+    action: evaluating every candidate in FP64 gives the same run."""
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(64, -math.inf, 5)
+    with lf.Graph(el.src, el.dst, exhaustive_fp64=True) as g1, lf.Graph(el.src, el.dst) as g2:
+        a = g1.run(64, -math.inf, 5)
+        b = g2.run(64, -math.inf, 5)
+        compare_run(a, ref)
+        compare_run(b, ref)
+        s1, s2 = g1.state(), g2.state()
+        for k in s1:
+            assert np.array_equal(s1[k], s2[k])
+
+
+@pytest.mark.parametrize("el", [CASES[-1], CASES[-2], CASES[-4], CASES[1]], ids=[IDS[-1], IDS[-2], IDS[-4], IDS[1]])
+@pytest.mark.parametrize("q", [1, 64, 4096])
+def test_persistent_loop_equals_per_queue_launches(lf, oracle_lib, el, q):
+    """The persistent queue kernel (default) and two launches per queue give
+    the oracle's run, queue for queue."""
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(q, 0.01, 50)
+    with lf.Graph(el.src, el.dst, per_queue_launches=True) as g1, lf.Graph(el.src, el.dst) as g2:
+        compare_run(g1.run(q, 0.01, 50), ref)
+        compare_run(g2.run(q, 0.01, 50), ref)
+        compare_state(g2, og)
+
+
+def test_barrier_timeout_is_reported_and_recoverable(lf, oracle_lib):
+    """A block that never reaches the grid barrier (injected on the host side
+    of the test through an option) makes every bounded wait run out: the call
+    returns LF_ERR_TIMEOUT instead of hanging, and the GPU stays usable."""
+    el = W.eu_core_like(seed=6)
+    with lf.Graph(el.src, el.dst, inject_barrier_stall=True, barrier_timeout_ms=50) as g:
+        with pytest.raises(lf.LazyFoxError) as ei:
+            g.run(64, 0.01, 5)
+        assert ei.value.status == lf.LF_ERR_TIMEOUT
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(64, 0.01, 50)
+    with lf.Graph(el.src, el.dst) as g:
+        compare_run(g.run(64, 0.01, 50), ref)
