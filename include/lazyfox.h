@@ -76,6 +76,11 @@ typedef struct lf_options {
                                 runs out ends the call with LF_ERR_TIMEOUT */
     int32_t inject_barrier_stall; /* test hook: 1 makes one block of the persistent kernel
                                 skip its barriers, so that the bounded waits run out */
+    int32_t barrier_mode;    /* persistent kernel's grid barrier: 0 (default) every block
+                                polls all arrival flags; 1 block 0 gathers them and
+                                publishes one release flag */
+    int32_t warps_per_node;  /* warps that evaluate one node together: 1, 2, 4 or 8; 0 (default)
+                                picks by queue size (more warps per node for small queues) */
 } lf_options;
 
 /* Per-run statistics.  The history pointers are optional caller buffers with
@@ -105,6 +110,8 @@ typedef struct lf_run_stats {
                                 (persistent kernel): 8 per node, and per moving node
                                 24 + 4|M(x)| + 12 per action, plus 16 per neighbour when
                                 the neighbour scan runs */
+    double prof_queue_us[4]; /* profile mode, persistent kernel: p50, p90, p99 and max of the
+                                time per queue (evaluate + apply + barriers), last iteration */
 } lf_run_stats;
 
 /* Device times of the phases of lf_graph_create. */

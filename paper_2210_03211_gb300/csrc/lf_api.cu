@@ -176,6 +176,8 @@ lf_status lf_graph_create(const int32_t *src, const int32_t *dst, int64_t num_ed
             g->per_queue = opt->per_queue_launches == 1 ? 1 : 0;
             if (opt->barrier_timeout_ms > 0) g->barrier_timeout_ms = opt->barrier_timeout_ms;
             g->inject_stall = opt->inject_barrier_stall == 1 ? 1 : 0;
+            g->barrier_mode = opt->barrier_mode == 1 ? 1 : 0;
+            g->warps_per_node = opt->warps_per_node;
             if ((g->alloc_cb == nullptr) != (g->free_cb == nullptr))
                 fail(LF_ERR_INVALID, "alloc and free callbacks must be set together");
         }

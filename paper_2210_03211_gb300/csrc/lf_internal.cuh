@@ -103,6 +103,8 @@ struct lf_graph {
     int32_t per_queue = 0;                         // 1: kernel launches per queue instead of the persistent loop
     int32_t barrier_timeout_ms = 2000;
     int32_t inject_stall = 0;
+    int32_t barrier_mode = 0;                      // grid barrier: 0 flat flags, 1 central release flag
+    int32_t warps_per_node = 0;                    // team size of the move evaluation (0: by queue size)
     unsigned long long launches = 0;               // kernels launched (host count)
     std::vector<std::pair<void *, size_t>> live;   // outstanding allocations
 
@@ -139,6 +141,10 @@ struct lf_graph {
     int32_t graph_q = 0, graph_K = 0;
     unsigned long long graph_kernels = 0;          // kernel nodes of iter_exec
     std::vector<cudaEvent_t> prof_ev;              // profile mode: 2 per queue
+    unsigned *bar_flags = nullptr;                 // grid barrier: one epoch flag per block
+    int bar_flags_cap = 0;
+    unsigned bar_epoch = 0;
+    unsigned long long *qtimes = nullptr;          // profile mode: per-queue time stamps
 };
 
 namespace lf {

@@ -7,6 +7,7 @@
 //   a8  bulk apply of one queue: membership rows and community aggregates,
 //       with the exact internal-edge correction for nodes that move together
 //   a9  iteration end: removal of degenerate communities, exact WCC-hat(P)
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 
@@ -29,7 +30,6 @@ struct RunArgs {
     const int32_t *order;
     const int32_t *pos;
     CommRec *comm;
-    unsigned long long *stamp;
     int32_t *mem;
     int32_t *nmem;
     int32_t K;
@@ -42,6 +42,7 @@ struct RunArgs {
     int64_t nnodes;
     int32_t warp_max_deg;
     int32_t profile;   // count algorithmic bytes of the move evaluation
+    unsigned long long *qtimes;   // profile mode: time stamp after each queue (persistent kernel)
     int32_t screen;    // 1: rule candidates out with the FP32 bound first
     float cc32;        // cc rounded to float (screen)
     float delta;       // relative error bound of the screen (see score32)
@@ -221,11 +222,10 @@ __device__ __forceinline__ float score32(int64_t n, int64_t m2, int64_t vol, flo
 // delta x (S_new + S_old) with delta covering the FP32 rounding, the FP64
 // rounding of the estimator (which grows with m2 and vol through C(din,2) and
 // D - din) and the two subtractions.
-__device__ __forceinline__ void screen_gain(const RunArgs &a, int32_t C, uint32_t v, int32_t d, float &g,
-                                           float &err) {
+__device__ __forceinline__ void screen_gain_rec(const RunArgs &a, const int4 &r, uint32_t v, int32_t d, float &g,
+                                               float &err) {
     const bool own = (v & OWN_FLAG) != 0;
     const int64_t k = (int64_t)(v & ~OWN_FLAG);
-    const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
     const int64_t n = r.x, m2 = (uint32_t)r.y, vol = (uint32_t)r.z;
     const float so = score32(n, m2, vol, a.cc32);
     const float sn = own ? score32(n - 1, m2 - 2 * k, vol - d, a.cc32) : score32(n + 1, m2 + 2 * k, vol + d, a.cc32);
@@ -244,24 +244,39 @@ __device__ __forceinline__ float warp_max_f(float x) {
     return x;
 }
 
-// Pass 1 over table slots [lo, hi): the largest lower bound of a join gain
-// and of a leave gain (per lane); each slot's upper and lower bounds are
-// kept in ub[] and ub[HB + slot].
+// Pass 1 over candidate slots [lo, hi) (empty slots are skipped): the largest
+// lower bound of a join gain and of a leave gain (per lane); each slot's
+// upper and lower bounds are kept in ub[] and lb[].  Four record loads are
+// issued before any of them is used.
 __device__ __forceinline__ void screen_bounds(const RunArgs &a, const int32_t *keys, const uint32_t *vals,
-                                              float *ub, uint32_t lo, uint32_t hi, int32_t d, float &lbj,
+                                              float *ub, float *lb, uint32_t lo, uint32_t hi, int32_t d, float &lbj,
                                               float &lbl) {
     const int lane = threadIdx.x & 31;
-    for (uint32_t s = lo + lane; s < hi; s += 32) {
-        const int32_t C = keys[s];
-        if (C == EMPTY_KEY) continue;
-        const uint32_t v = vals[s];
-        float g, e;
-        screen_gain(a, C, v, d, g, e);
-        const float lb = __fsub_rn(g, e);
-        ub[s] = __fadd_rn(g, e);
-        ub[HB + s] = lb;
-        if (v & OWN_FLAG) lbl = fmaxf(lbl, lb);
-        else lbj = fmaxf(lbj, lb);
+    for (uint32_t s0 = lo + lane; s0 < hi; s0 += 128) {
+        int32_t C[4];
+        uint32_t v[4];
+        int4 r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t s = s0 + 32u * u;
+            C[u] = s < hi ? keys[s] : EMPTY_KEY;
+            v[u] = s < hi ? vals[s] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            r[u] = C[u] != EMPTY_KEY ? __ldcg(reinterpret_cast<const int4 *>(&a.comm[C[u]])) : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (C[u] == EMPTY_KEY) continue;
+            float g, e;
+            screen_gain_rec(a, r[u], v[u], d, g, e);
+            const float l = __fsub_rn(g, e);
+            const uint32_t s = s0 + 32u * u;
+            ub[s] = __fadd_rn(g, e);
+            lb[s] = l;
+            if (v[u] & OWN_FLAG) lbl = fmaxf(lbl, l);
+            else lbj = fmaxf(lbj, l);
+        }
     }
 }
 
@@ -280,8 +295,8 @@ __device__ __forceinline__ bool survives(float ub, uint32_t v, float lbj, float 
     return ub > 0.f && ub >= ((v & OWN_FLAG) ? lbl : lbj);
 }
 
-__device__ void count_survivors(const int32_t *keys, const uint32_t *vals, const float *ubs, uint32_t lo,
-                                uint32_t hi, float lbj, float lbl, Survivors &sv) {
+__device__ void count_survivors(const int32_t *keys, const uint32_t *vals, const float *ubs, const float *lbs,
+                                uint32_t lo, uint32_t hi, float lbj, float lbl, Survivors &sv) {
     const int lane = threadIdx.x & 31;
     sv = Survivors{0, 0, -1, -1, 0u, 0u, 0.f, 0.f};
     for (uint32_t base = lo; base < hi; base += 32) {
@@ -295,7 +310,7 @@ __device__ void count_survivors(const int32_t *keys, const uint32_t *vals, const
             if (C != EMPTY_KEY) {
                 v = vals[s];
                 if (survives(ubs[s], v, lbj, lbl)) {
-                    lb = ubs[HB + s];
+                    lb = lbs[s];
                     if (v & OWN_FLAG) sl = true; else sj = true;
                 }
             }
@@ -365,103 +380,252 @@ __device__ void eval_survivors(const RunArgs &a, const int32_t *keys, const uint
     __syncwarp();
 }
 
-// Saturating "how many actions of this queue target C" counter, tagged with
-// the queue's serial number so that it never needs clearing.
-__device__ __forceinline__ void stamp_add(unsigned long long *w, unsigned long long serial) {
-    unsigned long long old = *((volatile unsigned long long *)w), assumed;
-    do {
-        assumed = old;
-        unsigned long long c = (assumed >> 2) == serial ? (assumed & 3ull) : 0ull;
-        unsigned long long nw = (serial << 2) | (c >= 2ull ? 2ull : c + 1ull);
-        if (nw == assumed) return;
-        old = atomicCAS(w, assumed, nw);
-    } while (old != assumed);
-}
-
-__device__ __forceinline__ bool stamp_multi(const unsigned long long *w, unsigned long long serial) {
-    unsigned long long v = __ldcg(w);
-    return (v >> 2) == serial && (v & 3ull) >= 2ull;
-}
-
 __device__ __forceinline__ void write_action(const RunArgs &a, int i, const Best &bj, const Best &bl,
                                              unsigned long long serial) {
     a.act[i] = bj.c;
     a.act[a.qcap + i] = bl.c;
     a.act[2 * a.qcap + i] = bj.k;
     a.act[3 * a.qcap + i] = bl.k;
-    if (bj.c >= 0) stamp_add(a.stamp + bj.c, serial);
-    if (bl.c >= 0) stamp_add(a.stamp + bl.c, serial);
+    (void)serial;
 }
 
 // One warp, one node: every membership of every neighbour goes into the
 // warp's table; equal ids arriving in the same step are merged first with
 // __match_any_sync, so each id costs one atomic per step.  `bound` (>= the
 // number of distinct ids) keeps the table at most half full.
-__device__ void eval_warp(const RunArgs &a, int i, int32_t x, int32_t d, int64_t bound, int32_t *keys,
-                          uint32_t *vals, float *ubs, int32_t *bkey, uint32_t *bval, unsigned long long serial) {
-    const int lane = threadIdx.x & 31;
-    uint32_t H = 32;
-    while ((int64_t)H < 2 * bound) H <<= 1;
-    const uint32_t hm = H - 1;
-    for (uint32_t s = lane; s < H; s += 32) {
-        keys[s] = EMPTY_KEY;
-        vals[s] = 0u;
+// Entry s of a membership row whose first eight entries are in r0, r1.
+__device__ __forceinline__ int32_t row_entry(const int4 &r0, const int4 &r1, const int32_t *row, int s) {
+    switch (s) {
+    case 0: return r0.x;
+    case 1: return r0.y;
+    case 2: return r0.z;
+    case 3: return r0.w;
+    case 4: return r1.x;
+    case 5: return r1.y;
+    case 6: return r1.z;
+    case 7: return r1.w;
+    default: return __ldcg(row + s);
     }
-    __syncwarp();
-    const int32_t cx = __ldcg(&a.nmem[x]);
-    const int32_t *rowx = a.mem + (int64_t)x * a.K;
-    for (int j = lane; j < cx; j += 32) ht_insert(keys, vals, hm, __ldcg(&rowx[j]), 0u, true);
-    __syncwarp();
-    const int64_t beg = a.off[x], end = a.off[x + 1];
-    unsigned long long pb = 0;
-    for (int64_t p0 = beg; p0 < end; p0 += 32) {
-        const int64_t p = p0 + lane;
-        int32_t y = 0, cy = 0;
-        if (p < end) {
-            y = a.adj[p];
-            cy = __ldcg(&a.nmem[y]);
-            pb += 8ull + 4ull * (unsigned long long)cy;
-        }
-        const int32_t cmax = __reduce_max_sync(FULL, cy);
-        const int32_t *rowy = a.mem + (int64_t)y * a.K;
-        for (int s = 0; s < cmax; ++s) {
-            int32_t C = s < cy ? __ldcg(&rowy[s]) : -2 - lane;
-            unsigned mask = __match_any_sync(FULL, C);
-            if (C >= 0 && lane == __ffs(mask) - 1) ht_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false);
-        }
+}
+
+// First eight entries of a row (rows are 16-byte aligned, K a multiple of 4).
+__device__ __forceinline__ void row_head(const int32_t *row, int32_t cnt, int4 &r0, int4 &r1) {
+    r0 = cnt > 0 ? __ldcg(reinterpret_cast<const int4 *>(row)) : make_int4(0, 0, 0, 0);
+    r1 = cnt > 4 ? __ldcg(reinterpret_cast<const int4 *>(row) + 1) : make_int4(0, 0, 0, 0);
+}
+
+// Team of T warps (T in 1, 2, 4, 8) working on one node.  Teams of one
+// block are numbered tm = warp / T; a team of the whole block synchronises with
+// __syncthreads, a single warp with __syncwarp, others with named barrier 1+tm.
+template <int T>
+__device__ __forceinline__ void team_sync(int tm) {
+    if constexpr (T == 1) {
+        __syncwarp();
+    } else if constexpr (T == EV_WARPS) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + tm), "r"(T * 32) : "memory");
     }
-    __syncwarp();
+}
+
+// Per-warp values a team exchanges through shared memory.
+struct TeamScratch {
+    long long part[EV_WARPS];
+    float lbj[EV_WARPS], lbl[EV_WARPS];
+    int cj[EV_WARPS], cl[EV_WARPS];
+    int32_t Cj[EV_WARPS], Cl[EV_WARPS];
+    uint32_t vj[EV_WARPS], vl[EV_WARPS];
+    float ulj[EV_WARPS], ull[EV_WARPS];
+    double bgj[EV_WARPS], bgl[EV_WARPS];
+    int32_t bcj[EV_WARPS], bcl[EV_WARPS], bkj[EV_WARPS], bkl[EV_WARPS];
+};
+
+// Evaluate node x with a team of T warps.  `bound` (the number of
+// (neighbour, community) entries plus x's own memberships) bounds the number
+// of distinct ids; the team's table is sized to stay at most half full.  Warp
+// w_in of the team takes adjacency chunks w_in, w_in + T, ... (its first chunk
+// and the chunk's membership counts arrive in y0 / c0) and a contiguous slice
+// of the table for the screen and the FP64 pass.
+// Second half of a node's evaluation, on the filled table of H slots: compact
+// the candidates, screen them in FP32, decide from the screen alone when one
+// candidate of a kind provably wins, evaluate the rest in FP64, reduce over
+// the team and record the actions.  bj / bl return the actions (team leader).
+template <int T>
+__device__ void decide_node(const RunArgs &a, int i, int32_t d, int32_t cx, uint32_t H, int32_t *keys,
+                            uint32_t *vals, float *ubs, int32_t *bkey, uint32_t *bval, TeamScratch &ts, int tm,
+                            int w_in, unsigned long long serial, unsigned long long pb, Best &bj_out,
+                            Best &bl_out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int w0 = tm * T;
+    // compact the occupied slots into a dense candidate list (ids into the
+    // upper-bound area, counts into the lower-bound area; the table itself is
+    // then free and holds the bounds)
+    uint32_t ncand, lo, hi;
+    int32_t *ck = reinterpret_cast<int32_t *>(ubs);
+    uint32_t *cv = reinterpret_cast<uint32_t *>(ubs + HB);
+    float *cub = reinterpret_cast<float *>(keys);
+    float *clb = reinterpret_cast<float *>(vals);
+    {
+        const uint32_t slice = (H + T - 1) / T;
+        const uint32_t tlo = min(H, (uint32_t)w_in * slice), thi = min(H, tlo + slice);
+        uint32_t cnt = 0;
+        for (uint32_t b0 = tlo; b0 < thi; b0 += 32) {
+            const uint32_t s = b0 + lane;
+            cnt += __popc(__ballot_sync(FULL, s < thi && keys[s] != EMPTY_KEY));
+        }
+        uint32_t offs = 0;
+        ncand = cnt;
+        if constexpr (T > 1) {
+            if (lane == 0) ts.part[w] = cnt;
+            team_sync<T>(tm);
+            ncand = 0;
+            for (int k = 0; k < T; ++k) {
+                const uint32_t c = (uint32_t)ts.part[w0 + k];
+                if (k < w_in) offs += c;
+                ncand += c;
+            }
+        }
+        const unsigned lt = lanemask_lt();
+        for (uint32_t b0 = tlo; b0 < thi; b0 += 32) {
+            const uint32_t s = b0 + lane;
+            const bool occ = s < thi && keys[s] != EMPTY_KEY;
+            const unsigned m = __ballot_sync(FULL, occ);
+            if (occ) {
+                const uint32_t q = offs + __popc(m & lt);
+                ck[q] = keys[s];
+                cv[q] = vals[s];
+            }
+            offs += __popc(m);
+        }
+        team_sync<T>(tm);
+        const uint32_t dslice = (ncand + T - 1) / T;
+        lo = min(ncand, (uint32_t)w_in * dslice);
+        hi = min(ncand, lo + dslice);
+    }
     Best bj{0.0, -1, 0}, bl{0.0, -1, 0};
     float lbj = -INFINITY, lbl = -INFINITY;
     bool do_j = true, do_l = true;
+    Best uj{0.0, -1, 0}, ul{0.0, -1, 0};   // decided by the screen alone
     if (a.screen) {
-        screen_bounds(a, keys, vals, ubs, 0, H, d, lbj, lbl);
+        screen_bounds(a, ck, cv, cub, clb, lo, hi, d, lbj, lbl);
         lbj = warp_max_f(lbj);
         lbl = warp_max_f(lbl);
-        __syncwarp();
+        if constexpr (T > 1) {
+            if (lane == 0) {
+                ts.lbj[w] = lbj;
+                ts.lbl[w] = lbl;
+            }
+            team_sync<T>(tm);
+            for (int k = 0; k < T; ++k) {
+                lbj = fmaxf(lbj, ts.lbj[w0 + k]);
+                lbl = fmaxf(lbl, ts.lbl[w0 + k]);
+            }
+        } else {
+            __syncwarp();
+        }
         Survivors sv;
-        count_survivors(keys, vals, ubs, 0, H, lbj, lbl, sv);
+        count_survivors(ck, cv, cub, clb, lo, hi, lbj, lbl, sv);
+        if constexpr (T > 1) {
+            if (lane == 0) {
+                ts.cj[w] = sv.cj; ts.Cj[w] = sv.Cj; ts.vj[w] = sv.vj; ts.ulj[w] = sv.lbj;
+                ts.cl[w] = sv.cl; ts.Cl[w] = sv.Cl; ts.vl[w] = sv.vl; ts.ull[w] = sv.lbl;
+            }
+            team_sync<T>(tm);
+            sv = Survivors{0, 0, -1, -1, 0u, 0u, 0.f, 0.f};
+            for (int k = 0; k < T; ++k) {
+                const int q = w0 + k;
+                if (ts.cj[q] > 0 && sv.cj == 0) { sv.Cj = ts.Cj[q]; sv.vj = ts.vj[q]; sv.lbj = ts.ulj[q]; }
+                if (ts.cl[q] > 0 && sv.cl == 0) { sv.Cl = ts.Cl[q]; sv.vl = ts.vl[q]; sv.lbl = ts.ull[q]; }
+                sv.cj += ts.cj[q];
+                sv.cl += ts.cl[q];
+            }
+        }
         do_j = sv.cj > 1 || (sv.cj == 1 && !(sv.lbj > 0.f));
         do_l = sv.cl > 1 || (sv.cl == 1 && !(sv.lbl > 0.f));
-        if (lane == 0) {
-            if (sv.cj == 1 && !do_j) bj = Best{INFINITY, sv.Cj, (int32_t)(sv.vj & ~OWN_FLAG)};
-            if (sv.cl == 1 && !do_l) bl = Best{INFINITY, sv.Cl, (int32_t)(sv.vl & ~OWN_FLAG)};
-        }
+        if (sv.cj == 1 && !do_j) uj = Best{INFINITY, sv.Cj, (int32_t)(sv.vj & ~OWN_FLAG)};
+        if (sv.cl == 1 && !do_l) ul = Best{INFINITY, sv.Cl, (int32_t)(sv.vl & ~OWN_FLAG)};
         if (sv.cj == 0) do_j = false;
         if (sv.cl == 0) do_l = false;
     }
-    if (do_j || do_l) eval_survivors(a, keys, vals, ubs, 0, H, d, lbj, lbl, do_j, do_l, bkey, bval, bj, bl);
-    if (a.profile)
-        for (uint32_t s = lane; s < H; s += 32) pb += keys[s] != EMPTY_KEY ? 16ull : 0ull;
+    if (do_j || do_l) eval_survivors(a, ck, cv, cub, lo, hi, d, lbj, lbl, do_j, do_l, bkey, bval, bj, bl);
+    if (a.profile && lane == 0) pb += 16ull * (unsigned long long)(hi - lo);
     warp_best(bj);
     warp_best(bl);
     if (a.profile) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) pb += __shfl_down_sync(FULL, pb, o);
-        if (lane == 0) atomicAdd(&a.ds->prof_bytes, pb + 44ull + 4ull * (unsigned long long)cx);
+        if (lane == 0) atomicAdd(&a.ds->prof_bytes, pb + (w_in == 0 ? 44ull + 4ull * (unsigned long long)cx : 0ull));
     }
-    if (lane == 0) write_action(a, i, bj, bl, serial);
-    __syncwarp();
+    if constexpr (T > 1) {
+        if (lane == 0) {
+            ts.bgj[w] = bj.g; ts.bcj[w] = bj.c; ts.bkj[w] = bj.k;
+            ts.bgl[w] = bl.g; ts.bcl[w] = bl.c; ts.bkl[w] = bl.k;
+        }
+        team_sync<T>(tm);
+        if (w_in == 0 && lane == 0) {
+            for (int k = 1; k < T; ++k) {
+                const int q = w0 + k;
+                if (better(ts.bgj[q], ts.bcj[q], bj.g, bj.c)) bj = Best{ts.bgj[q], ts.bcj[q], ts.bkj[q]};
+                if (better(ts.bgl[q], ts.bcl[q], bl.g, bl.c)) bl = Best{ts.bgl[q], ts.bcl[q], ts.bkl[q]};
+            }
+        }
+    }
+    if (w_in == 0 && lane == 0) {
+        if (uj.c >= 0) bj = uj;
+        if (ul.c >= 0) bl = ul;
+        write_action(a, i, bj, bl, serial);
+    }
+    bj_out = bj;
+    bl_out = bl;
+    team_sync<T>(tm);
+}
+
+template <int T>
+__device__ void eval_team(const RunArgs &a, int i, int32_t x, int32_t d, int64_t beg, int64_t end, int64_t bound,
+                          int32_t y0, int32_t c0, int32_t *keys, uint32_t *vals, float *ubs, int32_t *bkey,
+                          uint32_t *bval, TeamScratch &ts, int tm, int w_in, unsigned long long serial) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tl = w_in * 32 + lane;
+    constexpr int NT = T * 32;
+    const int w0 = tm * T;   // first warp of the team
+    uint32_t H = 32;
+    while ((int64_t)H < 2 * bound) H <<= 1;
+    const uint32_t hm = H - 1;
+    for (uint32_t s = tl; s < H; s += NT) {
+        keys[s] = EMPTY_KEY;
+        vals[s] = 0u;
+    }
+    team_sync<T>(tm);
+    const int32_t cx = __ldcg(&a.nmem[x]);
+    const int32_t *rowx = a.mem + (int64_t)x * a.K;
+    for (int j = tl; j < cx; j += NT) ht_insert(keys, vals, hm, __ldcg(&rowx[j]), 0u, true);
+    team_sync<T>(tm);
+    unsigned long long pb = 0;
+    const int64_t first = beg + w_in * 32;
+    for (int64_t p0 = first; p0 < end; p0 += NT) {
+        const int64_t p = p0 + lane;
+        int32_t y = 0, cy = 0;
+        if (p0 == first) {
+            y = y0;
+            cy = c0;
+        } else if (p < end) {
+            y = a.adj[p];
+            cy = __ldcg(&a.nmem[y]);
+        }
+        if (p < end) pb += 8ull + 4ull * (unsigned long long)cy;
+        const int32_t cmax = __reduce_max_sync(FULL, cy);
+        const int32_t *rowy = a.mem + (int64_t)y * a.K;
+        int4 r0, r1;
+        row_head(rowy, cy, r0, r1);
+        for (int s = 0; s < cmax; ++s) {
+            int32_t C = s < cy ? row_entry(r0, r1, rowy, s) : -2 - lane;
+            unsigned mask = __match_any_sync(FULL, C);
+            if (C >= 0 && lane == __ffs(mask) - 1) ht_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false);
+        }
+    }
+    team_sync<T>(tm);
+    Best bj, bl;
+    decide_node<T>(a, i, d, cx, H, keys, vals, ubs, bkey, bval, ts, tm, w_in, serial, pb, bj, bl);
 }
 
 __device__ __forceinline__ uint32_t part_of(int32_t C, int P) {
@@ -524,8 +688,10 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
                 }
                 const int32_t cmax = __reduce_max_sync(FULL, cy);
                 const int32_t *rowy = a.mem + (int64_t)y * a.K;
+                int4 r0, r1;
+                row_head(rowy, cy, r0, r1);
                 for (int s = 0; s < cmax; ++s) {
-                    int32_t C = s < cy ? __ldcg(&rowy[s]) : -1;
+                    int32_t C = s < cy ? row_entry(r0, r1, rowy, s) : -1;
                     if (C >= 0 && P > 1 && part_of(C, P) != (uint32_t)part) C = -1;
                     if (C < 0) C = -2 - lane;
                     unsigned mask = __match_any_sync(FULL, C);
@@ -544,7 +710,7 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
             const uint32_t lo = min(H, (uint32_t)w * slice), hi = min(H, lo + slice);
             if (a.screen) {
                 float wj = lbj, wl = lbl;
-                screen_bounds(a, keys, vals, ubs, lo, hi, d, wj, wl);
+                screen_bounds(a, keys, vals, ubs, ubs + HB, lo, hi, d, wj, wl);
                 wj = warp_max_f(wj);
                 wl = warp_max_f(wl);
                 if (lane == 0) {
@@ -594,30 +760,87 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
 
 struct EvalShared {
     int32_t hub[EV_WARPS];
+    long long hub_bound[EV_WARPS];
     int nhub;
     BlockScratch bs;
+    TeamScratch ts;
     int32_t bkey[EV_WARPS][32];
     uint32_t bval[EV_WARPS][32];
 };
 
-// One block evaluates the queue's nodes base .. base+EV_WARPS-1: a warp per
-// node, then the block together for each node too large for a warp's table.
-__device__ void eval_group(const RunArgs &a, int64_t bstart, int32_t blen, int base, int32_t kb,
-                           unsigned long long serial, int32_t *s_keys, uint32_t *s_vals, float *s_ub,
-                           EvalShared &es) {
+// Static data of a team's next node, fetched ahead of time (the node order,
+// degrees, offsets and adjacency never change during a run); y0 is this
+// warp's first adjacency chunk (chunk w_in of the node).
+struct NodePrefetch {
+    int32_t x, d, y0, valid;
+    int64_t beg, end;
+};
+
+__device__ __forceinline__ void prefetch_node(const RunArgs &a, int64_t bstart, int32_t blen, int i, int w_in,
+                                              NodePrefetch &pf) {
+    const int lane = threadIdx.x & 31;
+    pf.valid = 0;
+    if (i >= blen) return;
+    pf.x = a.order[bstart + i];
+    pf.d = a.deg[pf.x];
+    pf.beg = a.off[pf.x];
+    pf.end = a.off[pf.x + 1];
+    const int64_t p = pf.beg + w_in * 32 + lane;
+    pf.y0 = p < pf.end ? a.adj[p] : 0;
+    pf.valid = 1;
+}
+
+// One block evaluates queue nodes base .. base + EV_WARPS/T - 1, one team of T
+// warps per node; nodes too large for a team's table are done afterwards by
+// the whole block (with several passes over hash parts if needed).
+template <int T>
+__device__ void eval_group(const RunArgs &a, int64_t bstart, int32_t blen, int base, unsigned long long serial,
+                           int32_t *s_keys, uint32_t *s_vals, float *s_ub, EvalShared &es,
+                           const NodePrefetch *pf = nullptr) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tm = w / T, w_in = w % T;
     if (threadIdx.x == 0) es.nhub = 0;
     __syncthreads();
-    const int i = base + w;
+    const int i = base + tm;
     if (i < blen) {
-        const int32_t x = a.order[bstart + i];
-        const int32_t d = a.deg[x];
-        const int64_t bound = (int64_t)(d + 1) * kb;
-        if (d <= a.warp_max_deg && bound <= HW / 2) {
-            eval_warp(a, i, x, d, bound, s_keys + w * HW, s_vals + w * HW, s_ub + w * HW, es.bkey[w], es.bval[w],
-                      serial);
-        } else if (lane == 0) {
-            es.hub[atomicAdd(&es.nhub, 1)] = i;
+        const bool have = pf && pf->valid;
+        const int32_t x = have ? pf->x : a.order[bstart + i];
+        const int32_t d = have ? pf->d : a.deg[x];
+        const int64_t beg = have ? pf->beg : a.off[x], end = have ? pf->end : a.off[x + 1];
+        // exact number of entries the histogram will receive
+        int32_t y0 = 0, c0 = 0;
+        long long entries = 0;
+        const int64_t first = beg + w_in * 32;
+        for (int64_t p0 = first; p0 < end; p0 += T * 32) {
+            const int64_t p = p0 + lane;
+            int32_t y = 0, cy = 0;
+            if (p < end) {
+                y = (have && p0 == first) ? pf->y0 : a.adj[p];
+                cy = __ldcg(&a.nmem[y]);
+            }
+            if (p0 == first) {
+                y0 = y;
+                c0 = cy;
+            }
+            entries += cy;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) entries += __shfl_xor_sync(FULL, entries, o);
+        if constexpr (T > 1) {
+            if (lane == 0) es.ts.part[w] = entries;
+            team_sync<T>(tm);
+            entries = 0;
+            for (int k = 0; k < T; ++k) entries += es.ts.part[tm * T + k];
+            team_sync<T>(tm);   // part[] is rewritten by the team's next node only after this
+        }
+        entries += __ldcg(&a.nmem[x]);
+        if (d <= a.warp_max_deg && entries <= (long long)T * HW / 2) {
+            eval_team<T>(a, i, x, d, beg, end, entries, y0, c0, s_keys + tm * T * HW, s_vals + tm * T * HW,
+                         s_ub + tm * T * HW, es.bkey[w], es.bval[w], es.ts, tm, w_in, serial);
+        } else if (w_in == 0 && lane == 0) {
+            const int h = atomicAdd(&es.nhub, 1);
+            es.hub[h] = i;
+            es.hub_bound[h] = entries;
         }
     }
     __syncthreads();
@@ -625,8 +848,7 @@ __device__ void eval_group(const RunArgs &a, int64_t bstart, int32_t blen, int b
     for (int h = 0; h < nh; ++h) {
         const int ih = es.hub[h];
         const int32_t x = a.order[bstart + ih];
-        eval_block(a, ih, x, (int64_t)(a.deg[x] + 1) * kb, s_keys, s_vals, s_ub, es.bkey[w], es.bval[w], es.bs,
-                   serial);
+        eval_block(a, ih, x, (int64_t)es.hub_bound[h], s_keys, s_vals, s_ub, es.bkey[w], es.bval[w], es.bs, serial);
     }
     __syncthreads();
 }
@@ -635,12 +857,12 @@ __device__ __forceinline__ unsigned long long queue_serial(const RunArgs &a, int
     return (unsigned long long)__ldcg(&a.ds->iter) * (unsigned long long)a.nbatches + (unsigned long long)bidx + 1ull;
 }
 
+template <int T>
 __global__ void __launch_bounds__(EV_THREADS) k_eval(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx) {
-    extern __shared__ int32_t ev_dyn[];   // HB keys, HB counts, HB screen bounds
+    extern __shared__ int32_t ev_dyn[];   // HB keys, HB counts, HB upper and HB lower screen bounds
     __shared__ EvalShared es;
-    const int32_t kb = __ldcg(&a.ds->kb);
-    eval_group(a, bstart, blen, blockIdx.x * EV_WARPS, kb, queue_serial(a, bidx), ev_dyn,
-               reinterpret_cast<uint32_t *>(ev_dyn + HB), reinterpret_cast<float *>(ev_dyn + 2 * HB), es);
+    eval_group<T>(a, bstart, blen, blockIdx.x * (EV_WARPS / T), queue_serial(a, bidx), ev_dyn,
+                  reinterpret_cast<uint32_t *>(ev_dyn + HB), reinterpret_cast<float *>(ev_dyn + 2 * HB), es);
 }
 
 // ---------------------------------------------------------------------------
@@ -660,8 +882,11 @@ __device__ void apply_node(const RunArgs &a, int64_t bstart, int32_t blen, int64
         return;
     }
     const int32_t x = a.order[bstart + i];
-    const bool need_j = j >= 0 && stamp_multi(a.stamp + j, serial);
-    const bool need_l = l >= 0 && stamp_multi(a.stamp + l, serial);
+    // neighbours acting on the same community in this queue (static adjacency
+    // and positions; only in-queue neighbours' actions are read)
+    (void)serial;
+    const bool need_j = j >= 0;
+    const bool need_l = l >= 0;
     int jj = 0, jl = 0, ll = 0;
     if (need_j || need_l) {
         for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
@@ -681,32 +906,44 @@ __device__ void apply_node(const RunArgs &a, int64_t bstart, int32_t blen, int64
         jl = __reduce_add_sync(FULL, jl);
         ll = __reduce_add_sync(FULL, ll);
     }
-    if (lane == 0) {
-        const int32_t d = a.deg[x];
-        int32_t *row = a.mem + (int64_t)x * a.K;
-        int32_t c = __ldcg(&a.nmem[x]);
+    const int32_t d = a.deg[x];
+    int32_t *row = a.mem + (int64_t)x * a.K;
+    const int32_t c = __ldcg(&a.nmem[x]);
+    int32_t c_new = c;
+    if (c <= 32) {
+        // whole row in one coalesced load; leave l, insert j, keep ascending order
+        const int32_t v = lane < c ? __ldcg(&row[lane]) : 0;
+        const bool keep = lane < c && v != l;
+        const unsigned km = __ballot_sync(FULL, keep);
+        const unsigned lt = lanemask_lt();
+        const int kept = __popc(km);
+        int ins = kept;   // slot of j among the kept entries
+        if (j >= 0) ins = __popc(__ballot_sync(FULL, keep && v < j));
+        if (j >= 0 && kept >= a.K) {
+            if (lane == 0) atomicOr(&a.ds->err, DERR_CAPACITY);
+        } else {
+            if (keep) {
+                const int dst = __popc(km & lt);
+                row[dst + ((j >= 0 && dst >= ins) ? 1 : 0)] = v;
+            }
+            if (j >= 0 && lane == 0) row[ins] = j;
+            c_new = kept + (j >= 0 ? 1 : 0);
+        }
+    } else if (lane == 0) {
+        int32_t cc = c;
         if (l >= 0) {
-            const int32_t kl = __ldcg(&a.act[3 * a.qcap + i]);
-            atomicAdd(&a.comm[l].n, -1);
-            atomicAdd(&a.comm[l].vol, (uint32_t)(-d));
-            atomicAdd(&a.comm[l].m2, (uint32_t)(-2 * kl + ll));
             int32_t o = 0;
-            for (int32_t s = 0; s < c; ++s) {
+            for (int32_t s = 0; s < cc; ++s) {
                 const int32_t v = __ldcg(&row[s]);
                 if (v != l) row[o++] = v;
             }
-            c = o;
-            ++nl;
+            cc = o;
         }
         if (j >= 0) {
-            const int32_t kj = __ldcg(&a.act[2 * a.qcap + i]);
-            atomicAdd(&a.comm[j].n, 1);
-            atomicAdd(&a.comm[j].vol, (uint32_t)d);
-            atomicAdd(&a.comm[j].m2, (uint32_t)(2 * kj + jj - 2 * jl));
-            if (c >= a.K) {
+            if (cc >= a.K) {
                 atomicOr(&a.ds->err, DERR_CAPACITY);
             } else {
-                int32_t s = c;
+                int32_t s = cc;
                 while (s > 0) {
                     const int32_t v = __ldcg(&row[s - 1]);
                     if (v <= j) break;
@@ -714,11 +951,27 @@ __device__ void apply_node(const RunArgs &a, int64_t bstart, int32_t blen, int64
                     --s;
                 }
                 row[s] = j;
-                ++c;
+                ++cc;
             }
+        }
+        c_new = cc;
+    }
+    if (lane == 0) {
+        if (l >= 0) {
+            const int32_t kl = __ldcg(&a.act[3 * a.qcap + i]);
+            atomicAdd(&a.comm[l].n, -1);
+            atomicAdd(&a.comm[l].vol, (uint32_t)(-d));
+            atomicAdd(&a.comm[l].m2, (uint32_t)(-2 * kl + ll));
+            ++nl;
+        }
+        if (j >= 0) {
+            const int32_t kj = __ldcg(&a.act[2 * a.qcap + i]);
+            atomicAdd(&a.comm[j].n, 1);
+            atomicAdd(&a.comm[j].vol, (uint32_t)d);
+            atomicAdd(&a.comm[j].m2, (uint32_t)(2 * kj + jj - 2 * jl));
             ++nj;
         }
-        a.nmem[x] = c;
+        a.nmem[x] = c_new;
         if (a.profile) {
             const unsigned long long nb_scan = (need_j || need_l) ? 16ull * (unsigned long long)(a.off[x + 1] - a.off[x]) : 0ull;
             atomicAdd(&a.ds->prof_bytes, 24ull + 4ull * (unsigned long long)c + 12ull * ((j >= 0) + (l >= 0)) + nb_scan);
@@ -757,61 +1010,308 @@ __global__ void __launch_bounds__(AP_THREADS) k_apply(RunArgs a, int64_t bstart,
 // barrier wait is bounded; a wait that runs out sets DERR_TIMEOUT and the
 // kernel returns (the other blocks then run out at their next wait).
 // ---------------------------------------------------------------------------
-__device__ bool grid_sync(DevScalars *ds, unsigned nblocks, long long spin_limit, int *s_ok) {
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier on per-block epoch flags (flags[0 .. nblocks-1]) and one
+// release flag (flags[nblocks]).  The block's threads meet at __syncthreads;
+// thread 0 publishes the arrival with a release store of the barrier's epoch
+// (the release orders every write the block made before the __syncthreads).
+//   mode 0 (flat): warp 0 of every block polls all arrival flags.
+//   mode 1 (central): warp 0 of block 0 polls the arrival flags and then
+//     publishes the epoch in the release flag, which the other blocks poll
+//     (one line, with a short back-off).
+// Polling uses relaxed loads; an acquire fence after the wait orders the
+// block's later reads after the other blocks' writes.  No read-modify-write
+// on a shared counter.  The wait is bounded: when it runs out (or another
+// block reported a timeout) DERR_TIMEOUT is set and false returned.
+__device__ bool grid_sync(unsigned *flags, unsigned nblocks, unsigned epoch, long long spin_limit, DevScalars *ds,
+                          int *s_ok, int mode) {
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0) st_release_u32(flags + blockIdx.x, epoch);
         int ok = 1;
-        volatile unsigned *genp = &ds->bar_gen;
-        const unsigned g = *genp;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&ds->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&ds->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ds->bar_gen, 1u);
-        } else {
-            long long it = 0;
-            while (*genp == g) {
-                if (++it > spin_limit) {
-                    atomicOr(&ds->err, DERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
+        long long it = 0;
+        const bool gather = mode == 0 || blockIdx.x == 0;
+        for (;;) {
+            bool done = true;
+            if (gather) {
+                for (unsigned b = lane; b < nblocks; b += 32)
+                    done = done && (int)(ld_relaxed_u32(flags + b) - epoch) >= 0;
+            } else {
+                done = (int)(ld_relaxed_u32(flags + nblocks) - epoch) >= 0;
             }
+            if (__all_sync(FULL, done)) break;
+            ++it;
+            if (it > spin_limit ||
+                ((it & 255) == 0 && (*((volatile int *)&ds->err) & DERR_TIMEOUT))) {
+                ok = 0;
+                break;
+            }
+            if (!gather) __nanosleep(32);
         }
-        __threadfence();
-        if (*((volatile int *)&ds->err) & DERR_TIMEOUT) ok = 0;
-        *s_ok = ok;
+        if (mode == 1 && blockIdx.x == 0 && lane == 0 && ok) st_release_u32(flags + nblocks, epoch);
+        fence_acq_rel_gpu();
+        if (lane == 0) {
+            if (!ok) atomicOr(&ds->err, DERR_TIMEOUT);
+            *s_ok = ok;
+        }
+        __syncwarp();
     }
     __syncthreads();
     return *s_ok != 0;
 }
 
+// ---------------------------------------------------------------------------
+// Fused warp path of the persistent kernel, for queues that fit in one round
+// (one warp per node).  All of a node's independent loads go out together:
+// its neighbours' membership counts, positions and row heads, and its own
+// count and row head.  The warp keeps the node's state in registers across
+// the grid barrier and applies its own action from them: in-queue
+// neighbours are recognised from the positions already loaded, the row is
+// rewritten from the registers.  Nodes with more than 32 neighbours or more
+// than 8 memberships take the general path.
+// ---------------------------------------------------------------------------
+struct WarpNode {
+    int64_t beg, end;
+    int32_t x, d, cx;
+    int32_t py0;       // this lane's first-chunk neighbour's position in the order (-1: none)
+    int4 rx0, rx1;     // own row head
+    int32_t j, l, kj, kl;
+    int valid, fused;
+};
+
+__device__ void eval_fused(const RunArgs &a, int64_t bstart, int32_t blen, int i, const NodePrefetch &pf,
+                           WarpNode &wn, int32_t *keys, uint32_t *vals, float *ubs, EvalShared &es,
+                           unsigned long long serial) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    wn.valid = i < blen;
+    wn.fused = 0;
+    wn.j = wn.l = -1;
+    if (!wn.valid) return;
+    const bool have = pf.valid != 0;
+    const int32_t x = have ? pf.x : a.order[bstart + i];
+    const int32_t d = have ? pf.d : a.deg[x];
+    const int64_t beg = have ? pf.beg : a.off[x], end = have ? pf.end : a.off[x + 1];
+    wn.x = x;
+    wn.d = d;
+    wn.beg = beg;
+    wn.end = end;
+    const bool on = beg + lane < end;
+    const int32_t y0 = have ? pf.y0 : (on ? a.adj[beg + lane] : 0);
+    // one round of independent loads
+    const int32_t *rowx = a.mem + (int64_t)x * a.K;
+    const int32_t *rowy = a.mem + (int64_t)y0 * a.K;
+    const int32_t cy0 = on ? __ldcg(&a.nmem[y0]) : 0;
+    wn.py0 = on ? a.pos[y0] : -1;
+    const int32_t cx = __ldcg(&a.nmem[x]);
+    wn.rx0 = __ldcg(reinterpret_cast<const int4 *>(rowx));
+    wn.rx1 = a.K >= 8 ? __ldcg(reinterpret_cast<const int4 *>(rowx) + 1) : make_int4(0, 0, 0, 0);
+    const int4 ry0 = on ? __ldcg(reinterpret_cast<const int4 *>(rowy)) : make_int4(0, 0, 0, 0);
+    const int4 ry1 = (on && a.K >= 8) ? __ldcg(reinterpret_cast<const int4 *>(rowy) + 1) : make_int4(0, 0, 0, 0);
+    wn.cx = cx;
+    long long entries = cy0;
+    for (int64_t p0 = beg + 32; p0 < end; p0 += 32) {   // nodes above 32 neighbours: count the rest
+        const int64_t p = p0 + lane;
+        if (p < end) entries += __ldcg(&a.nmem[a.adj[p]]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) entries += __shfl_xor_sync(FULL, entries, o);
+    entries += cx;
+    if (d > a.warp_max_deg || entries > HW / 2) {   // the whole block evaluates it afterwards
+        if (lane == 0) {
+            const int h = atomicAdd(&es.nhub, 1);
+            es.hub[h] = i;
+            es.hub_bound[h] = entries;
+        }
+        return;
+    }
+    if (d > 32 || cx > 8) {   // general one-warp path (reloads what it needs)
+        eval_team<1>(a, i, x, d, beg, end, entries, y0, cy0, keys, vals, ubs, es.bkey[w], es.bval[w], es.ts, w, 0,
+                     serial);
+        return;
+    }
+    uint32_t H = 32;
+    while ((int64_t)H < 2 * entries) H <<= 1;
+    const uint32_t hm = H - 1;
+    for (uint32_t s = lane; s < H; s += 32) {
+        keys[s] = EMPTY_KEY;
+        vals[s] = 0u;
+    }
+    __syncwarp();
+    if (lane < cx) ht_insert(keys, vals, hm, row_entry(wn.rx0, wn.rx1, rowx, lane), 0u, true);
+    __syncwarp();
+    const int32_t cmax = __reduce_max_sync(FULL, cy0);
+    for (int s = 0; s < cmax; ++s) {
+        int32_t C = s < cy0 ? row_entry(ry0, ry1, rowy, s) : -2 - lane;
+        unsigned mask = __match_any_sync(FULL, C);
+        if (C >= 0 && lane == __ffs(mask) - 1) ht_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false);
+    }
+    unsigned long long pb = on ? 8ull + 4ull * (unsigned long long)cy0 : 0ull;
+    __syncwarp();
+    Best bj, bl;
+    decide_node<1>(a, i, d, cx, H, keys, vals, ubs, es.bkey[w], es.bval[w], es.ts, w, 0, serial, pb, bj, bl);
+    wn.j = __shfl_sync(FULL, bj.c, 0);
+    wn.kj = __shfl_sync(FULL, bj.k, 0);
+    wn.l = __shfl_sync(FULL, bl.c, 0);
+    wn.kl = __shfl_sync(FULL, bl.k, 0);
+    wn.fused = 1;
+}
+
+__device__ void apply_fused(const RunArgs &a, int64_t bstart, int32_t blen, int i, const WarpNode &wn,
+                            unsigned long long serial, unsigned long long &nj, unsigned long long &nl) {
+    if (!wn.valid) return;
+    if (!wn.fused) {
+        apply_node(a, bstart, blen, i, serial, nj, nl);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int32_t j = wn.j, l = wn.l;
+    if (j < 0 && l < 0) {
+        if (a.profile && lane == 0) atomicAdd(&a.ds->prof_bytes, 8ull);
+        return;
+    }
+    int jj = 0, jl = 0, ll = 0;
+    if (wn.py0 >= bstart && wn.py0 < bstart + blen) {
+        const int64_t iy = wn.py0 - bstart;
+        const int32_t aj = __ldcg(&a.act[iy]), al = __ldcg(&a.act[a.qcap + iy]);
+        jj = j >= 0 && aj == j;
+        jl = j >= 0 && al == j;
+        ll = l >= 0 && al == l;
+    }
+    jj = __reduce_add_sync(FULL, jj);
+    jl = __reduce_add_sync(FULL, jl);
+    ll = __reduce_add_sync(FULL, ll);
+    // new row from the registers: leave l, insert j, ascending
+    int32_t *row = a.mem + (int64_t)wn.x * a.K;
+    const int32_t c = wn.cx;
+    const int32_t v = lane < c ? row_entry(wn.rx0, wn.rx1, row, lane) : 0;
+    const bool keep = lane < c && v != l;
+    const unsigned km = __ballot_sync(FULL, keep);
+    const int kept = __popc(km);
+    int ins = kept;
+    if (j >= 0) ins = __popc(__ballot_sync(FULL, keep && v < j));
+    int32_t c_new = c;
+    if (j >= 0 && kept >= a.K) {
+        if (lane == 0) atomicOr(&a.ds->err, DERR_CAPACITY);
+    } else {
+        if (keep) {
+            const int dst = __popc(km & lanemask_lt());
+            row[dst + ((j >= 0 && dst >= ins) ? 1 : 0)] = v;
+        }
+        if (j >= 0 && lane == 0) row[ins] = j;
+        c_new = kept + (j >= 0 ? 1 : 0);
+    }
+    if (lane == 0) {
+        if (l >= 0) {
+            atomicAdd(&a.comm[l].n, -1);
+            atomicAdd(&a.comm[l].vol, (uint32_t)(-wn.d));
+            atomicAdd(&a.comm[l].m2, (uint32_t)(-2 * wn.kl + ll));
+            ++nl;
+        }
+        if (j >= 0) {
+            atomicAdd(&a.comm[j].n, 1);
+            atomicAdd(&a.comm[j].vol, (uint32_t)wn.d);
+            atomicAdd(&a.comm[j].m2, (uint32_t)(2 * wn.kj + jj - 2 * jl));
+            ++nj;
+        }
+        a.nmem[wn.x] = c_new;
+        if (a.profile)
+            atomicAdd(&a.ds->prof_bytes, 24ull + 4ull * (unsigned long long)c + 12ull * ((j >= 0) + (l >= 0)) +
+                                             16ull * (unsigned long long)wn.d);
+    }
+}
+
+template <int T>
 __global__ void __launch_bounds__(EV_THREADS, 2) k_iterate(RunArgs a, int64_t q, int64_t first, int64_t count,
-                                                        long long spin_limit, int inject_stall) {
+                                                           long long spin_limit, int inject_stall, unsigned *flags,
+                                                           unsigned epoch, int bar_mode) {
     extern __shared__ int32_t ev_dyn[];
     __shared__ EvalShared es;
     __shared__ int s_ok;
     int32_t *s_keys = ev_dyn;
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(ev_dyn + HB);
     float *s_ub = reinterpret_cast<float *>(ev_dyn + 2 * HB);
-    const int32_t kb = __ldcg(&a.ds->kb);
+    constexpr int TEAMS = EV_WARPS / T;
     const int64_t n = a.nnodes;
     const unsigned nblocks = gridDim.x;
     const int64_t warps = (int64_t)gridDim.x * EV_WARPS;
-    const int64_t gw = (int64_t)blockIdx.x * EV_WARPS + (threadIdx.x >> 5);
+    const int64_t teams = (int64_t)gridDim.x * TEAMS;
+    const int w = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * EV_WARPS + w;
     unsigned long long nj = 0, nl = 0;
     if (inject_stall && blockIdx.x == 0) return;   // test hook: a block that never arrives
+    NodePrefetch pf;
+    pf.valid = 0;
+    if (a.qtimes && blockIdx.x == 0 && threadIdx.x == 0) a.qtimes[0] = global_ns();
+    if constexpr (T == 1) {
+        if (q <= warps) {   // every queue in one round: fused evaluate + apply per warp
+            WarpNode wn;
+            for (int64_t b = first; b < first + count; ++b) {
+                const int64_t bstart = b * q;
+                const int32_t blen = (int32_t)min(q, n - bstart);
+                const unsigned long long serial = queue_serial(a, b);
+                if (threadIdx.x == 0) es.nhub = 0;
+                __syncthreads();
+                eval_fused(a, bstart, blen, (int)gw, pf, wn, s_keys + w * HW, s_vals + w * HW, s_ub + w * HW, es,
+                           serial);
+                __syncthreads();
+                const int nh = es.nhub;
+                for (int h = 0; h < nh; ++h) {
+                    const int ih = es.hub[h];
+                    eval_block(a, ih, a.order[bstart + ih], (int64_t)es.hub_bound[h], s_keys, s_vals, s_ub, es.bkey[w],
+                               es.bval[w], es.bs, serial);
+                }
+                if (!grid_sync(flags, nblocks, ++epoch, spin_limit, a.ds, &s_ok, bar_mode)) return;
+                if (b + 1 < first + count) {
+                    const int64_t nstart = (b + 1) * q;
+                    prefetch_node(a, nstart, (int32_t)min(q, n - nstart), (int)gw, 0, pf);
+                } else {
+                    pf.valid = 0;
+                }
+                apply_fused(a, bstart, blen, (int)gw, wn, serial, nj, nl);
+                if (!grid_sync(flags, nblocks, ++epoch, spin_limit, a.ds, &s_ok, bar_mode)) return;
+                if (a.qtimes && blockIdx.x == 0 && threadIdx.x == 0) a.qtimes[b - first + 1] = global_ns();
+            }
+            flush_counts(a, nj, nl);
+            return;
+        }
+    }
     for (int64_t b = first; b < first + count; ++b) {
         const int64_t bstart = b * q;
         const int32_t blen = (int32_t)min(q, n - bstart);
         const unsigned long long serial = queue_serial(a, b);
-        for (int64_t base = (int64_t)blockIdx.x * EV_WARPS; base < blen; base += warps)
-            eval_group(a, bstart, blen, (int)base, kb, serial, s_keys, s_vals, s_ub, es);
-        if (!grid_sync(a.ds, nblocks, spin_limit, &s_ok)) return;
+        const int64_t base0 = (int64_t)blockIdx.x * TEAMS;
+        for (int64_t base = base0; base < blen; base += teams)
+            eval_group<T>(a, bstart, blen, (int)base, serial, s_keys, s_vals, s_ub, es, base == base0 ? &pf : nullptr);
+        if (!grid_sync(flags, nblocks, ++epoch, spin_limit, a.ds, &s_ok, bar_mode)) return;
+        // the next queue's first node of this team: its static data loads while
+        // this queue is applied and the barrier completes
+        if (b + 1 < first + count) {
+            const int64_t nstart = (b + 1) * q;
+            prefetch_node(a, nstart, (int32_t)min(q, n - nstart), (int)(base0 + w / T), w % T, pf);
+        } else {
+            pf.valid = 0;
+        }
         for (int64_t i = gw; i < blen; i += warps) apply_node(a, bstart, blen, i, serial, nj, nl);
-        if (!grid_sync(a.ds, nblocks, spin_limit, &s_ok)) return;
+        if (!grid_sync(flags, nblocks, ++epoch, spin_limit, a.ds, &s_ok, bar_mode)) return;
+        if (a.qtimes && blockIdx.x == 0 && threadIdx.x == 0) a.qtimes[b - first + 1] = global_ns();
     }
     flush_counts(a, nj, nl);
 }
@@ -983,7 +1483,6 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.order = g->order;
     a.pos = g->pos;
     a.comm = g->comm;
-    a.stamp = g->stamp;
     a.mem = g->mem;
     a.nmem = g->nmem;
     a.K = g->K;
@@ -996,6 +1495,7 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.nnodes = g->n;
     a.warp_max_deg = g->warp_max_degree > 0 ? g->warp_max_degree : 0x7fffffff;
     a.profile = g->profile;
+    a.qtimes = g->qtimes;
     // FP32 screen: cc must be a normal float with room to spare; delta bounds
     // 15 FP32 roundings (20 ulp) and the FP32 subtraction, the FP64 estimator's error u (m2 + 3 vol +
     // 17) with m2, vol <= 2m, the two gain subtractions, and a 2% margin.
@@ -1018,15 +1518,53 @@ void record_event(lf_graph *g, cudaEvent_t e, bool capturing) {
     else LF_CUDA(cudaEventRecord(e, g->stream));
 }
 
+int num_sms() {
+    int dev = 0, sms = 0;
+    LF_CUDA(cudaGetDevice(&dev));
+    LF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return std::max(1, sms);
+}
+
+// Warps per node: as many as keep q x T warps within about 16 per SM, so that
+// small queues spread each node's loads over more warps.
+int choose_team(lf_graph *g, int64_t q) {
+    if (g->warps_per_node == 1 || g->warps_per_node == 2 || g->warps_per_node == 4 || g->warps_per_node == 8)
+        return g->warps_per_node;
+    const int64_t target = (int64_t)num_sms() * 16;
+    int T = EV_WARPS;
+    while (T > 1 && q * T > target) T >>= 1;
+    return T;
+}
+
+template <int T>
+void launch_eval(lf_graph *g, const RunArgs &a, int64_t bstart, int32_t blen, int64_t b) {
+    constexpr int teams = EV_WARPS / T;
+    k_eval<T><<<(unsigned)((blen + teams - 1) / teams), EV_THREADS, EV_DYN_SMEM, g->stream>>>(a, bstart, blen, b);
+}
+
+void set_eval_attrs() {
+    LF_CUDA(cudaFuncSetAttribute(k_eval<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_eval<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_eval<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_eval<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+}
+
 void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int64_t count,
                     bool capturing = false) {
+    const int T = choose_team(g, q);
 
     const bool prof = g->profile && (int64_t)g->prof_ev.size() >= 2 * (first + count);
     for (int64_t b = first; b < first + count; ++b) {
         const int64_t bstart = b * q;
         const int32_t blen = (int32_t)std::min<int64_t>(q, g->n - bstart);
         if (prof) record_event(g, g->prof_ev[2 * b], capturing);
-        k_eval<<<(unsigned)((blen + EV_WARPS - 1) / EV_WARPS), EV_THREADS, EV_DYN_SMEM, g->stream>>>(a, bstart, blen, b); ++g->launches;
+        switch (T) {
+        case 1: launch_eval<1>(g, a, bstart, blen, b); break;
+        case 2: launch_eval<2>(g, a, bstart, blen, b); break;
+        case 4: launch_eval<4>(g, a, bstart, blen, b); break;
+        default: launch_eval<8>(g, a, bstart, blen, b); break;
+        }
+        ++g->launches;
         if (prof) record_event(g, g->prof_ev[2 * b + 1], capturing);
         k_apply<<<grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30), AP_THREADS, 0, g->stream>>>(a, bstart, blen, b); ++g->launches;
     }
@@ -1053,9 +1591,8 @@ void ensure_capacity(lf_graph *g, int64_t q) {
     const int64_t n = g->n;
     if (!g->comm) {
         g->comm = dalloc_n<CommRec>(g, n);
-        g->stamp = dalloc_n<unsigned long long>(g, n);
         g->nmem = dalloc_n<int32_t>(g, n);
-        g->K = std::max(2, g->member_slots);
+        g->K = std::max(4, (g->member_slots + 3) / 4 * 4);   // rows start on 16-byte boundaries
         g->mem = dalloc_n<int32_t>(g, n * g->K);
     }
     if (g->qcap < q) {
@@ -1085,28 +1622,46 @@ double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
     return (double)t;
 }
 
+template <int T>
+const void *iterate_kernel() {
+    return (const void *)k_iterate<T>;
+}
+
+const void *iterate_kernel_for(int T) {
+    switch (T) {
+    case 1: return iterate_kernel<1>();
+    case 2: return iterate_kernel<2>();
+    case 4: return iterate_kernel<4>();
+    default: return iterate_kernel<8>();
+    }
+}
+
 // Blocks of the persistent queue kernel that can be resident at once.
-int persistent_grid_max(lf_graph *g) {
-    int dev = 0, sms = 0, per_sm = 0;
-    LF_CUDA(cudaGetDevice(&dev));
-    LF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    LF_CUDA(cudaFuncSetAttribute(k_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
-    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iterate, EV_THREADS, EV_DYN_SMEM));
+int persistent_grid_max(lf_graph *g, int T) {
+    int per_sm = 0;
+    const void *k = iterate_kernel_for(T);
+    LF_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, EV_THREADS, EV_DYN_SMEM));
     (void)g;
-    return std::max(1, per_sm) * std::max(1, sms);
+    return std::max(1, per_sm) * num_sms();
 }
 
 // One cooperative launch runs queues first .. first+count-1.
-void launch_persistent(lf_graph *g, RunArgs a, int64_t q, int64_t first, int64_t count, int grid_max,
+void launch_persistent(lf_graph *g, RunArgs a, int64_t q, int64_t first, int64_t count, int grid_max, int T,
                        cudaEvent_t e0, cudaEvent_t e1) {
     if (count <= 0) return;
-    const int64_t want = (q + EV_WARPS - 1) / EV_WARPS;
+    const int64_t teams = EV_WARPS / T;
+    const int64_t want = (q + teams - 1) / teams;
     unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, grid_max));
-    long long spin = (long long)g->barrier_timeout_ms * 10000ll;   // ~100 ns per wait step
+    long long spin = (long long)g->barrier_timeout_ms * 4000ll;   // >= ~250 ns per poll of the flags
     int inject = g->inject_stall;
-    void *args[] = {&a, &q, &first, &count, &spin, &inject};
+    unsigned *flags = g->bar_flags;
+    unsigned epoch = g->bar_epoch;
+    g->bar_epoch += (unsigned)(2 * count);
+    int bar_mode = g->barrier_mode;
+    void *args[] = {&a, &q, &first, &count, &spin, &inject, &flags, &epoch, &bar_mode};
     if (e0) LF_CUDA(cudaEventRecord(e0, g->stream));
-    LF_CUDA(cudaLaunchCooperativeKernel((const void *)k_iterate, dim3(grid), dim3(EV_THREADS), args, EV_DYN_SMEM,
+    LF_CUDA(cudaLaunchCooperativeKernel(iterate_kernel_for(T), dim3(grid), dim3(EV_THREADS), args, EV_DYN_SMEM,
                                         g->stream));
     ++g->launches;
     if (e1) LF_CUDA(cudaEventRecord(e1, g->stream));
@@ -1116,15 +1671,18 @@ void launch_persistent(lf_graph *g, RunArgs a, int64_t q, int64_t first, int64_t
 
 void free_run_state(lf_graph *g) {
     drop_graph(g);
+    if (g->qtimes) dfree(g, g->qtimes);
+    g->qtimes = nullptr;
+    if (g->bar_flags) dfree(g, g->bar_flags);
+    g->bar_flags = nullptr;
+    g->bar_flags_cap = 0;
     for (auto e : g->prof_ev) cudaEventDestroy(e);
     g->prof_ev.clear();
     if (g->act) dfree(g, g->act);
     if (g->mem) dfree(g, g->mem);
     if (g->nmem) dfree(g, g->nmem);
-    if (g->stamp) dfree(g, g->stamp);
     if (g->comm) dfree(g, g->comm);
     g->act = g->mem = g->nmem = nullptr;
-    g->stamp = nullptr;
     g->comm = nullptr;
     g->qcap = 0;
     g->K = 0;
@@ -1139,7 +1697,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     const int64_t n = g->n;
     const int64_t q = std::max<int64_t>(1, std::min<int64_t>(q_in, std::max<int64_t>(n, 1)));
     ensure_capacity(g, q);
-    LF_CUDA(cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+    set_eval_attrs();
     cudaEvent_t ev[3];
     for (auto &e : ev) LF_CUDA(cudaEventCreate(&e));
     struct EvGuard {
@@ -1151,7 +1709,6 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     LF_CUDA(cudaEventRecord(ev[0], st));
     // reset run state
     LF_CUDA(cudaMemsetAsync(g->comm, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(CommRec), st));
-    LF_CUDA(cudaMemsetAsync(g->stamp, 0, (size_t)std::max<int64_t>(n, 1) * 8, st));
     LF_CUDA(cudaMemsetAsync(g->nmem, 0, (size_t)std::max<int64_t>(n, 1) * 4, st));
     LF_CUDA(cudaMemsetAsync(g->ds->sacc, 0, sizeof(g->ds->sacc), st));
     {
@@ -1176,6 +1733,11 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     }
     double prof_ms = 0.0;
     int64_t prof_launches = 0;
+    double qpct[4] = {0, 0, 0, 0};
+    if (g->profile && !g->per_queue && nb_all > 0) {
+        if (g->qtimes) dfree(g, g->qtimes);
+        g->qtimes = dalloc_n<unsigned long long>(g, nb_all + 1);
+    }
 
     // ---- a6: initial clustering
     int64_t k0 = 0;
@@ -1224,7 +1786,17 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
 
     const int64_t nb = n > 0 ? (n + q - 1) / q : 0;
     const bool persistent = !g->per_queue;
-    const int grid_max = persistent ? persistent_grid_max(g) : 0;
+    const int team = choose_team(g, q);
+    const int grid_max = persistent ? persistent_grid_max(g, team) : 0;
+    if (persistent) {
+        if (g->bar_flags_cap < grid_max + 1) {
+            if (g->bar_flags) dfree(g, g->bar_flags);
+            g->bar_flags = dalloc_n<unsigned>(g, grid_max + 1);
+            g->bar_flags_cap = grid_max + 1;
+        }
+        LF_CUDA(cudaMemsetAsync(g->bar_flags, 0, (size_t)(grid_max + 1) * sizeof(unsigned), st));
+        g->bar_epoch = 0;
+    }
     cudaEvent_t pev[2] = {nullptr, nullptr};
     if (persistent && g->profile)
         for (auto &e : pev) LF_CUDA(cudaEventCreate(&e));
@@ -1245,7 +1817,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         a.nbatches = nb;
         const bool partial = max_batches >= 0 && batches + nb > max_batches;
         if (partial) {
-            if (persistent) launch_persistent(g, a, q, 0, max_batches - batches, grid_max, nullptr, nullptr);
+            if (persistent) launch_persistent(g, a, q, 0, max_batches - batches, grid_max, team, nullptr, nullptr);
             else launch_batches(g, a, q, 0, max_batches - batches);
             batches = max_batches;
             LF_CUDA(cudaStreamSynchronize(st));
@@ -1255,7 +1827,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             break;
         }
         if (persistent) {
-            launch_persistent(g, a, q, 0, nb, grid_max, pev[0], pev[1]);
+            launch_persistent(g, a, q, 0, nb, grid_max, team, pev[0], pev[1]);
             launch_iteration_end(g, a);
         } else if (g->use_graphs > 0 && max_batches < 0) {
             if (!g->iter_exec || g->graph_q != q || g->graph_K != g->K) {
@@ -1292,6 +1864,16 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         if (g->profile && persistent) {
             prof_ms += elapsed_ms(pev[0], pev[1]);
             prof_launches += 1;
+            if (g->qtimes && nb > 0) {
+                std::vector<unsigned long long> t((size_t)nb + 1);
+                LF_CUDA(cudaMemcpy(t.data(), g->qtimes, (size_t)(nb + 1) * 8, cudaMemcpyDeviceToHost));
+                std::vector<double> dt((size_t)nb);
+                for (int64_t b = 0; b < nb; ++b) dt[(size_t)b] = 1e-3 * (double)(t[(size_t)b + 1] - t[(size_t)b]);
+                std::sort(dt.begin(), dt.end());
+                const double fr[3] = {0.5, 0.9, 0.99};
+                for (int k = 0; k < 3; ++k) qpct[k] = dt[(size_t)std::min<int64_t>(nb - 1, (int64_t)(fr[k] * nb))];
+                qpct[3] = dt.back();
+            }
         } else if (g->profile) {
             for (int64_t b = 0; b < nb && !std::isnan(prof_ms); ++b) {
                 float t = 0.f;
@@ -1347,6 +1929,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             LF_CUDA(cudaMemcpy(&pbytes, &g->ds->prof_bytes, 8, cudaMemcpyDeviceToHost));
         }
         stats->prof_move_bytes = (int64_t)pbytes;
+        for (int k = 0; k < 4; ++k) stats->prof_queue_us[k] = qpct[k];
     }
 }
 

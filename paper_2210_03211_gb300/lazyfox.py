@@ -43,7 +43,8 @@ class Options(C.Structure):
                 ("member_slots", C.c_int32), ("warp_max_degree", C.c_int32),
                 ("use_graphs", C.c_int32), ("profile", C.c_int32), ("exhaustive_fp64", C.c_int32),
                 ("per_queue_launches", C.c_int32), ("barrier_timeout_ms", C.c_int32),
-                ("inject_barrier_stall", C.c_int32)]
+                ("inject_barrier_stall", C.c_int32), ("barrier_mode", C.c_int32),
+                ("warps_per_node", C.c_int32)]
 
 
 class RunStatsC(C.Structure):
@@ -54,7 +55,7 @@ class RunStatsC(C.Structure):
                 ("wcc_history", C.POINTER(C.c_double)), ("joins_history", C.POINTER(C.c_int64)),
                 ("leaves_history", C.POINTER(C.c_int64)), ("num_launches", C.c_int64),
                 ("prof_move_launches", C.c_int64), ("prof_move_ms", C.c_double),
-                ("prof_move_bytes", C.c_int64)]
+                ("prof_move_bytes", C.c_int64), ("prof_queue_us", C.c_double * 4)]
 
 
 class CreateStatsC(C.Structure):
@@ -150,6 +151,7 @@ class RunStats:
     prof_move_launches: int = 0
     prof_move_ms: float = 0.0
     prof_move_bytes: int = 0
+    prof_queue_us: tuple = (0.0, 0.0, 0.0, 0.0)
 
 
 class Graph:
@@ -163,7 +165,8 @@ class Graph:
     def __init__(self, src, dst, *, stream=None, allocator: str = "torch", member_slots: int = 0,
                  warp_max_degree: int = 0, use_graphs: bool = True, profile: bool = False,
                  exhaustive_fp64: bool = False, per_queue_launches: bool = False,
-                 barrier_timeout_ms: int = 0, inject_barrier_stall: bool = False, device=None):
+                 barrier_timeout_ms: int = 0, inject_barrier_stall: bool = False, barrier_mode: int = 0,
+                 warps_per_node: int = 0, device=None):
         import torch
         self._L = load_library()
         self._h = C.c_void_p()
@@ -193,6 +196,8 @@ class Graph:
         opt.per_queue_launches = 1 if per_queue_launches else 0
         opt.barrier_timeout_ms = int(barrier_timeout_ms)
         opt.inject_barrier_stall = 1 if inject_barrier_stall else 0
+        opt.barrier_mode = int(barrier_mode)
+        opt.warps_per_node = int(warps_per_node)
         if isinstance(src, torch.Tensor):
             if src.dtype != torch.int32 or dst.dtype != torch.int32 or not src.is_cuda:
                 raise TypeError("device edge lists must be int32 CUDA tensors")
@@ -258,7 +263,7 @@ class Graph:
         return RunStats(k, bool(st.converged), st.num_batches, st.wcc_initial, T[:k].copy(), J[:k].copy(),
                         Lv[:k].copy(), st.num_communities, st.num_memberships, st.ms_total, st.ms_init,
                         st.ms_iterations, st.num_launches, st.prof_move_launches, st.prof_move_ms,
-                        st.prof_move_bytes)
+                        st.prof_move_bytes, tuple(st.prof_queue_us))
 
     def communities(self):
         """(offsets int64[k+1], members int32[...]) in original node ids."""

@@ -268,3 +268,16 @@ def test_barrier_timeout_is_reported_and_recoverable(lf, oracle_lib):
     ref = og.run(64, 0.01, 50)
     with lf.Graph(el.src, el.dst) as g:
         compare_run(g.run(64, 0.01, 50), ref)
+
+
+@pytest.mark.parametrize("el", [CASES[-1], CASES[-2], CASES[-4], CASES[-5]], ids=[IDS[-1], IDS[-2], IDS[-4], IDS[-5]])
+@pytest.mark.parametrize("team", [1, 2, 4, 8])
+@pytest.mark.parametrize("per_queue", [False, True])
+def test_team_sizes_give_the_same_run(lf, oracle_lib, el, team, per_queue):
+    """1, 2, 4 or 8 warps per evaluated node, persistent or per-queue launches:
+    the same actions as the oracle, queue for queue."""
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(48, -math.inf, 4)
+    with lf.Graph(el.src, el.dst, warps_per_node=team, per_queue_launches=per_queue) as g:
+        compare_run(g.run(48, -math.inf, 4), ref)
+        compare_state(g, og)
