@@ -242,6 +242,33 @@ lf_status lf_get_state(lf_graph *g, int64_t *mem_offsets, int32_t *mem_ids,
 lf_status lf_run_partial(lf_graph *g, int32_t queue_size, double wcc_threshold, int32_t max_iters,
                          int64_t max_batches, lf_run_stats *stats);
 
+/*
+ * lf_triangles_noalloc -- t(x,V) and vt(x,V) for callers that cannot allocate
+ * device memory when they call: for example a program whose device memory is
+ * owned entirely by another allocator, or a latency-critical loop in which an
+ * allocation could stall or fail.  It runs the same triangle kernels as
+ * lf_graph_create but allocates nothing: the kernels' working memory (edge
+ * marks, hub list, counters) comes from one array of 16 MiB reserved
+ * statically in this library, which every GPU that loads the library holds
+ * until the process exits.  The paper has no counterpart of this call.
+ * oriented_offsets: device, num_nodes+1 int64 offsets of a degree-ordered
+ *                   orientation (as returned by lf_get_oriented): out-rows
+ *                   ascending, every undirected edge exactly once;
+ * out_neighbours  : device, num_edges int32;
+ * t, vt           : device outputs, num_nodes each (overwritten);
+ * stream          : cudaStream_t the work is queued on (NULL: legacy default).
+ * Limit: num_edges + 4 num_nodes + ~1 KiB must fit in the 16 MiB array, else
+ * LF_ERR_CAPACITY (nothing is launched).  The call returns when the work is
+ * queued; results are ready when the stream reaches them.
+ * The first call on each device looks the array up (with that device
+ * current); make that first call before any stream capture.  Every call uses
+ * the same array, which keeps the previous call's contents (the call clears
+ * what must start at zero): calls whose work overlaps on a GPU race with each
+ * other and must be ordered by the caller (e.g. one stream).
+ */
+lf_status lf_triangles_noalloc(const int64_t *oriented_offsets, const int32_t *out_neighbours,
+                               int64_t num_nodes, int64_t num_edges, int64_t *t, int32_t *vt, void *stream);
+
 /* Release every device buffer and the handle (NULL is a no-op). */
 void lf_graph_destroy(lf_graph *g);
 

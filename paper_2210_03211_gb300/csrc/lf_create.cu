@@ -6,6 +6,7 @@
 //   a4  vt(x,V) from the edge marks
 //   a5  local CC, node order (exact rational compare), global cc
 #include <cstring>
+#include <mutex>
 
 #include "lf_internal.cuh"
 
@@ -693,4 +694,96 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
     cs.num_launches = (int64_t)g->launches;
 }
 
+// ---------------------------------------------------------------------------
+// Triangle counts without any allocation.
+//
+// For callers that cannot allocate device memory at the time of the call
+// (device memory owned entirely by another allocator, or a latency-critical
+// loop where an allocation could stall or fail): the same triangle kernels as
+// lf_graph_create, with their working memory (edge marks, hub list, counters)
+// taken from one array reserved statically in this library.  Every GPU that
+// loads the library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;   // 16 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Device address of the array on the current device (the host-side symbol is
+// only a stand-in), looked up once per device with that device current.
+unsigned char *noalloc_scratch() {
+    int dev = 0;
+    LF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) fail(LF_ERR_CAPACITY, "device %d beyond %d", dev, NOALLOC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        LF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        LF_CUDA(cudaFuncSetAttribute(k_tri_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)((size_t)TRI_BLOCK_LIST * 9)));
+        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
+size_t noalloc_scratch_needed(int64_t n, int64_t m) {
+    return round256(sizeof(DevScalars)) + 256 + round256((size_t)n * sizeof(int32_t)) + round256((size_t)m);
+}
+
+void triangles_noalloc(const int64_t *ooff, const int32_t *oadj, int64_t n, int64_t m, int64_t *t, int32_t *vt,
+                       cudaStream_t st) {
+    if (n < 0 || m < 0) fail(LF_ERR_INVALID, "negative size (n=%lld, m=%lld)", (long long)n, (long long)m);
+    const size_t need = noalloc_scratch_needed(n, m);
+    if (need > NOALLOC_SCRATCH_BYTES)
+        fail(LF_ERR_CAPACITY,
+             "graph too large for the static scratch: needs %zu bytes (m + 4n + %zu), limit %zu bytes (16 MiB)", need,
+             round256(sizeof(DevScalars)) + 256, NOALLOC_SCRATCH_BYTES);
+    if (n > 0 && (!ooff || !t || !vt)) fail(LF_ERR_INVALID, "NULL device pointer");
+    if (m > 0 && !oadj) fail(LF_ERR_INVALID, "NULL device pointer");
+    unsigned char *base = noalloc_scratch();
+    DevScalars *ds = reinterpret_cast<DevScalars *>(base);
+    uint32_t *nh = reinterpret_cast<uint32_t *>(base + round256(sizeof(DevScalars)));
+    int32_t *hubs = reinterpret_cast<int32_t *>(base + round256(sizeof(DevScalars)) + 256);
+    uint8_t *sup = base + round256(sizeof(DevScalars)) + 256 + round256((size_t)n * sizeof(int32_t));
+    // the array keeps the previous call's contents: clear what must start at zero
+    LF_CUDA(cudaMemsetAsync(ds, 0, sizeof(DevScalars), st));
+    LF_CUDA(cudaMemsetAsync(nh, 0, sizeof(uint32_t), st));
+    if (m > 0) LF_CUDA(cudaMemsetAsync(sup, 0, (size_t)m, st));
+    if (n == 0) return;
+    LF_CUDA(cudaMemsetAsync(t, 0, (size_t)n * sizeof(int64_t), st));
+    LF_CUDA(cudaMemsetAsync(vt, 0, (size_t)n * sizeof(int32_t), st));
+    unsigned long long *utri = reinterpret_cast<unsigned long long *>(t);
+    k_select_hubs<<<grid_for(n, 256, 8192), 256, 0, st>>>(ooff, n, hubs, nh);
+    LF_LAUNCHED();
+    k_tri_warp<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(ooff, oadj, n, utri, sup, ds);
+    LF_LAUNCHED();
+    k_tri_block<<<304, TRI_BLOCK_THREADS, (size_t)TRI_BLOCK_LIST * 9, st>>>(ooff, oadj, hubs, nh, utri, sup, ds);
+    LF_LAUNCHED();
+    k_vt<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(ooff, oadj, sup, n, vt, ds);
+    LF_LAUNCHED();
+}
+
 }  // namespace lf
+
+extern "C" lf_status lf_triangles_noalloc(const int64_t *oriented_offsets, const int32_t *out_neighbours,
+                                          int64_t num_nodes, int64_t num_edges, int64_t *t, int32_t *vt,
+                                          void *stream) {
+    try {
+        lf::triangles_noalloc(oriented_offsets, out_neighbours, num_nodes, num_edges, t, vt,
+                              static_cast<cudaStream_t>(stream));
+        return LF_OK;
+    } catch (const lf::Error &e) {
+        return e.status;
+    } catch (...) {
+        lf::set_error(LF_ERR_CUDA, "unexpected internal error");
+        return LF_ERR_CUDA;
+    }
+}

@@ -24,7 +24,7 @@ _STATUS = {1: "LF_ERR_INVALID", 2: "LF_ERR_OOM", 3: "LF_ERR_CUDA", 4: "LF_ERR_CA
 ABI_FUNCTIONS = ("lf_graph_create", "lf_run", "lf_run_partial", "lf_get_communities",
                  "lf_get_node_stats", "lf_get_sizes", "lf_get_create_stats", "lf_get_csr",
                  "lf_get_oriented", "lf_get_order", "lf_get_state", "lf_graph_destroy",
-                 "lf_last_error")
+                 "lf_last_error", "lf_triangles_noalloc")
 
 
 class LazyFoxError(RuntimeError):
@@ -93,6 +93,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "lf_get_state": (C.c_int, [P, i64p, i32p, i64p, i64p, i64p, i64p, i64p]),
         "lf_graph_destroy": (None, [P]),
         "lf_last_error": (C.c_char_p, []),
+        "lf_triangles_noalloc": (C.c_int, [P, P, C.c_int64, C.c_int64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
