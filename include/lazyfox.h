@@ -69,9 +69,11 @@ typedef struct lf_options {
                                 and count its algorithmic bytes (lf_run_stats.prof_*) */
     int32_t exhaustive_fp64; /* 1: evaluate every candidate gain in FP64 (no FP32 screen);
                                 the chosen actions are the same either way */
-    int32_t per_queue_launches; /* 0 (default): one persistent cooperative kernel per
-                                iteration runs every queue (evaluate, grid barrier, apply,
-                                grid barrier); 1: two kernel launches per queue */
+    int32_t per_queue_launches; /* 1: kernel launches per queue (evaluate, apply), an
+                                iteration captured in a CUDA graph; 2: one persistent
+                                cooperative kernel per iteration runs every queue
+                                (evaluate, grid barrier, apply, grid barrier); 0 (default):
+                                persistent for queues of at most 256 nodes, else per queue */
     int32_t barrier_timeout_ms; /* bound on one grid-barrier wait (0: 2000 ms); a wait that
                                 runs out ends the call with LF_ERR_TIMEOUT */
     int32_t inject_barrier_stall; /* test hook: 1 makes one block of the persistent kernel

@@ -173,7 +173,7 @@ lf_status lf_graph_create(const int32_t *src, const int32_t *dst, int64_t num_ed
             g->use_graphs = opt->use_graphs < 0 ? 0 : 1;
             g->profile = opt->profile == 1 ? 1 : 0;
             g->screen = opt->exhaustive_fp64 == 1 ? 0 : 1;
-            g->per_queue = opt->per_queue_launches == 1 ? 1 : 0;
+            g->per_queue = opt->per_queue_launches == 1 ? 1 : (opt->per_queue_launches == 2 ? 0 : -1);
             if (opt->barrier_timeout_ms > 0) g->barrier_timeout_ms = opt->barrier_timeout_ms;
             g->inject_stall = opt->inject_barrier_stall == 1 ? 1 : 0;
             g->barrier_mode = opt->barrier_mode == 1 ? 1 : 0;

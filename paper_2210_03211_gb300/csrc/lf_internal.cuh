@@ -100,7 +100,7 @@ struct lf_graph {
     int32_t use_graphs = 1;
     int32_t profile = 0;
     int32_t screen = 1;                            // FP32 candidate screen in the move evaluation
-    int32_t per_queue = 0;                         // 1: kernel launches per queue instead of the persistent loop
+    int32_t per_queue = -1;                        // 1: launches per queue, 0: persistent loop, -1: by queue size
     int32_t barrier_timeout_ms = 2000;
     int32_t inject_stall = 0;
     int32_t barrier_mode = 0;                      // grid barrier: 0 flat flags, 1 central release flag
@@ -145,6 +145,16 @@ struct lf_graph {
     int bar_flags_cap = 0;
     unsigned bar_epoch = 0;
     unsigned long long *qtimes = nullptr;          // profile mode: per-queue time stamps
+    // hubs evaluated with global-memory tables (plan for queue size hub_plan_q, row capacity hub_plan_K)
+    int32_t *hub_pos = nullptr;
+    int64_t *hub_qoff = nullptr;
+    int64_t *hub_toff = nullptr;
+    uint32_t *hub_tcap = nullptr;
+    int32_t *hub_scratch = nullptr;
+    int64_t hub_slots = 0;
+    std::vector<int64_t> hub_qoff_host;
+    int64_t hub_plan_q = 0;
+    int32_t hub_plan_K = 0;
 };
 
 namespace lf {

@@ -21,6 +21,7 @@ constexpr int EV_THREADS = EV_WARPS * 32;
 constexpr int HW = 512;              // hash slots of one warp
 constexpr int HB = EV_WARPS * HW;    // hash slots of a block (hub nodes)
 constexpr int AP_THREADS = 256;
+constexpr int32_t HUGE_DEG = 384;   // nodes above this degree get a global-memory table
 constexpr size_t EV_DYN_SMEM = (size_t)HB * 16;   // keys, counts, upper and lower screen bounds
 
 struct RunArgs {
@@ -42,6 +43,18 @@ struct RunArgs {
     int64_t nnodes;
     int32_t warp_max_deg;
     int32_t profile;   // count algorithmic bytes of the move evaluation
+    // hubs: nodes of degree > huge_deg are evaluated one block each with a
+    // hash table in global memory (hkeys/hvals/hub_ub/hub_lb at hub_toff[h]),
+    // listed per queue: hub_pos[hub_qoff[b] .. hub_qoff[b+1]) are positions
+    int32_t huge_deg;
+    const int32_t *hub_pos;
+    const int64_t *hub_qoff;
+    const int64_t *hub_toff;
+    const uint32_t *hub_tcap;
+    int32_t *hkeys;
+    uint32_t *hvals;
+    float *hub_ub;
+    float *hub_lb;
     unsigned long long *qtimes;   // profile mode: time stamp after each queue (persistent kernel)
     int32_t screen;    // 1: rule candidates out with the FP32 bound first
     float cc32;        // cc rounded to float (screen)
@@ -643,13 +656,15 @@ struct BlockScratch {
 // hash and each part is counted in the block's table in its own pass; if a
 // pass overflows the table, P doubles and the evaluation restarts.
 __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, int32_t *keys, uint32_t *vals,
-                           float *ubs, int32_t *bkey, uint32_t *bval, BlockScratch &bs, unsigned long long serial) {
+                           float *ubs, int32_t *bkey, uint32_t *bval, BlockScratch &bs, unsigned long long serial,
+                           float *lbs = nullptr, uint32_t hcap = HB) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int32_t d = a.deg[x];
     const int32_t cx = __ldcg(&a.nmem[x]);
     const int32_t *rowx = a.mem + (int64_t)x * a.K;
     const int64_t beg = a.off[x], end = a.off[x + 1];
-    int P = bound <= HB / 2 ? 1 : (int)((bound + HB / 4 - 1) / (HB / 4));
+    if (!lbs) lbs = ubs + HB;
+    int P = bound <= hcap / 2 ? 1 : (int)((bound + hcap / 4 - 1) / (hcap / 4));
     Best bj, bl;
     unsigned long long pb = 0;
     for (;;) {
@@ -658,7 +673,7 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
         pb = 0;
         // running best lower bounds over the parts seen so far
         float lbj = -INFINITY, lbl = -INFINITY;
-        uint32_t H = HB;
+        uint32_t H = hcap;
         if (P == 1) {
             H = 32;
             while ((int64_t)H < 2 * bound) H <<= 1;
@@ -710,7 +725,7 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
             const uint32_t lo = min(H, (uint32_t)w * slice), hi = min(H, lo + slice);
             if (a.screen) {
                 float wj = lbj, wl = lbl;
-                screen_bounds(a, keys, vals, ubs, ubs + HB, lo, hi, d, wj, wl);
+                screen_bounds(a, keys, vals, ubs, lbs, lo, hi, d, wj, wl);
                 wj = warp_max_f(wj);
                 wl = warp_max_f(wl);
                 if (lane == 0) {
@@ -758,6 +773,35 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
     __syncthreads();
 }
 
+// The hubs of queue b, one block each (block-strided), each with its own
+// hash table in global memory sized for (d+1) x K entries when the run was
+// planned: one pass over the neighbours however many distinct communities
+// they bring.
+__device__ void eval_huge(const RunArgs &a, int64_t bstart, int64_t b, unsigned long long serial, int32_t *bkey,
+                          uint32_t *bval, BlockScratch &bs) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ long long s_entries[EV_WARPS];
+    if (!a.hub_qoff) return;
+    for (int64_t h = a.hub_qoff[b] + blockIdx.x; h < a.hub_qoff[b + 1]; h += gridDim.x) {
+        const int64_t p = a.hub_pos[h];
+        const int32_t x = a.order[p];
+        const int64_t beg = a.off[x], end = a.off[x + 1];
+        long long e = 0;
+        for (int64_t q = beg + threadIdx.x; q < end; q += EV_THREADS) e += __ldcg(&a.nmem[a.adj[q]]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(FULL, e, o);
+        if (lane == 0) s_entries[w] = e;
+        __syncthreads();
+        long long entries = __ldcg(&a.nmem[x]);
+        for (int k = 0; k < EV_WARPS; ++k) entries += s_entries[k];
+        __syncthreads();
+        const int64_t t0 = a.hub_toff[h];
+        const uint32_t cap = a.hub_tcap[h];
+        eval_block(a, (int)(p - bstart), x, entries, a.hkeys + t0, a.hvals + t0, a.hub_ub + t0, bkey, bval, bs, serial,
+                   a.hub_lb + t0, cap);
+    }
+}
+
 struct EvalShared {
     int32_t hub[EV_WARPS];
     long long hub_bound[EV_WARPS];
@@ -802,10 +846,16 @@ __device__ void eval_group(const RunArgs &a, int64_t bstart, int32_t blen, int b
     if (threadIdx.x == 0) es.nhub = 0;
     __syncthreads();
     const int i = base + tm;
-    if (i < blen) {
+    bool mine = i < blen;
+    int32_t x = 0, d = 0;
+    if (mine) {
         const bool have = pf && pf->valid;
-        const int32_t x = have ? pf->x : a.order[bstart + i];
-        const int32_t d = have ? pf->d : a.deg[x];
+        x = have ? pf->x : a.order[bstart + i];
+        d = have ? pf->d : a.deg[x];
+        mine = d <= a.huge_deg;   // hubs are evaluated by eval_huge
+    }
+    if (mine) {
+        const bool have = pf && pf->valid;
         const int64_t beg = have ? pf->beg : a.off[x], end = have ? pf->end : a.off[x + 1];
         // exact number of entries the histogram will receive
         int32_t y0 = 0, c0 = 0;
@@ -855,6 +905,14 @@ __device__ void eval_group(const RunArgs &a, int64_t bstart, int32_t blen, int b
 
 __device__ __forceinline__ unsigned long long queue_serial(const RunArgs &a, int64_t bidx) {
     return (unsigned long long)__ldcg(&a.ds->iter) * (unsigned long long)a.nbatches + (unsigned long long)bidx + 1ull;
+}
+
+__global__ void __launch_bounds__(EV_THREADS) k_eval_huge(RunArgs a, int64_t bstart, int64_t bidx) {
+    __shared__ BlockScratch bs;
+    __shared__ int32_t bkey[EV_WARPS][32];
+    __shared__ uint32_t bval[EV_WARPS][32];
+    const int w = threadIdx.x >> 5;
+    eval_huge(a, bstart, bidx, queue_serial(a, bidx), bkey[w], bval[w], bs);
 }
 
 template <int T>
@@ -1108,6 +1166,7 @@ __device__ void eval_fused(const RunArgs &a, int64_t bstart, int32_t blen, int i
     const bool have = pf.valid != 0;
     const int32_t x = have ? pf.x : a.order[bstart + i];
     const int32_t d = have ? pf.d : a.deg[x];
+    if (d > a.huge_deg) return;   // evaluated by eval_huge; applied by the general path
     const int64_t beg = have ? pf.beg : a.off[x], end = have ? pf.end : a.off[x + 1];
     wn.x = x;
     wn.d = d;
@@ -1267,6 +1326,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_iterate(RunArgs a, int64_t q,
                 const int64_t bstart = b * q;
                 const int32_t blen = (int32_t)min(q, n - bstart);
                 const unsigned long long serial = queue_serial(a, b);
+                eval_huge(a, bstart, b, serial, es.bkey[w], es.bval[w], es.bs);
                 if (threadIdx.x == 0) es.nhub = 0;
                 __syncthreads();
                 eval_fused(a, bstart, blen, (int)gw, pf, wn, s_keys + w * HW, s_vals + w * HW, s_ub + w * HW, es,
@@ -1298,6 +1358,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_iterate(RunArgs a, int64_t q,
         const int32_t blen = (int32_t)min(q, n - bstart);
         const unsigned long long serial = queue_serial(a, b);
         const int64_t base0 = (int64_t)blockIdx.x * TEAMS;
+        eval_huge(a, bstart, b, serial, es.bkey[w], es.bval[w], es.bs);
         for (int64_t base = base0; base < blen; base += teams)
             eval_group<T>(a, bstart, blen, (int)base, serial, s_keys, s_vals, s_ub, es, base == base0 ? &pf : nullptr);
         if (!grid_sync(flags, nblocks, ++epoch, spin_limit, a.ds, &s_ok, bar_mode)) return;
@@ -1496,6 +1557,15 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.warp_max_deg = g->warp_max_degree > 0 ? g->warp_max_degree : 0x7fffffff;
     a.profile = g->profile;
     a.qtimes = g->qtimes;
+    a.huge_deg = g->hub_qoff ? HUGE_DEG : 0x7fffffff;
+    a.hub_pos = g->hub_pos;
+    a.hub_qoff = g->hub_qoff;
+    a.hub_toff = g->hub_toff;
+    a.hub_tcap = g->hub_tcap;
+    a.hkeys = g->hub_scratch;
+    a.hvals = reinterpret_cast<uint32_t *>(g->hub_scratch + g->hub_slots);
+    a.hub_ub = reinterpret_cast<float *>(g->hub_scratch + 2 * g->hub_slots);
+    a.hub_lb = reinterpret_cast<float *>(g->hub_scratch + 3 * g->hub_slots);
     // FP32 screen: cc must be a normal float with room to spare; delta bounds
     // 15 FP32 roundings (20 ulp) and the FP32 subtraction, the FP64 estimator's error u (m2 + 3 vol +
     // 17) with m2, vol <= 2m, the two gain subtractions, and a 2% margin.
@@ -1558,6 +1628,11 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
         const int64_t bstart = b * q;
         const int32_t blen = (int32_t)std::min<int64_t>(q, g->n - bstart);
         if (prof) record_event(g, g->prof_ev[2 * b], capturing);
+        const int64_t nh = g->hub_qoff_host.empty() ? 0 : g->hub_qoff_host[(size_t)b + 1] - g->hub_qoff_host[(size_t)b];
+        if (nh > 0) {
+            k_eval_huge<<<(unsigned)nh, EV_THREADS, 0, g->stream>>>(a, bstart, b);
+            ++g->launches;
+        }
         switch (T) {
         case 1: launch_eval<1>(g, a, bstart, blen, b); break;
         case 2: launch_eval<2>(g, a, bstart, blen, b); break;
@@ -1667,10 +1742,80 @@ void launch_persistent(lf_graph *g, RunArgs a, int64_t q, int64_t first, int64_t
     if (e1) LF_CUDA(cudaEventRecord(e1, g->stream));
 }
 
+void free_hub_plan(lf_graph *g) {
+    if (g->hub_pos) dfree(g, g->hub_pos);
+    if (g->hub_qoff) dfree(g, g->hub_qoff);
+    if (g->hub_toff) dfree(g, g->hub_toff);
+    if (g->hub_tcap) dfree(g, g->hub_tcap);
+    if (g->hub_scratch) dfree(g, g->hub_scratch);
+    g->hub_pos = nullptr;
+    g->hub_qoff = nullptr;
+    g->hub_toff = nullptr;
+    g->hub_tcap = nullptr;
+    g->hub_scratch = nullptr;
+    g->hub_slots = 0;
+    g->hub_qoff_host.clear();
+    g->hub_plan_q = 0;
+    g->hub_plan_K = 0;
+}
+
+// Static per-run plan of the hubs (degree > HUGE_DEG): their positions per
+// queue and a table of pow2 >= 2 (d+1) K slots each (K bounds every row, so
+// (d+1) K bounds the entries).  Queues run one after the other, so the
+// tables of every queue share one scratch area.
+void build_hub_plan(lf_graph *g, int64_t q) {
+    if (g->hub_plan_q == q && g->hub_plan_K == g->K) return;
+    free_hub_plan(g);
+    g->hub_plan_q = q;
+    g->hub_plan_K = g->K;
+    const int64_t n = g->n;
+    if (n == 0 || g->max_deg <= HUGE_DEG) return;
+    std::vector<int32_t> order((size_t)n), deg((size_t)n);
+    LF_CUDA(cudaMemcpyAsync(order.data(), g->order, (size_t)n * 4, cudaMemcpyDeviceToHost, g->stream));
+    LF_CUDA(cudaMemcpyAsync(deg.data(), g->deg, (size_t)n * 4, cudaMemcpyDeviceToHost, g->stream));
+    LF_CUDA(cudaStreamSynchronize(g->stream));
+    const int64_t nb = (n + q - 1) / q;
+    std::vector<int32_t> pos;
+    std::vector<int64_t> qoff((size_t)nb + 1, 0), toff;
+    std::vector<uint32_t> tcap;
+    int64_t slots = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        qoff[(size_t)b] = (int64_t)pos.size();
+        int64_t used = 0;
+        for (int64_t p = b * q; p < std::min(n, (b + 1) * q); ++p) {
+            const int32_t d = deg[(size_t)order[(size_t)p]];
+            if (d <= HUGE_DEG) continue;
+            uint64_t cap = 32;
+            while (cap < 2ull * (uint64_t)(d + 1) * (uint64_t)g->K) cap <<= 1;
+            pos.push_back((int32_t)p);
+            toff.push_back(used);
+            tcap.push_back((uint32_t)cap);
+            used += (int64_t)cap;
+        }
+        slots = std::max(slots, used);
+    }
+    qoff[(size_t)nb] = (int64_t)pos.size();
+    g->hub_qoff_host = qoff;
+    if (pos.empty()) return;
+    const int64_t H = (int64_t)pos.size();
+    g->hub_pos = dalloc_n<int32_t>(g, H);
+    g->hub_qoff = dalloc_n<int64_t>(g, nb + 1);
+    g->hub_toff = dalloc_n<int64_t>(g, H);
+    g->hub_tcap = dalloc_n<uint32_t>(g, H);
+    g->hub_scratch = dalloc_n<int32_t>(g, 4 * slots);
+    g->hub_slots = slots;
+    LF_CUDA(cudaMemcpyAsync(g->hub_pos, pos.data(), (size_t)H * 4, cudaMemcpyHostToDevice, g->stream));
+    LF_CUDA(cudaMemcpyAsync(g->hub_qoff, qoff.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice, g->stream));
+    LF_CUDA(cudaMemcpyAsync(g->hub_toff, toff.data(), (size_t)H * 8, cudaMemcpyHostToDevice, g->stream));
+    LF_CUDA(cudaMemcpyAsync(g->hub_tcap, tcap.data(), (size_t)H * 4, cudaMemcpyHostToDevice, g->stream));
+    LF_CUDA(cudaStreamSynchronize(g->stream));
+}
+
 }  // namespace
 
 void free_run_state(lf_graph *g) {
     drop_graph(g);
+    free_hub_plan(g);
     if (g->qtimes) dfree(g, g->qtimes);
     g->qtimes = nullptr;
     if (g->bar_flags) dfree(g, g->bar_flags);
@@ -1723,7 +1868,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     RunArgs a = make_args(g, device_readback(g));
     const unsigned long long launches0 = g->launches;
     const int64_t nb_all = n > 0 ? (n + q - 1) / q : 0;
-    if (g->profile && g->per_queue && (int64_t)g->prof_ev.size() < 2 * nb_all) {
+    if (g->profile && (int64_t)g->prof_ev.size() < 2 * nb_all) {
         drop_graph(g);   // a captured graph would not record the new events
         while ((int64_t)g->prof_ev.size() < 2 * nb_all) {
             cudaEvent_t e;
@@ -1734,7 +1879,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     double prof_ms = 0.0;
     int64_t prof_launches = 0;
     double qpct[4] = {0, 0, 0, 0};
-    if (g->profile && !g->per_queue && nb_all > 0) {
+    if (g->profile && nb_all > 0) {
         if (g->qtimes) dfree(g, g->qtimes);
         g->qtimes = dalloc_n<unsigned long long>(g, nb_all + 1);
     }
@@ -1785,7 +1930,9 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     g->ran = true;
 
     const int64_t nb = n > 0 ? (n + q - 1) / q : 0;
-    const bool persistent = !g->per_queue;
+    // measured on GB300: the persistent loop wins for small queues (grid
+    // barriers over few blocks), launches per queue for large ones
+    const bool persistent = g->per_queue == 0 || (g->per_queue < 0 && q <= 256);
     const int team = choose_team(g, q);
     const int grid_max = persistent ? persistent_grid_max(g, team) : 0;
     if (persistent) {
@@ -1813,6 +1960,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     unsigned long long last_live = (unsigned long long)k0, last_memb = (unsigned long long)n;
     for (int32_t it = 1; it <= max_iters; ++it) {
         if (maxcnt + 1 > g->K) grow_rows(g, maxcnt + 1);
+        build_hub_plan(g, q);
         a = make_args(g, device_readback(g));
         a.nbatches = nb;
         const bool partial = max_batches >= 0 && batches + nb > max_batches;

@@ -165,7 +165,7 @@ class Graph:
 
     def __init__(self, src, dst, *, stream=None, allocator: str = "torch", member_slots: int = 0,
                  warp_max_degree: int = 0, use_graphs: bool = True, profile: bool = False,
-                 exhaustive_fp64: bool = False, per_queue_launches: bool = False,
+                 exhaustive_fp64: bool = False, per_queue_launches: bool | None = None,
                  barrier_timeout_ms: int = 0, inject_barrier_stall: bool = False, barrier_mode: int = 0,
                  warps_per_node: int = 0, device=None):
         import torch
@@ -194,7 +194,8 @@ class Graph:
         opt.use_graphs = 0 if use_graphs else -1
         opt.profile = 1 if profile else 0
         opt.exhaustive_fp64 = 1 if exhaustive_fp64 else 0
-        opt.per_queue_launches = 1 if per_queue_launches else 0
+        # True: launches per queue; False: persistent loop; None: by queue size
+        opt.per_queue_launches = 0 if per_queue_launches is None else (1 if per_queue_launches else 2)
         opt.barrier_timeout_ms = int(barrier_timeout_ms)
         opt.inject_barrier_stall = 1 if inject_barrier_stall else 0
         opt.barrier_mode = int(barrier_mode)

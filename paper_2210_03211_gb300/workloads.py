@@ -172,7 +172,8 @@ def _powerlaw_sizes(s: Stream, lo: int, hi: int, tau: float, total: int) -> np.n
 def planted_chung_lu(n: int, avg_degree: float, gamma: float, max_degree: float,
                      size_lo: int, size_hi: int, seed: int, tau: float = 2.0,
                      r_probs=(0.55, 0.25, 0.13, 0.07), mu: float = 0.3,
-                     sparse_ids: bool = True, name: str = "planted_chung_lu") -> EdgeList:
+                     sparse_ids: bool = True, name: str = "planted_chung_lu",
+                     max_fill: float | None = None) -> EdgeList:
     """Chung-Lu power-law graph with planted overlapping communities.
 
     Node weights w_i ~ (i + 1)^(-1/(gamma-1)), scaled to mean ``avg_degree``
@@ -181,8 +182,8 @@ def planted_chung_lu(n: int, avg_degree: float, gamma: float, max_degree: float,
     sizes follow a power law with exponent ``tau`` on [size_lo, size_hi].  A
     fraction 1-mu of the edge endpoints is drawn inside communities, each
     endpoint with probability proportional to w_v / r_v among the
-    community's members; the remaining fraction mu is a global Chung-Lu
-    background.  Duplicate edges and self-loops are left in; the method's
+    community's members (at most ``max_fill`` x its pairs, if given); the
+    remaining fraction mu is a global Chung-Lu background.  Duplicate edges and self-loops are left in; the method's
     preprocessing removes them.
     """
     s = Stream(seed, 11)
@@ -219,7 +220,10 @@ def planted_chung_lu(n: int, avg_degree: float, gamma: float, max_degree: float,
     e_intra = (1.0 - mu) * target_edges * A / A.sum()
     # integer edge budgets with a random rounding
     e_c = np.floor(e_intra + s.uniform(num_comms)).astype(np.int64)
-    e_c = np.where(ends - starts >= 2, e_c, 0)
+    sz = (ends - starts).astype(np.int64)
+    if max_fill is not None:   # keep small communities from saturating (their draws would repeat)
+        e_c = np.minimum(e_c, np.floor(max_fill * sz * (sz - 1) / 2.0).astype(np.int64))
+    e_c = np.where(sz >= 2, e_c, 0)
     n_in = int(e_c.sum())
     comm_of_edge = np.repeat(np.arange(num_comms, dtype=np.int64), e_c)
 
@@ -288,8 +292,10 @@ def large_like(seed: int = 4, scale: float = 1.0) -> EdgeList:
     """3.07M nodes, ~117M edges, degree exponent 2.2, max degree ~33k,
     planted community sizes 10-5,000 (queue sizes 1024, 65536; 20 iterations)."""
     n = max(1000, int(round(3_070_000 * scale)))
-    return planted_chung_lu(n, avg_degree=82.0, gamma=2.2, max_degree=33_000.0,
-                            size_lo=10, size_hi=5000, seed=seed, name="large_like")
+    # weight cap above the target maximum degree: a hub's weight is split over
+    # saturated communities and the background, realising ~32k neighbours
+    return planted_chung_lu(n, avg_degree=136.0, gamma=2.2, max_degree=95_000.0,
+                            size_lo=10, size_hi=5000, seed=seed, name="large_like", max_fill=0.5)
 
 
 # --- small graphs for tests ---------------------------------------------------

@@ -1,0 +1,53 @@
+"""Host-side multi-rank logic of bench.py (replicas; max of times and sum of
+units over ranks) on two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, results):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+    r, w, _ = bench.dist_setup(False)
+    assert (r, w) == (rank, world)
+    local_ms = 100.0 + 50.0 * rank          # rank 1 is slower
+    local_units = 1000.0 * (rank + 1)
+    total_ms = bench.reduce_max(local_ms, w, torch.device("cpu"))
+    units = bench.reduce_sum(local_units, w, torch.device("cpu"))
+    bench.barrier(w)
+    results[rank] = (total_ms, units)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_max_time_and_the_total_units():
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        results = mgr.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_rank_main, args=(r, 2, port, results)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        assert results[0] == results[1] == (150.0, 3000.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    args = type("A", (), dict(steps=1, warmup=0, gpus=2))()
+    assert bench.run_reference(args, bench.WORKLOADS["eu"], 1) == 0
+    assert capsys.readouterr().out == ""

@@ -245,11 +245,11 @@ def test_fp32_screen_changes_no_decision(lf, oracle_lib, el):
 @pytest.mark.parametrize("el", [CASES[-1], CASES[-2], CASES[-4], CASES[1]], ids=[IDS[-1], IDS[-2], IDS[-4], IDS[1]])
 @pytest.mark.parametrize("q", [1, 64, 4096])
 def test_persistent_loop_equals_per_queue_launches(lf, oracle_lib, el, q):
-    """The persistent queue kernel (default) and two launches per queue give
+    """The persistent queue kernel and two launches per queue give
     the oracle's run, queue for queue."""
     og = oracle_lib.OracleGraph(el.src, el.dst)
     ref = og.run(q, 0.01, 50)
-    with lf.Graph(el.src, el.dst, per_queue_launches=True) as g1, lf.Graph(el.src, el.dst) as g2:
+    with lf.Graph(el.src, el.dst, per_queue_launches=True) as g1, lf.Graph(el.src, el.dst, per_queue_launches=False) as g2:
         compare_run(g1.run(q, 0.01, 50), ref)
         compare_run(g2.run(q, 0.01, 50), ref)
         compare_state(g2, og)
@@ -260,7 +260,7 @@ def test_barrier_timeout_is_reported_and_recoverable(lf, oracle_lib):
     of the test through an option) makes every bounded wait run out: the call
     returns LF_ERR_TIMEOUT instead of hanging, and the GPU stays usable."""
     el = W.eu_core_like(seed=6)
-    with lf.Graph(el.src, el.dst, inject_barrier_stall=True, barrier_timeout_ms=50) as g:
+    with lf.Graph(el.src, el.dst, inject_barrier_stall=True, barrier_timeout_ms=50, per_queue_launches=False) as g:
         with pytest.raises(lf.LazyFoxError) as ei:
             g.run(64, 0.01, 5)
         assert ei.value.status == lf.LF_ERR_TIMEOUT
@@ -281,3 +281,80 @@ def test_team_sizes_give_the_same_run(lf, oracle_lib, el, team, per_queue):
     with lf.Graph(el.src, el.dst, warps_per_node=team, per_queue_launches=per_queue) as g:
         compare_run(g.run(48, -math.inf, 4), ref)
         compare_state(g, og)
+
+
+@pytest.mark.parametrize("q", [1024, 65536])
+def test_large_shape_scaled_parity(lf, oracle_lib, q):
+    """The 3.07M-node workload's shape (Chung-Lu exponent 2.2, community sizes
+    10-5,000, heavy hubs) at 2% scale, at the large queue sizes, 20 iterations
+    without early stop: every output equal to the oracle's."""
+    el = W.large_like(scale=0.02)
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(q, -math.inf, 20)
+    with lf.Graph(el.src, el.dst) as g:
+        compare_preprocessing(g, og)
+        compare_run(g.run(q, -math.inf, 20), ref)
+        compare_state(g, og)
+
+
+def _recount(off, adj, s):
+    """n_C, m_C and vol_C recounted from memberships (numpy, any size)."""
+    n = off.shape[0] - 1
+    k = s["n"].shape[0]
+    cnt = np.diff(s["mem_off"])
+    node_of = np.repeat(np.arange(n), cnt)
+    deg = np.diff(off)
+    n_c = np.bincount(s["mem_ids"], minlength=k)
+    vol_c = np.bincount(s["mem_ids"], weights=deg[node_of], minlength=k).astype(np.int64)
+    # internal edges: pairs (x, y) adjacent with a common community, counted per community
+    key = node_of.astype(np.int64) * (k + 1) + s["mem_ids"]
+    order = np.argsort(key)
+    key = key[order]
+    src = np.repeat(np.arange(n), deg)
+    m2 = np.zeros(k, np.int64)
+    for lo in range(0, n, 200_000):   # node blocks keep memory bounded
+        hi = min(n, lo + 200_000)
+        e0, e1 = off[lo], off[hi]
+        xs, ys = src[e0:e1], adj[e0:e1]
+        a0, a1 = s["mem_off"][xs], s["mem_off"][xs + 1]
+        reps = a1 - a0
+        xi = np.repeat(np.arange(xs.shape[0]), reps)
+        cs = s["mem_ids"][np.repeat(a0, reps) + (np.arange(reps.sum()) - np.repeat(np.cumsum(reps) - reps, reps))]
+        q = ys[xi].astype(np.int64) * (k + 1) + cs
+        hit = np.searchsorted(key, q)
+        ok = (hit < key.shape[0]) & (key[np.minimum(hit, key.shape[0] - 1)] == q)
+        m2 += np.bincount(cs[ok], minlength=k)
+    return n_c, m2 // 2, vol_c
+
+
+@pytest.mark.skipif(not __import__("os").environ.get("LF_TEST_LARGE"), reason="set LF_TEST_LARGE=1 (several minutes)")
+def test_large_full_size_sampled(lf, oracle_lib):
+    """Full 3.07M-node / ~115M-edge workload at queue size 65536: preprocessing
+    equal to the oracle's (CSR and labels), t(x,V) and vt(x,V) on sampled
+    nodes by the oracle's per-node count, the node order consistent with
+    those counts, and after the run every community aggregate equal to its
+    recount from the memberships."""
+    el = W.large_like()
+    og = oracle_lib.OracleGraph(el.src, el.dst, prepare=False)
+    with lf.Graph(el.src, el.dst) as g:
+        off, adj, labels = g.csr()
+        ooff, oadj, olabels = og.csr()
+        assert np.array_equal(labels, olabels) and np.array_equal(off, ooff) and np.array_equal(adj, oadj)
+        t, vt, cc = g.node_stats()
+        rng = np.random.default_rng(0)
+        deg = np.diff(off)
+        sample = np.concatenate([rng.choice(g.n, 150, replace=False), np.argsort(deg)[-50:]])
+        for x in sample:
+            assert (t[x], vt[x]) == og.node_triangles(int(x)), x
+        order = g.order()
+        for a in range(0, g.n - 1, 997):   # sampled neighbours in the order, compared exactly
+            xa, xb = int(order[a]), int(order[a + 1])
+            ca = (int(t[xa]), int(deg[xa]) * (int(deg[xa]) - 1) // 2) if deg[xa] > 1 else (0, 1)
+            cb = (int(t[xb]), int(deg[xb]) * (int(deg[xb]) - 1) // 2) if deg[xb] > 1 else (0, 1)
+            lhs, rhs = ca[0] * cb[1], cb[0] * ca[1]
+            assert lhs > rhs or (lhs == rhs and (deg[xa] > deg[xb] or (deg[xa] == deg[xb] and xa < xb)))
+        st = g.run(65536, -math.inf, 20)
+        assert st.iterations == 20
+        s = g.state()
+        n_c, m_c, vol_c = _recount(off, adj, s)
+        assert np.array_equal(n_c, s["n"]) and np.array_equal(m_c, s["m"]) and np.array_equal(vol_c, s["vol"])
