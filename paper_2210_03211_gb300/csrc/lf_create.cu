@@ -13,8 +13,10 @@
 namespace lf {
 namespace {
 
-constexpr int TRI_WARP_MAX = 64;        // out-degree handled by one warp
-constexpr int TRI_BLOCK_LIST = 16384;   // out-neighbour list held in shared memory by one block
+constexpr int TRI_WARP_MAX = 128;       // out-degree handled by one warp
+constexpr int TRI_MID_MAX = 2048;       // out-degree handled by one 256-thread block
+constexpr int TRI_MID_THREADS = 256;
+constexpr int TRI_BLOCK_LIST = 16384;   // out-neighbour list held in shared memory by one big block
 constexpr int TRI_BLOCK_THREADS = 1024;
 
 // ---- a1 --------------------------------------------------------------------
@@ -190,81 +192,251 @@ __device__ __forceinline__ int find_sorted(const int32_t *list, int len, int32_t
     return -1;
 }
 
-// One warp per node u with 2 <= d+(u) <= TRI_WARP_MAX.  For every v in N+(u)
-// the warp streams N+(v) and looks each w up in N+(u) (kept in shared
-// memory): w found means triangle (u, v, w) with rank u < v < w, met exactly
-// once.  Credits: t[u] += |N+(u) & N+(v)| summed over v, t[v] += that count
-// per v (one atomic per oriented edge), t[w] accumulated per position of w
-// in N+(u) (one atomic per oriented edge).  Edge marks: v->w directly,
-// u->v and u->w from the per-position counters.
-__global__ void __launch_bounds__(256) k_tri_warp(const int64_t *ooff, const int32_t *oadj, int64_t n,
+// Triangles, credited without per-triangle global atomics.  For a node u,
+// every w in N+(v) for v in N+(u) that is also in N+(u) closes the triangle
+// (u, v, w) with rank u < v < w, met exactly once.  Credits: t[v] and t[w]
+// through one counter per position of N+(u) (a single global atomic per
+// position at the end), t[u] as their common total.  Edge marks: v->w when
+// found, u->v and u->w from the counters.
+//
+// The work of a node is flattened: the lists N+(v) are laid end to end
+// (prefix sums of their lengths in shared memory) and consumed 32 elements
+// per lane group whatever the v boundaries, so short lists leave no lanes
+// idle; each lane issues TRI_UNROLL independent loads before it uses any.
+// Membership in N+(u) goes through a shared-memory hash table of the ids.
+
+constexpr int TRI_UNROLL = 4;
+constexpr int TW_HASH = 2 * TRI_WARP_MAX;   // slots of a warp's table (load <= 1/2)
+constexpr int TM_HASH = 2 * TRI_MID_MAX;    // slots of a block's table
+
+template <int HS, typename IdxT>
+__device__ __forceinline__ int tri_lookup(const int32_t *hk, const IdxT *hp, int32_t w) {
+    uint32_t h = hash32((uint32_t)w) & (HS - 1);
+    for (int probe = 0; probe < HS; ++probe) {
+        const int32_t k = hk[h];
+        if (k == w) return (int)hp[h];
+        if (k == -1) return -1;
+        h = (h + 1) & (HS - 1);
+    }
+    return -1;
+}
+
+template <int HS, typename IdxT>
+__device__ __forceinline__ void tri_insert(int32_t *hk, IdxT *hp, int32_t v, int k) {
+    uint32_t h = hash32((uint32_t)v) & (HS - 1);
+    while (atomicCAS(&hk[h], -1, v) != -1) h = (h + 1) & (HS - 1);
+    hp[h] = (IdxT)k;
+}
+
+// Elements [e_begin, e_end) of a node's flattened stream, walked by one warp
+// from position p (pre[p] <= e_begin).  Returns this lane's triangle count.
+template <int HS, typename IdxT>
+__device__ __forceinline__ int tri_stream(int e_begin, int e_end, int p, const int32_t *pre, const long long *base,
+                                          const int32_t *__restrict__ oadj, int32_t lo_id, int32_t hi_id,
+                                          const int32_t *hk, const IdxT *hp, int *cnt, uint8_t *sup, int lane) {
+    int tu = 0;
+    for (int e0 = e_begin; e0 < e_end; e0 += 32 * TRI_UNROLL) {
+        int pp[TRI_UNROLL];
+        long long at[TRI_UNROLL];
+        int32_t x[TRI_UNROLL];
+#pragma unroll
+        for (int j = 0; j < TRI_UNROLL; ++j) {
+            const int e = e0 + j * 32 + lane;
+            pp[j] = -1;
+            at[j] = 0;
+            x[j] = 0;
+            if (e < e_end) {
+                while (pre[p + 1] <= e) ++p;
+                at[j] = base[p] + (e - pre[p]);
+                pp[j] = p;
+                x[j] = oadj[at[j]];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TRI_UNROLL; ++j) {
+            if (pp[j] >= 0 && x[j] >= lo_id && x[j] <= hi_id) {
+                const int idx = tri_lookup<HS, IdxT>(hk, hp, x[j]);
+                if (idx >= 0) {
+                    atomicAdd(&cnt[idx], 1);
+                    atomicAdd(&cnt[pp[j]], 1);
+                    sup[at[j]] = 1;
+                    ++tu;
+                }
+            }
+        }
+        p = __shfl_sync(FULL, p, 31);   // lane 31 holds the furthest position
+    }
+    return tu;
+}
+
+// One warp per node u with 2 <= d+(u) <= TRI_WARP_MAX.
+__global__ void __launch_bounds__(256) k_tri_warp(const int64_t *ooff, const int32_t *__restrict__ oadj, int64_t n,
                                                   unsigned long long *tri, uint8_t *sup, DevScalars *ds) {
+    __shared__ long long s_base[8][TRI_WARP_MAX];
     __shared__ int32_t s_list[8][TRI_WARP_MAX];
-    __shared__ int32_t s_top[8][TRI_WARP_MAX];
-    __shared__ int32_t s_mid[8][TRI_WARP_MAX];
+    __shared__ int32_t s_pre[8][TRI_WARP_MAX + 1];
+    __shared__ int32_t s_cnt[8][TRI_WARP_MAX];
+    __shared__ int32_t s_hk[8][TW_HASH];
+    __shared__ uint8_t s_hp[8][TW_HASH];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int32_t *list = s_list[w], *top = s_top[w], *mid = s_mid[w];
+    int32_t *list = s_list[w], *pre = s_pre[w], *cnt = s_cnt[w], *hk = s_hk[w];
+    long long *base = s_base[w];
+    uint8_t *hp = s_hp[w];
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long found = 0;
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
         const int64_t s = ooff[u];
         const int du = (int)(ooff[u + 1] - s);
         if (du < 2 || du > TRI_WARP_MAX) continue;
-        for (int i = lane; i < du; i += 32) {
-            list[i] = oadj[s + i];
-            top[i] = 0;
-            mid[i] = 0;
-        }
-        __syncwarp();
-        const int32_t lo_id = list[0], hi_id = list[du - 1];
-        unsigned long long tu = 0;
-        for (int p = 0; p < du; ++p) {
-            const int32_t v = list[p];
-            const int64_t sv = ooff[v];
-            const int dv = (int)(ooff[v + 1] - sv);
-            int c = 0;
-            for (int j = lane; j < dv; j += 32) {
-                int32_t x = oadj[sv + j];
-                if (x < lo_id || x > hi_id) continue;
-                int idx = find_sorted(list, du, x);
-                if (idx >= 0) {
-                    atomicAdd(&top[idx], 1);
-                    sup[sv + j] = 1;
-                    ++c;
-                }
+        for (int k = lane; k < TW_HASH; k += 32) hk[k] = -1;
+        int carry = 0;
+        for (int k0 = 0; k0 < du; k0 += 32) {
+            const int k = k0 + lane;
+            int len = 0;
+            if (k < du) {
+                const int32_t v = oadj[s + k];
+                const int64_t b = ooff[v];
+                list[k] = v;
+                base[k] = b;
+                len = (int)(ooff[v + 1] - b);
+                cnt[k] = 0;
             }
-            c = __reduce_add_sync(FULL, c);
-            if (c > 0 && lane == 0) {
-                atomicAdd(&tri[v], (unsigned long long)c);
-                mid[p] = 1;
+            int x = len;   // inclusive warp scan of the lengths
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
             }
-            tu += (unsigned long long)c;
+            if (k < du) pre[k + 1] = carry + x;
+            carry += __shfl_sync(FULL, x, 31);
         }
+        if (lane == 0) pre[0] = 0;
         __syncwarp();
-        for (int i = lane; i < du; i += 32) {
-            int cnt = top[i];
-            if (cnt > 0) atomicAdd(&tri[list[i]], (unsigned long long)cnt);
-            if (cnt > 0 || mid[i]) sup[s + i] = 1;
+        for (int k = lane; k < du; k += 32) tri_insert<TW_HASH, uint8_t>(hk, hp, list[k], k);
+        __syncwarp();
+        int tu = tri_stream<TW_HASH, uint8_t>(0, pre[du], 0, pre, base, oadj, list[0], list[du - 1], hk, hp, cnt,
+                                              sup, lane);
+        __syncwarp();
+        for (int k = lane; k < du; k += 32) {
+            const int c = cnt[k];
+            if (c > 0) {
+                atomicAdd(&tri[list[k]], (unsigned long long)c);
+                sup[s + k] = 1;
+            }
         }
-        if (lane == 0 && tu > 0) atomicAdd(&tri[u], tu);
-        found += tu;
+        tu = __reduce_add_sync(FULL, tu);
+        if (lane == 0 && tu > 0) atomicAdd(&tri[u], (unsigned long long)tu);
+        found += (unsigned long long)tu;
         __syncwarp();
     }
     if (lane == 0 && found) atomicAdd(&ds->num_tri, found);
 }
 
-// One block per node with d+(u) > TRI_WARP_MAX; warps take the v's.  When the
+// One 256-thread block per node with TRI_WARP_MAX < d+(u) <= TRI_MID_MAX: the
+// stream is cut into one contiguous range per warp.
+__global__ void __launch_bounds__(TRI_MID_THREADS) k_tri_mid(const int64_t *ooff, const int32_t *__restrict__ oadj,
+                                                             const int32_t *mids, const uint32_t *nmid,
+                                                             unsigned long long *tri, uint8_t *sup, DevScalars *ds) {
+    extern __shared__ long long mid_dyn[];
+    long long *base = mid_dyn;                                            // TRI_MID_MAX
+    int32_t *hk = reinterpret_cast<int32_t *>(mid_dyn + TRI_MID_MAX);     // TM_HASH
+    int32_t *list = hk + TM_HASH;                                         // TRI_MID_MAX
+    int32_t *pre = list + TRI_MID_MAX;                                    // TRI_MID_MAX + 1
+    int32_t *cnt = pre + TRI_MID_MAX + 1;                                 // TRI_MID_MAX
+    uint16_t *hp = reinterpret_cast<uint16_t *>(cnt + TRI_MID_MAX);       // TM_HASH
+    __shared__ int32_t s_part[TRI_MID_THREADS / 32];
+    __shared__ unsigned long long s_tu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int NW = TRI_MID_THREADS / 32;
+    constexpr int PER = TRI_MID_MAX / TRI_MID_THREADS;
+    for (uint32_t h = blockIdx.x; h < *nmid; h += gridDim.x) {
+        const int32_t u = mids[h];
+        const int64_t s = ooff[u];
+        const int du = (int)(ooff[u + 1] - s);
+        if (threadIdx.x == 0) s_tu = 0;
+        for (int k = threadIdx.x; k < TM_HASH; k += TRI_MID_THREADS) hk[k] = -1;
+        // lengths: thread t owns entries t*PER .. t*PER+PER-1, then a block scan
+        int lens[PER];
+        int sum = 0;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int k = threadIdx.x * PER + j;
+            lens[j] = 0;
+            if (k < du) {
+                const int32_t v = oadj[s + k];
+                const int64_t b = ooff[v];
+                list[k] = v;
+                base[k] = b;
+                lens[j] = (int)(ooff[v + 1] - b);
+                cnt[k] = 0;
+            }
+            sum += lens[j];
+        }
+        int x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_part[w] = x;
+        __syncthreads();
+        int run = x - sum;
+        for (int k = 0; k < w; ++k) run += s_part[k];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int k = threadIdx.x * PER + j;
+            if (k < du) pre[k] = run;
+            run += lens[j];
+        }
+        if (threadIdx.x == TRI_MID_THREADS - 1) pre[du] = run;
+        for (int k = threadIdx.x; k < du; k += TRI_MID_THREADS) tri_insert<TM_HASH, uint16_t>(hk, hp, list[k], k);
+        __syncthreads();
+        const int total = pre[du];
+        const int eb = (int)((long long)total * w / NW), ee = (int)((long long)total * (w + 1) / NW);
+        int tu = 0;
+        if (eb < ee) {
+            // first position whose range holds eb (pre is ascending, pre[du] > eb)
+            int lo = 0, hi = du - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (pre[mid + 1] <= eb) lo = mid + 1; else hi = mid;
+            }
+            tu = tri_stream<TM_HASH, uint16_t>(eb, ee, lo, pre, base, oadj, list[0], list[du - 1], hk, hp, cnt, sup,
+                                               lane);
+        }
+        tu = __reduce_add_sync(FULL, tu);
+        if (lane == 0 && tu) atomicAdd(&s_tu, (unsigned long long)tu);
+        __syncthreads();
+        for (int k = threadIdx.x; k < du; k += TRI_MID_THREADS) {
+            const int c = cnt[k];
+            if (c > 0) {
+                atomicAdd(&tri[list[k]], (unsigned long long)c);
+                sup[s + k] = 1;
+            }
+        }
+        if (threadIdx.x == 0 && s_tu) {
+            atomicAdd(&tri[u], s_tu);
+            atomicAdd(&ds->num_tri, s_tu);
+        }
+        __syncthreads();
+    }
+}
+
+constexpr size_t TRI_MID_SMEM = (size_t)TRI_MID_MAX * 8 + (size_t)TM_HASH * 4 + (size_t)(3 * TRI_MID_MAX + 1) * 4 +
+                                (size_t)TM_HASH * 2;
+
+// One block per node with d+(u) > TRI_MID_MAX; warps take the v's.  When the
 // list does not fit in shared memory, the look-ups go to global memory and
 // the credits are made per triangle.
 __global__ void __launch_bounds__(TRI_BLOCK_THREADS) k_tri_block(const int64_t *ooff, const int32_t *oadj,
-                                                                 const int32_t *hubs, const uint32_t *nhubs,
+                                                                 const int32_t *bigs_end, const uint32_t *nbig,
                                                                  unsigned long long *tri, uint8_t *sup,
                                                                  DevScalars *ds) {
     extern __shared__ int32_t dyn[];
     __shared__ unsigned long long s_tu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (uint32_t h = blockIdx.x; h < *nhubs; h += gridDim.x) {
-        const int32_t u = hubs[h];
+    for (uint32_t h = blockIdx.x; h < *nbig; h += gridDim.x) {
+        const int32_t u = bigs_end[-1 - (int64_t)h];
         const int64_t s = ooff[u];
         const int du = (int)(ooff[u + 1] - s);
         const bool in_smem = du <= TRI_BLOCK_LIST;
@@ -325,10 +497,636 @@ __global__ void __launch_bounds__(TRI_BLOCK_THREADS) k_tri_block(const int64_t *
     }
 }
 
-__global__ void k_select_hubs(const int64_t *ooff, int64_t n, int32_t *hubs, uint32_t *nhubs) {
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
-        if (ooff[u + 1] - ooff[u] > TRI_WARP_MAX) hubs[atomicAdd(nhubs, 1u)] = (int32_t)u;
+// Nodes for the block kernels: mid-size ones from the front of `hubs`
+// (count nh[0]), big ones from the back (count nh[1]); n entries hold both.
+__global__ void k_select_hubs(const int64_t *ooff, int64_t n, int32_t *hubs, uint32_t *nh) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t du = ooff[u + 1] - ooff[u];
+        if (du > TRI_MID_MAX) hubs[n - 1 - atomicAdd(&nh[1], 1u)] = (int32_t)u;
+        else if (du > TRI_WARP_MAX) hubs[atomicAdd(&nh[0], 1u)] = (int32_t)u;
+    }
 }
+
+constexpr size_t TRI_BIG_SMEM = (size_t)TRI_BLOCK_LIST * 9;
+
+void set_triangle_attrs() {
+    LF_CUDA(cudaFuncSetAttribute(k_tri_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TRI_BIG_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_tri_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TRI_MID_SMEM));
+}
+
+// Triangle counts and support marks of an oriented graph with n > 0 nodes.
+// `hubs` holds n ints of scratch and `nh` two counters that start at zero.
+// Returns the number of kernels launched.
+int launch_triangles(const int64_t *ooff, const int32_t *oadj, int64_t n, int32_t *hubs, uint32_t *nh,
+                     unsigned long long *tri, uint8_t *sup, DevScalars *ds, cudaStream_t st) {
+    const int sms = 152;
+    k_select_hubs<<<grid_for(n, 256, 8192), 256, 0, st>>>(ooff, n, hubs, nh);
+    LF_LAUNCHED();
+    k_tri_warp<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(ooff, oadj, n, tri, sup, ds);
+    LF_LAUNCHED();
+    k_tri_mid<<<sms * 8, TRI_MID_THREADS, TRI_MID_SMEM, st>>>(ooff, oadj, hubs, nh, tri, sup, ds);
+    LF_LAUNCHED();
+    k_tri_block<<<2 * sms, TRI_BLOCK_THREADS, TRI_BIG_SMEM, st>>>(ooff, oadj, hubs + n, nh + 1, tri, sup, ds);
+    LF_LAUNCHED();
+    return 4;
+}
+
+
+// ---- a3, main path: triangles by their middle vertex ------------------------
+// A triangle u < v < w (rank order) is found at v: for every in-neighbour u of
+// v (u -> v), the list N+(u) is streamed and each w in it probed against
+// N+(v).  The elements read are sum over u of d+(u)^2, against sum over v of
+// d-(v) d+(v) when triangles are found at u, several times fewer on
+// power-law graphs, whose middle-rank nodes have long out-lists.
+// Credits of a triangle (u, v, w): t[w] and the mark v->w through one counter
+// per position of N+(v); t[u] and the mark u->v through one counter per
+// in-neighbour; t[v] as the common total; the mark u->w where w is met.
+// The streams of all in-neighbours are laid end to end, as above.
+//
+// Most stream elements are not in N+(v).  Each is first tested against a
+// one-bit-per-slot filter of N+(v) (one shared load); the few that pass are
+// queued per warp and looked up 32 at a time in the exact set, so the costly
+// path runs on full warps.
+
+constexpr int TV_WARP_DPLUS = 128;   // |N+(v)| hashed by one warp
+constexpr int TV_WARP_DEG = 1024;    // deg(v) walked by one warp
+constexpr int TV_ROUND = 64;         // entries of N(v) compacted per warp round
+constexpr int TV_ITEM = 512;         // entries of N(v) per block item
+constexpr int TV_BLOCK_DPLUS = 1024; // |N+(v)| hashed by one block
+constexpr int TV_THREADS = 256;
+constexpr int TV_WHASH = 2 * TV_WARP_DPLUS;   // slots: buckets of four ids, at most half full
+constexpr int TV_BHASH = 2 * TV_BLOCK_DPLUS;
+constexpr int TV_WBITS_LOG = 11;     // filter bits per warp table (>= 16 per id)
+constexpr int TV_BBITS_LOG = 14;     // filter bits per block table
+constexpr int TV_QUEUE = 64;         // queued candidates per warp
+
+__device__ __forceinline__ uint32_t tv_mix(int32_t w) { return (uint32_t)w * 0x9E3779B1u; }   // Knuth
+
+// Set of ids with their positions: buckets of four slots read as one 16-byte
+// shared load, multiplicative hashing on the bucket index, linear probing
+// over buckets.  At most half full, so a lookup nearly always reads one
+// bucket.
+template <int SLOTS, typename IdxT>
+struct TvBuckets {
+    static constexpr int NB = SLOTS / 4;
+    static constexpr int SHIFT = 32 - __builtin_ctz(NB);
+    int32_t *hk;   // SLOTS ids, -1 = empty; 16-byte aligned
+    IdxT *hp;      // SLOTS positions
+    __device__ __forceinline__ static uint32_t bucket(int32_t w) { return tv_mix(w) >> SHIFT; }
+    __device__ __forceinline__ void insert(int32_t v, int k) const {
+        uint32_t b = bucket(v);
+        for (;;) {
+#pragma unroll
+            for (int sl = 0; sl < 4; ++sl)
+                if (atomicCAS(&hk[4 * b + sl], -1, v) == -1) {
+                    hp[4 * b + sl] = (IdxT)k;
+                    return;
+                }
+            b = (b + 1) & (NB - 1);
+        }
+    }
+    __device__ __forceinline__ int find(int32_t w) const {
+        uint32_t b = bucket(w);
+        for (int probe = 0; probe < NB; ++probe) {
+            const int4 q = reinterpret_cast<const int4 *>(hk)[b];
+            const int sl = q.x == w ? 0 : q.y == w ? 1 : q.z == w ? 2 : q.w == w ? 3 : -1;
+            if (sl >= 0) return (int)hp[4 * b + sl];
+            if (q.w == -1) return -1;   // slots fill in order, so a free last slot ends the chain
+            b = (b + 1) & (NB - 1);
+        }
+        return -1;
+    }
+};
+using TvHash8 = TvBuckets<TV_WHASH, uint8_t>;
+using TvHash16 = TvBuckets<TV_BHASH, uint16_t>;
+
+struct TvSorted {  // N+(v) as a sorted list, in shared or global memory
+    const int32_t *list;
+    int len;
+    __device__ __forceinline__ int find(int32_t w) const {
+        int lo = 0, hi = len - 1;
+        while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            const int32_t x = list[mid];
+            if (x == w) return mid;
+            if (x < w) lo = mid + 1; else hi = mid - 1;
+        }
+        return -1;
+    }
+};
+
+template <int LOGB>
+__device__ __forceinline__ void tv_filter_add(uint32_t *bits, int32_t w) {
+    const uint32_t h = tv_mix(w) >> (32 - LOGB);
+    atomicOr(&bits[h >> 5], 1u << (h & 31));
+}
+
+template <int LOGB>
+__device__ __forceinline__ bool tv_filter_has(const uint32_t *bits, int32_t w) {
+    const uint32_t h = tv_mix(w) >> (32 - LOGB);
+    return (bits[h >> 5] >> (h & 31)) & 1u;
+}
+
+// Shared arrays of one round: compacted in-neighbours u; ooff[u], turned into
+// ooff[u] - pre[u] once the prefix sums pre of d+(u) are known, so that stream
+// element e of position p sits at oadj[shift[p] + e]; triangles per u; and the
+// stream index at which v appears in N+(u).
+template <typename Idx>
+struct TvRound {
+    int32_t *ul;
+    Idx *shift;   // int32_t when the oriented CSR has fewer than 2^31 entries
+    int32_t *pre;
+    int32_t *hits;
+    int32_t *vrel;
+};
+
+struct TvQueue {   // one warp's candidates: id, stream index, position
+    int32_t *x;
+    int32_t *e;
+    int32_t *p;
+};
+
+// Elements [e_begin, e_end) of a round's stream, walked by one warp from
+// position p (pre[p] <= e_begin).  LOCAL: per-position counters of N+(v) in
+// `cnt`; otherwise t[w] and the mark v->w are written directly.  Returns this
+// lane's triangle count.
+template <bool LOCAL, int LOGB, typename Idx, typename Set>
+__device__ __forceinline__ int tv_stream(int e_begin, int e_end, int p, const TvRound<Idx> &r,
+                                         const int32_t *__restrict__ oadj, int32_t v, int64_t vs,
+                                         const uint32_t *bits, const Set &set, const TvQueue &q, int *cnt,
+                                         unsigned long long *tri, uint8_t *sup, int lane) {
+    int tv = 0, qn = 0;
+    const unsigned lt = lanemask_lt();
+    // lanes below `count` take the last `count` queue entries
+    auto drain = [&](int count) {
+        __syncwarp();
+        if (lane < count) {
+            const int k = qn - count + lane;
+            const int32_t x = q.x[k];
+            const int pp = q.p[k];
+            const int idx = set.find(x);
+            if (idx >= 0) {
+                if (LOCAL) {
+                    atomicAdd(&cnt[idx], 1);
+                } else {
+                    atomicAdd(&tri[x], 1ull);
+                    sup[vs + idx] = 1;
+                }
+                atomicAdd(&r.hits[pp], 1);
+                sup[r.shift[pp] + (Idx)q.e[k]] = 1;
+                ++tv;
+            }
+        }
+        qn -= count;
+        __syncwarp();
+    };
+    for (int e0 = e_begin; e0 < e_end; e0 += 32 * TRI_UNROLL) {
+        int pp[TRI_UNROLL];
+        int32_t x[TRI_UNROLL];
+        if (e0 + 32 * TRI_UNROLL <= e_end) {   // full steps: no bound checks
+#pragma unroll
+            for (int j = 0; j < TRI_UNROLL; ++j) {
+                const int e = e0 + j * 32 + lane;
+                while (r.pre[p + 1] <= e) ++p;
+                pp[j] = p;
+                x[j] = oadj[r.shift[p] + (Idx)e];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < TRI_UNROLL; ++j) {
+                const int e = e0 + j * 32 + lane;
+                pp[j] = -1;
+                x[j] = 0;
+                if (e < e_end) {
+                    while (r.pre[p + 1] <= e) ++p;
+                    pp[j] = p;
+                    x[j] = oadj[r.shift[p] + (Idx)e];
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TRI_UNROLL; ++j) {
+            const int e = e0 + j * 32 + lane;
+            bool cand = false;
+            if (pp[j] >= 0) {
+                if (x[j] == v) r.vrel[pp[j]] = e;
+                cand = tv_filter_has<LOGB>(bits, x[j]);
+            }
+            const unsigned m = __ballot_sync(FULL, cand);
+            if (cand) {
+                const int k = qn + __popc(m & lt);
+                q.x[k] = x[j];
+                q.e[k] = e;
+                q.p[k] = pp[j];
+            }
+            qn += __popc(m);
+            if (qn >= 32) drain(32);
+        }
+        p = __shfl_sync(FULL, p, 31);   // lane 31 holds the furthest position
+    }
+    if (qn > 0) drain(qn);
+    __syncwarp();   // every vrel and hits write seen by the warp's readers
+    return tv;
+}
+
+// The in-neighbours u of v with d+(u) >= 2 among C entries of N(v) a lane
+// holds (entries j0 + c * 32): loads first, then the warp ballots.  Returns
+// the entries kept by this warp (written from slot `at` on); lengths go to
+// pre[slot + 1].
+template <int C, typename Idx>
+__device__ __forceinline__ int tv_compact(const int32_t *adj, const int32_t *deg, const int64_t *ooff, int64_t as,
+                                          int j0, int jend, int32_t dv, int32_t v, int at, const TvRound<Idx> &r,
+                                          int lane) {
+    int32_t u[C], du[C];
+    long long b[C];
+    int len[C];
+    bool keep[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int j = j0 + c * 32;
+        u[c] = j < jend ? adj[as + j] : -1;
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) du[c] = u[c] >= 0 ? deg[u[c]] : 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        b[c] = 0;
+        len[c] = 0;
+        if (u[c] >= 0 && ranks_above(dv, v, du[c], u[c])) {
+            b[c] = ooff[u[c]];
+            len[c] = (int)(ooff[u[c] + 1] - b[c]);
+        }
+        keep[c] = len[c] >= 2;
+    }
+    int kept = 0;
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const unsigned mask = __ballot_sync(FULL, keep[c]);
+        if (keep[c]) {
+            const int slot = at + kept + __popc(mask & lt);
+            r.ul[slot] = u[c];
+            r.shift[slot] = (Idx)b[c];
+            r.pre[slot + 1] = len[c];
+            r.hits[slot] = 0;
+        }
+        kept += __popc(mask);
+    }
+    return kept;
+}
+
+// One warp per node v with 1 <= d+(v) <= TV_WARP_DPLUS and deg(v) <= TV_WARP_DEG.
+// A resident grid; each warp takes runs of TV_WARP_BATCH node ids from a
+// counter, so that a block is not held by one long node while its other warps
+// idle.
+constexpr int TV_WARP_BATCH = 64;
+
+template <typename Idx>
+__global__ void __launch_bounds__(256, 5) k_tv_warp(const int64_t *off, const int32_t *adj, const int32_t *deg,
+                                                    const int64_t *ooff, const int32_t *__restrict__ oadj,
+                                                    int64_t n, uint32_t *next, unsigned long long *tri, uint8_t *sup,
+                                                    DevScalars *ds) {
+    __shared__ Idx s_shift[8][TV_ROUND];
+    __shared__ int32_t s_ul[8][TV_ROUND];
+    __shared__ int32_t s_pre[8][TV_ROUND + 1];
+    __shared__ int32_t s_hits[8][TV_ROUND];
+    __shared__ int32_t s_vrel[8][TV_ROUND];
+    __shared__ int32_t s_cnt[8][TV_WARP_DPLUS];
+    __shared__ __align__(16) int32_t s_hk[8][TV_WHASH];
+    __shared__ uint8_t s_hp[8][TV_WHASH];
+    __shared__ uint32_t s_bits[8][(1 << TV_WBITS_LOG) / 32];
+    __shared__ int32_t s_q[8][3][TV_QUEUE];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const TvRound<Idx> r{s_ul[w], s_shift[w], s_pre[w], s_hits[w], s_vrel[w]};
+    const TvQueue q{s_q[w][0], s_q[w][1], s_q[w][2]};
+    int32_t *cnt = s_cnt[w], *hk = s_hk[w];
+    uint32_t *bits = s_bits[w];
+    const TvHash8 set{hk, s_hp[w]};
+    unsigned long long found = 0;
+    int64_t vv = 0, vend = 0;
+    for (;;) {
+        if (vv == vend) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = (unsigned long long)atomicAdd(next, 1u) * TV_WARP_BATCH;
+            b0 = __shfl_sync(FULL, b0, 0);
+            if ((int64_t)b0 >= n) break;
+            vv = (int64_t)b0;
+            vend = min(n, vv + TV_WARP_BATCH);
+        }
+        const int32_t v = (int32_t)(vv++);
+        const int64_t vs = ooff[v];
+        const int dpv = (int)(ooff[v + 1] - vs);
+        const int64_t as = off[v];
+        const int dv = (int)(off[v + 1] - as);
+        if (dpv < 1 || dpv > TV_WARP_DPLUS || dv > TV_WARP_DEG || dv == dpv) continue;
+        for (int k = lane; k < TV_WHASH; k += 32) hk[k] = -1;
+        for (int k = lane; k < (1 << TV_WBITS_LOG) / 32; k += 32) bits[k] = 0;
+        __syncwarp();
+        for (int k = lane; k < dpv; k += 32) {
+            const int32_t x = oadj[vs + k];
+            set.insert(x, k);
+            tv_filter_add<TV_WBITS_LOG>(bits, x);
+            cnt[k] = 0;
+        }
+        int tv = 0;
+        for (int r0 = 0; r0 < dv; r0 += TV_ROUND) {
+            const int nk = tv_compact<TV_ROUND / 32>(adj, deg, ooff, as, r0 + lane, min(dv, r0 + TV_ROUND), dv, v, 0,
+                                                     r, lane);
+            if (nk == 0) continue;
+            __syncwarp();
+            int carry = 0;
+            for (int k0 = 0; k0 < nk; k0 += 32) {   // prefix sums of the lengths, in place
+                const int k = k0 + lane;
+                int x = k < nk ? r.pre[k + 1] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (k < nk) r.pre[k + 1] = carry + x;
+                carry += __shfl_sync(FULL, x, 31);
+            }
+            if (lane == 0) r.pre[0] = 0;
+            __syncwarp();
+            for (int k = lane; k < nk; k += 32) r.shift[k] -= (Idx)r.pre[k];
+            __syncwarp();
+            tv += tv_stream<true, TV_WBITS_LOG>(0, r.pre[nk], 0, r, oadj, v, vs, bits, set, q, cnt, tri, sup, lane);
+            for (int k = lane; k < nk; k += 32) {
+                const int h = r.hits[k];
+                if (h > 0) {
+                    atomicAdd(&tri[r.ul[k]], (unsigned long long)h);
+                    sup[r.shift[k] + (Idx)r.vrel[k]] = 1;
+                }
+            }
+            __syncwarp();
+        }
+        for (int k = lane; k < dpv; k += 32) {
+            const int c = cnt[k];
+            if (c > 0) {
+                atomicAdd(&tri[oadj[vs + k]], (unsigned long long)c);
+                sup[vs + k] = 1;
+            }
+        }
+        tv = __reduce_add_sync(FULL, tv);
+        if (lane == 0 && tv > 0) atomicAdd(&tri[v], (unsigned long long)tv);
+        found += (unsigned long long)tv;
+        __syncwarp();
+    }
+    if (lane == 0 && found) atomicAdd(&ds->num_tri, found);
+}
+
+// Block items: (v, a run of TV_ITEM entries of N(v)), for the nodes the warp
+// kernel leaves.  BIG = false: |N+(v)| <= TV_BLOCK_DPLUS, hashed, counters in
+// shared memory.  BIG = true: N+(v) sorted in shared memory (global beyond
+// TRI_BLOCK_LIST ids), t[w] and v->w written per triangle.  Items are taken
+// from a counter, so long and short ones balance across the blocks.
+constexpr int TV_NW = TV_THREADS / 32;
+constexpr size_t tv_round_smem(size_t idx_bytes) {
+    return (size_t)TV_ITEM * idx_bytes + (size_t)(4 * TV_ITEM + 4) * 4 + (size_t)TV_NW * 3 * TV_QUEUE * 4 +
+           ((size_t)1 << TV_BBITS_LOG) / 8;
+}
+constexpr size_t tv_items_smem(bool big, size_t idx_bytes) {
+    return tv_round_smem(idx_bytes) +
+           (big ? (size_t)TRI_BLOCK_LIST * 4 : (size_t)TV_BHASH * 6 + (size_t)TV_BLOCK_DPLUS * 4);
+}
+
+template <bool BIG, typename Idx>
+__global__ void __launch_bounds__(TV_THREADS) k_tv_items(const int64_t *off, const int32_t *adj, const int32_t *deg,
+                                                         const int64_t *ooff, const int32_t *__restrict__ oadj,
+                                                         const unsigned long long *items, const uint32_t *nitems,
+                                                         uint32_t *next, unsigned long long *tri, uint8_t *sup,
+                                                         DevScalars *ds) {
+    extern __shared__ int4 tv_dyn[];
+    Idx *shift = reinterpret_cast<Idx *>(tv_dyn);                            // TV_ITEM
+    int32_t *ul = reinterpret_cast<int32_t *>(shift + TV_ITEM);             // TV_ITEM
+    int32_t *pre = ul + TV_ITEM;                                             // TV_ITEM + 1 (+3 padding)
+    int32_t *hits = pre + TV_ITEM + 4;                                       // TV_ITEM
+    int32_t *vrel = hits + TV_ITEM;                                          // TV_ITEM
+    int32_t *qbuf = vrel + TV_ITEM;                                          // TV_NW * 3 * TV_QUEUE
+    uint32_t *bits = reinterpret_cast<uint32_t *>(qbuf + TV_NW * 3 * TV_QUEUE);   // 2^TV_BBITS_LOG bits
+    int32_t *hk = reinterpret_cast<int32_t *>(bits + (1 << TV_BBITS_LOG) / 32);  // TV_BHASH, 16-byte aligned
+    int32_t *cnt = hk + TV_BHASH;                                            // TV_BLOCK_DPLUS
+    uint16_t *hp = reinterpret_cast<uint16_t *>(cnt + TV_BLOCK_DPLUS);      // TV_BHASH
+    int32_t *slist = hk;                                                     // BIG: TRI_BLOCK_LIST ids
+    __shared__ int32_t s_part[TV_NW];
+    __shared__ uint32_t s_item;
+    __shared__ unsigned long long s_tv;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const TvRound<Idx> r{ul, shift, pre, hits, vrel};
+    const TvQueue q{qbuf + w * 3 * TV_QUEUE, qbuf + w * 3 * TV_QUEUE + TV_QUEUE, qbuf + w * 3 * TV_QUEUE + 2 * TV_QUEUE};
+    const uint32_t count = *nitems;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(next, 1u);
+            s_tv = 0;
+        }
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= count) break;
+        const unsigned long long item = BIG ? items[-1 - (int64_t)it] : items[it];
+        const int32_t v = (int32_t)(item >> 32);
+        const int chunk = (int)(item & 0xffffffffu);
+        const int64_t vs = ooff[v];
+        const int dpv = (int)(ooff[v + 1] - vs);
+        const int64_t as = off[v];
+        const int dv = (int)(off[v + 1] - as);
+        const int32_t *glist = oadj + vs;
+        // membership structures of N+(v): the filter, and the exact set
+        for (int k = threadIdx.x; k < (1 << TV_BBITS_LOG) / 32; k += TV_THREADS) bits[k] = 0;
+        if (!BIG)
+            for (int k = threadIdx.x; k < TV_BHASH; k += TV_THREADS) hk[k] = -1;
+        __syncthreads();
+        for (int k = threadIdx.x; k < dpv; k += TV_THREADS) {
+            const int32_t x = glist[k];
+            tv_filter_add<TV_BBITS_LOG>(bits, x);
+            if (!BIG) {
+                TvHash16{hk, hp}.insert(x, k);
+                cnt[k] = 0;
+            } else if (dpv <= TRI_BLOCK_LIST) {
+                slist[k] = x;
+            }
+        }
+        // compaction of this item's in-neighbours: each warp takes a run of
+        // TV_ITEM / TV_NW entries
+        constexpr int RUN = TV_ITEM / TV_NW;
+        const int j0 = chunk * TV_ITEM + w * RUN;
+        const int jend = min(dv, chunk * TV_ITEM + TV_ITEM);
+        {
+            // count first, so that the warps' slots can be placed
+            int32_t u[RUN / 32];
+            bool keep[RUN / 32];
+            long long b[RUN / 32];
+            int len[RUN / 32];
+            int wk = 0;
+#pragma unroll
+            for (int c = 0; c < RUN / 32; ++c) {
+                const int j = j0 + c * 32 + lane;
+                u[c] = j < jend ? adj[as + j] : -1;
+            }
+#pragma unroll
+            for (int c = 0; c < RUN / 32; ++c) {
+                keep[c] = false;
+                b[c] = 0;
+                len[c] = 0;
+                if (u[c] >= 0 && ranks_above(dv, v, deg[u[c]], u[c])) {
+                    b[c] = ooff[u[c]];
+                    len[c] = (int)(ooff[u[c] + 1] - b[c]);
+                    keep[c] = len[c] >= 2;
+                }
+                wk += __popc(__ballot_sync(FULL, keep[c]));
+            }
+            if (lane == 0) s_part[w] = wk;
+            __syncthreads();
+            int at = 0;
+            for (int k = 0; k < w; ++k) at += s_part[k];
+            const unsigned lt = lanemask_lt();
+#pragma unroll
+            for (int c = 0; c < RUN / 32; ++c) {
+                const unsigned mask = __ballot_sync(FULL, keep[c]);
+                if (keep[c]) {
+                    const int slot = at + __popc(mask & lt);
+                    ul[slot] = u[c];
+                    shift[slot] = (Idx)b[c];
+                    pre[slot + 1] = len[c];
+                    hits[slot] = 0;
+                }
+                at += __popc(mask);
+            }
+        }
+        int nk = 0;
+        for (int k = 0; k < TV_NW; ++k) nk += s_part[k];
+        __syncthreads();
+        if (nk > 0) {
+            // prefix sums of the lengths: thread t owns entries PER t .. PER t + PER - 1
+            constexpr int PER = TV_ITEM / TV_THREADS;
+            int lens[PER];
+            int sum = 0;
+#pragma unroll
+            for (int c = 0; c < PER; ++c) {
+                const int k = threadIdx.x * PER + c;
+                lens[c] = k < nk ? pre[k + 1] : 0;
+                sum += lens[c];
+            }
+            int x = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
+            }
+            __syncthreads();   // every length read before any prefix is written
+            if (lane == 31) s_part[w] = x;
+            __syncthreads();
+            int run = x - sum;
+            for (int k = 0; k < w; ++k) run += s_part[k];
+#pragma unroll
+            for (int c = 0; c < PER; ++c) {
+                const int k = threadIdx.x * PER + c;
+                if (k < nk) pre[k] = run;
+                run += lens[c];
+            }
+            if (threadIdx.x == TV_THREADS - 1) pre[nk] = run;
+            __syncthreads();
+            for (int k = threadIdx.x; k < nk; k += TV_THREADS) shift[k] -= (Idx)pre[k];
+            __syncthreads();
+            const int total = pre[nk];
+            const int eb = (int)((long long)total * w / TV_NW), ee = (int)((long long)total * (w + 1) / TV_NW);
+            int tv = 0;
+            if (eb < ee) {
+                int lo = 0, hi = nk - 1;   // first position whose range holds eb
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (pre[mid + 1] <= eb) lo = mid + 1; else hi = mid;
+                }
+                if (!BIG)
+                    tv = tv_stream<true, TV_BBITS_LOG>(eb, ee, lo, r, oadj, v, vs, bits, TvHash16{hk, hp}, q, cnt,
+                                                       tri, sup, lane);
+                else
+                    tv = tv_stream<false, TV_BBITS_LOG>(eb, ee, lo, r, oadj, v, vs, bits,
+                                                        TvSorted{dpv <= TRI_BLOCK_LIST ? slist : glist, dpv}, q, cnt,
+                                                        tri, sup, lane);
+            }
+            tv = __reduce_add_sync(FULL, tv);
+            if (lane == 0 && tv) atomicAdd(&s_tv, (unsigned long long)tv);
+            __syncthreads();
+            for (int k = threadIdx.x; k < nk; k += TV_THREADS) {
+                const int h = hits[k];
+                if (h > 0) {
+                    atomicAdd(&tri[ul[k]], (unsigned long long)h);
+                    sup[shift[k] + (Idx)vrel[k]] = 1;
+                }
+            }
+        }
+        if (!BIG)
+            for (int k = threadIdx.x; k < dpv; k += TV_THREADS) {
+                const int c = cnt[k];
+                if (c > 0) {
+                    atomicAdd(&tri[glist[k]], (unsigned long long)c);
+                    sup[vs + k] = 1;
+                }
+            }
+        if (threadIdx.x == 0 && s_tv) {
+            atomicAdd(&tri[v], s_tv);
+            atomicAdd(&ds->num_tri, s_tv);
+        }
+        __syncthreads();
+    }
+}
+
+// Items for the block kernels: hashed ones from the front (count cnt[0]), big
+// ones from the back (count cnt[1]); `cap` entries hold both.
+__global__ void k_tv_plan(const int64_t *off, const int64_t *ooff, int64_t n, unsigned long long *items, int64_t cap,
+                          uint32_t *cnt) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t dpv = ooff[v + 1] - ooff[v];
+        const int64_t dv = off[v + 1] - off[v];
+        if (dpv < 1 || dv == dpv) continue;
+        if (dpv <= TV_WARP_DPLUS && dv <= TV_WARP_DEG) continue;
+        const uint32_t nch = (uint32_t)((dv + TV_ITEM - 1) / TV_ITEM);
+        if (dpv <= TV_BLOCK_DPLUS) {
+            const uint32_t at = atomicAdd(&cnt[0], nch);
+            for (uint32_t c = 0; c < nch; ++c) items[at + c] = ((unsigned long long)v << 32) | c;
+        } else {
+            const uint32_t at = atomicAdd(&cnt[1], nch);
+            for (uint32_t c = 0; c < nch; ++c) items[cap - 1 - (int64_t)(at + c)] = ((unsigned long long)v << 32) | c;
+        }
+    }
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    LF_CUDA(cudaGetDevice(&dev));
+    LF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return sms > 0 ? sms : 1;
+}
+
+// Triangles of the oriented graph by their middle vertex.  `cnt` holds five
+// counters that start at zero.  Returns the number of kernels launched.
+template <typename Idx>
+int launch_tv(const int64_t *off, const int32_t *adj, const int32_t *deg, const int64_t *ooff, const int32_t *oadj,
+              int64_t n, unsigned long long *items, int64_t cap, uint32_t *cnt, unsigned long long *tri,
+              uint8_t *sup, DevScalars *ds, cudaStream_t st) {
+    constexpr size_t hs = tv_items_smem(false, sizeof(Idx)), bs = tv_items_smem(true, sizeof(Idx));
+    LF_CUDA(cudaFuncSetAttribute(k_tv_items<false, Idx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs));
+    LF_CUDA(cudaFuncSetAttribute(k_tv_items<true, Idx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs));
+    int per_sm = 0;
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tv_warp<Idx>, 256, 0));
+    const int sms = sm_count();
+    k_tv_plan<<<grid_for(n, 256, 8192), 256, 0, st>>>(off, ooff, n, items, cap, cnt);
+    LF_LAUNCHED();
+    k_tv_items<false, Idx><<<sms * 5, TV_THREADS, hs, st>>>(off, adj, deg, ooff, oadj, items, cnt, cnt + 2, tri, sup,
+                                                            ds);
+    LF_LAUNCHED();
+    k_tv_items<true, Idx><<<sms * 2, TV_THREADS, bs, st>>>(off, adj, deg, ooff, oadj, items + cap, cnt + 1, cnt + 3,
+                                                           tri, sup, ds);
+    LF_LAUNCHED();
+    k_tv_warp<Idx><<<sms * std::max(1, per_sm), 256, 0, st>>>(off, adj, deg, ooff, oadj, n, cnt + 4, tri, sup, ds);
+    LF_LAUNCHED();
+    return 4;
+}
+
+// Capacity of the item array: nodes with deg > TV_WARP_DEG or d+ > TV_WARP_DPLUS
+// number at most 2m / (TV_WARP_DPLUS + 1), plus one item per TV_ITEM entries.
+int64_t tv_item_cap(int64_t m) { return 2 * m / (TV_WARP_DPLUS + 1) + 2 * m / TV_ITEM + 2; }
 
 // ---- a4 --------------------------------------------------------------------
 __global__ void k_vt(const int64_t *ooff, const int32_t *oadj, const uint8_t *sup, int64_t n, int32_t *vt,
@@ -520,8 +1318,8 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
         dsrc = own_src;
         ddst = own_dst;
     }
-    unsigned long long *tmp64 = dalloc_n<unsigned long long>(g, 2);
-    LF_CUDA(cudaMemsetAsync(tmp64, 0, 2 * sizeof(unsigned long long), st));
+    unsigned long long *tmp64 = dalloc_n<unsigned long long>(g, 4);
+    LF_CUDA(cudaMemsetAsync(tmp64, 0, 4 * sizeof(unsigned long long), st));
     int32_t minus1 = -1;
     LF_CUDA(cudaMemcpyAsync(&ds->max_id, &minus1, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     unsigned long long nonloops = 0;
@@ -624,18 +1422,18 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
     LF_CUDA(cudaMemsetAsync(sup, 0, (size_t)(m > 0 ? m : 1), st));
     unsigned long long *utri = reinterpret_cast<unsigned long long *>(g->tri);
     if (n > 0) {
-        int32_t *hubs = dalloc_n<int32_t>(g, n);
-        uint32_t *nh = reinterpret_cast<uint32_t *>(tmp64);
-        LF_CUDA(cudaMemsetAsync(nh, 0, sizeof(uint32_t), st));
-        k_select_hubs<<<grid_for(n, 256, 8192), 256, 0, st>>>(g->ooff, n, hubs, nh); ++g->launches;
-        LF_LAUNCHED();
-        k_tri_warp<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(g->ooff, g->oadj, n, utri, sup, ds); ++g->launches;
-        LF_LAUNCHED();
-        const size_t smem = (size_t)TRI_BLOCK_LIST * 9;
-        LF_CUDA(cudaFuncSetAttribute(k_tri_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_tri_block<<<304, TRI_BLOCK_THREADS, smem, st>>>(g->ooff, g->oadj, hubs, nh, utri, sup, ds); ++g->launches;
-        LF_LAUNCHED();
-        dfree(g, hubs);
+        const int64_t cap = tv_item_cap(m);
+        unsigned long long *items = dalloc_n<unsigned long long>(g, cap);
+        // [0..1] item counts, [2..3] item counters, [4] node-run counter
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(tmp64);
+        LF_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(uint32_t), st));
+        if (m < (int64_t)INT32_MAX)
+            g->launches += launch_tv<int32_t>(g->off, g->adj, g->deg, g->ooff, g->oadj, n, items, cap, cnt, utri, sup,
+                                              ds, st);
+        else
+            g->launches += launch_tv<long long>(g->off, g->adj, g->deg, g->ooff, g->oadj, n, items, cap, cnt, utri,
+                                                sup, ds, st);
+        dfree(g, items);
     }
     pt.mark();   // 3
     if (n > 0) {
@@ -725,8 +1523,7 @@ unsigned char *noalloc_scratch() {
     if (!g_noalloc_ptr[dev]) {
         void *p = nullptr;
         LF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        LF_CUDA(cudaFuncSetAttribute(k_tri_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)((size_t)TRI_BLOCK_LIST * 9)));
+        set_triangle_attrs();
         g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
     }
     return g_noalloc_ptr[dev];
@@ -755,18 +1552,13 @@ void triangles_noalloc(const int64_t *ooff, const int32_t *oadj, int64_t n, int6
     uint8_t *sup = base + round256(sizeof(DevScalars)) + 256 + round256((size_t)n * sizeof(int32_t));
     // the array keeps the previous call's contents: clear what must start at zero
     LF_CUDA(cudaMemsetAsync(ds, 0, sizeof(DevScalars), st));
-    LF_CUDA(cudaMemsetAsync(nh, 0, sizeof(uint32_t), st));
+    LF_CUDA(cudaMemsetAsync(nh, 0, 2 * sizeof(uint32_t), st));
     if (m > 0) LF_CUDA(cudaMemsetAsync(sup, 0, (size_t)m, st));
     if (n == 0) return;
     LF_CUDA(cudaMemsetAsync(t, 0, (size_t)n * sizeof(int64_t), st));
     LF_CUDA(cudaMemsetAsync(vt, 0, (size_t)n * sizeof(int32_t), st));
     unsigned long long *utri = reinterpret_cast<unsigned long long *>(t);
-    k_select_hubs<<<grid_for(n, 256, 8192), 256, 0, st>>>(ooff, n, hubs, nh);
-    LF_LAUNCHED();
-    k_tri_warp<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(ooff, oadj, n, utri, sup, ds);
-    LF_LAUNCHED();
-    k_tri_block<<<304, TRI_BLOCK_THREADS, (size_t)TRI_BLOCK_LIST * 9, st>>>(ooff, oadj, hubs, nh, utri, sup, ds);
-    LF_LAUNCHED();
+    launch_triangles(ooff, oadj, n, hubs, nh, utri, sup, ds, st);
     k_vt<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(ooff, oadj, sup, n, vt, ds);
     LF_LAUNCHED();
 }

@@ -344,3 +344,22 @@ def random_graph(n: int, m: int, seed: int, hubs: int = 0, hub_degree: int = 0,
         src = np.concatenate([src, dst[pick]])
         dst = np.concatenate([dst, src[pick]])
     return EdgeList(src.astype(np.int32), dst.astype(np.int32), f"random_n{n}_m{m}_s{seed}")
+
+
+def wide_fan(spokes: int = 2100, leaves: int = 20000, leaf_degree: int = 252, chords: int = 5000,
+             seed: int = 0) -> EdgeList:
+    """A centre joined to `spokes` nodes that are busier than it (each leaf
+    picks `leaf_degree` random spokes, plus `chords` random spoke-spoke
+    edges), so that the degree orientation gives the centre an out-degree of
+    about `spokes` and every leaf one of `leaf_degree`: the out-degree range
+    that per-warp triangle work cannot hold."""
+    s = Stream(seed, 23)
+    centre = np.zeros(spokes, np.int64)
+    sp = np.arange(1, spokes + 1, dtype=np.int64)
+    leaf = np.repeat(np.arange(spokes + 1, spokes + 1 + leaves, dtype=np.int64), leaf_degree)
+    pick = 1 + s.integers(0, spokes, leaves * leaf_degree)
+    ca = 1 + s.integers(0, spokes, chords)
+    cb = 1 + s.integers(0, spokes, chords)
+    src = np.concatenate([centre, leaf, ca])
+    dst = np.concatenate([sp, pick, cb])
+    return EdgeList(src.astype(np.int32), dst.astype(np.int32), f"wide_fan_{spokes}_{leaves}x{leaf_degree}")

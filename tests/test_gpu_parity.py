@@ -283,6 +283,20 @@ def test_team_sizes_give_the_same_run(lf, oracle_lib, el, team, per_queue):
         compare_state(g, og)
 
 
+@pytest.mark.parametrize("spokes,leaves,leaf_degree", [(2100, 20000, 252), (600, 5000, 140)])
+def test_triangle_tiers_parity(lf, oracle_lib, spokes, leaves, leaf_degree):
+    """Out-degrees beyond one warp's list (129-2048: the block walk; above
+    2048: the big-node kernel) next to short ones: t(x,V), vt(x,V), order and
+    cc bit-exact, then two iterations with every node hub-sized."""
+    el = W.wide_fan(spokes, leaves, leaf_degree, chords=5000, seed=spokes)
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(4096, -math.inf, 2)
+    with lf.Graph(el.src, el.dst) as g:
+        compare_preprocessing(g, og)
+        compare_run(g.run(4096, -math.inf, 2), ref)
+        compare_state(g, og)
+
+
 @pytest.mark.parametrize("q", [1024, 65536])
 def test_large_shape_scaled_parity(lf, oracle_lib, q):
     """The 3.07M-node workload's shape (Chung-Lu exponent 2.2, community sizes

@@ -28,9 +28,11 @@ def lf():
     return lazyfox
 
 
-def test_noalloc_triangles_equal_the_allocating_path_twice(lf):
+@pytest.mark.parametrize("make", [lambda: W.dblp_like(seed=5, scale=0.05), lambda: W.wide_fan(seed=9)],
+                         ids=["dblp_like_5pct", "wide_fan"])
+def test_noalloc_triangles_equal_the_allocating_path_twice(lf, make):
     import torch
-    el = W.dblp_like(seed=5, scale=0.05)
+    el = make()
     with lf.Graph(el.src, el.dst) as g:
         t_ref, vt_ref, _ = g.node_stats()
         ooff, oadj = g.oriented()
