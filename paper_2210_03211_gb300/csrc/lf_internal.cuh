@@ -153,8 +153,26 @@ struct lf_graph {
     int32_t *hub_scratch = nullptr;
     int64_t hub_slots = 0;
     std::vector<int64_t> hub_qoff_host;
+    // chunks of HUGE_CHUNK neighbours per hub: (hub, chunk) pairs listed per
+    // queue, chunks per hub, chunks finished per hub (zero between queues)
+    int32_t *hub_chunk_h = nullptr;
+    int32_t *hub_chunk_c = nullptr;
+    int32_t *hub_nch = nullptr;
+    uint32_t *hub_done = nullptr;
+    uint32_t *hub_ncand = nullptr;      // distinct ids in each hub's table, listed in its lower-bound area
+    std::vector<int64_t> hub_cqoff_host;
     int64_t hub_plan_q = 0;
     int32_t hub_plan_K = 0;
+    // nodes of degree > TOT_CHUNK in the WCC-hat total, counted in chunks of
+    // neighbours (plan for row capacity tot_plan_K)
+    int32_t *tot_hubs = nullptr;        // node ids, degree descending
+    int32_t *tot_chunk_hub = nullptr;   // hub index of each chunk
+    int32_t *tot_first = nullptr;       // first chunk of each hub (tot_nh + 1 entries)
+    int32_t *tot_cnt = nullptr;         // tot_nh x tot_plan_K counts, zero between launches
+    uint32_t *tot_done = nullptr;       // chunks finished per hub, zero between launches
+    uint32_t *tot_next = nullptr;       // work counters: node runs, chunks
+    int64_t tot_nh = 0, tot_nchunks = 0;
+    int32_t tot_plan_K = 0;
 };
 
 namespace lf {

@@ -55,10 +55,23 @@ struct RunArgs {
     uint32_t *hvals;
     float *hub_ub;
     float *hub_lb;
+    const int32_t *hub_chunk_h;   // per-queue launches: hub and chunk of each block
+    const int32_t *hub_chunk_c;
+    const int32_t *hub_nch;
+    uint32_t *hub_done;
+    uint32_t *hub_ncand;
     unsigned long long *qtimes;   // profile mode: time stamp after each queue (persistent kernel)
     int32_t screen;    // 1: rule candidates out with the FP32 bound first
     float cc32;        // cc rounded to float (screen)
     float delta;       // relative error bound of the screen (see score32)
+    // WCC-hat total: nodes of degree > TOT_CHUNK are counted in chunks
+    const int32_t *tot_hubs;
+    const int32_t *tot_chunk_hub;
+    const int32_t *tot_first;
+    int32_t *tot_cnt;
+    uint32_t *tot_done;
+    uint32_t *tot_next;
+    int64_t tot_nchunks;
 };
 
 // ---------------------------------------------------------------------------
@@ -773,6 +786,10 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
     __syncthreads();
 }
 
+__device__ __forceinline__ unsigned long long queue_serial(const RunArgs &a, int64_t bidx) {
+    return (unsigned long long)__ldcg(&a.ds->iter) * (unsigned long long)a.nbatches + (unsigned long long)bidx + 1ull;
+}
+
 // The hubs of queue b, one block each (block-strided), each with its own
 // hash table in global memory sized for (d+1) x K entries when the run was
 // planned: one pass over the neighbours however many distinct communities
@@ -799,6 +816,167 @@ __device__ void eval_huge(const RunArgs &a, int64_t bstart, int64_t b, unsigned 
         const uint32_t cap = a.hub_tcap[h];
         eval_block(a, (int)(p - bstart), x, entries, a.hkeys + t0, a.hvals + t0, a.hub_ub + t0, bkey, bval, bs, serial,
                    a.hub_lb + t0, cap);
+        for (uint32_t s = threadIdx.x; s < cap; s += EV_THREADS) {   // tables are left clean between uses
+            a.hkeys[t0 + s] = EMPTY_KEY;
+            a.hvals[t0 + s] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+// Insert into a hub's global table; a new id also gets its slot appended to
+// the hub's list of occupied slots.  False if the table is full.
+__device__ __forceinline__ bool hub_insert(int32_t *keys, uint32_t *vals, uint32_t hm, int32_t key, uint32_t add,
+                                           bool own, int32_t *list, uint32_t *ncand) {
+    uint32_t h = hash32((uint32_t)key) & hm;
+    for (uint32_t probe = 0; probe <= hm; ++probe) {
+        const int32_t prev = atomicCAS(&keys[h], EMPTY_KEY, key);
+        if (prev == EMPTY_KEY || prev == key) {
+            if (own) atomicOr(&vals[h], OWN_FLAG);
+            else atomicAdd(&vals[h], add);
+            if (prev == EMPTY_KEY) list[atomicAdd(ncand, 1u)] = (int32_t)h;
+            return true;
+        }
+        h = (h + 1) & hm;
+    }
+    return false;
+}
+
+// Per-queue launches: one block per chunk of HUGE_CHUNK neighbours of a hub.
+// Each block adds its neighbours' memberships to the hub's table in global
+// memory (the first chunk also the hub's own row); the block that finishes
+// the hub's last chunk screens and evaluates the candidates, records the
+// actions and clears the table.
+constexpr int HUGE_CHUNK = 2048;
+
+__device__ void huge_decide(const RunArgs &a, int i, int32_t d, int32_t cx, const int32_t *keys, const uint32_t *vals,
+                            float *ubs, float *lbs, uint32_t H, int32_t *bkey, uint32_t *bval, BlockScratch &bs,
+                            unsigned long long serial) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t slice = (H + EV_WARPS - 1) / EV_WARPS;
+    const uint32_t lo = min(H, (uint32_t)w * slice), hi = min(H, lo + slice);
+    float lbj = -INFINITY, lbl = -INFINITY;
+    if (a.screen) {
+        float wj = lbj, wl = lbl;
+        screen_bounds(a, keys, vals, ubs, lbs, lo, hi, d, wj, wl);
+        wj = warp_max_f(wj);
+        wl = warp_max_f(wl);
+        if (lane == 0) {
+            bs.lbj[w] = wj;
+            bs.lbl[w] = wl;
+        }
+        __syncthreads();
+        for (int ww = 0; ww < EV_WARPS; ++ww) {
+            lbj = fmaxf(lbj, bs.lbj[ww]);
+            lbl = fmaxf(lbl, bs.lbl[ww]);
+        }
+    }
+    Best bj{0.0, -1, 0}, bl{0.0, -1, 0};
+    eval_survivors(a, keys, vals, ubs, lo, hi, d, lbj, lbl, true, true, bkey, bval, bj, bl);
+    if (a.profile) {
+        unsigned long long pb = 0;
+        for (uint32_t s = lo + lane; s < hi; s += 32) pb += keys[s] != EMPTY_KEY ? 16ull : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pb += __shfl_down_sync(FULL, pb, o);
+        if (lane == 0) atomicAdd(&a.ds->prof_bytes, pb + (w == 0 ? 44ull + 4ull * (unsigned long long)cx : 0ull));
+    }
+    warp_best(bj);
+    warp_best(bl);
+    if (lane == 0) {
+        bs.gj[w] = bj.g; bs.cj[w] = bj.c; bs.kj[w] = bj.k;
+        bs.gl[w] = bl.g; bs.cl[w] = bl.c; bs.kl[w] = bl.k;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Best fj{0.0, -1, 0}, fl{0.0, -1, 0};
+        for (int ww = 0; ww < EV_WARPS; ++ww) {
+            if (better(bs.gj[ww], bs.cj[ww], fj.g, fj.c)) fj = Best{bs.gj[ww], bs.cj[ww], bs.kj[ww]};
+            if (better(bs.gl[ww], bs.cl[ww], fl.g, fl.c)) fl = Best{bs.gl[ww], bs.cl[ww], bs.kl[ww]};
+        }
+        write_action(a, i, fj, fl, serial);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(EV_THREADS) k_huge_chunks(RunArgs a, int64_t bstart, int64_t bidx, int64_t cbase) {
+    __shared__ BlockScratch bs;
+    __shared__ int32_t bkey[EV_WARPS][32];
+    __shared__ uint32_t bval[EV_WARPS][32];
+    __shared__ unsigned s_last;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t ch = cbase + blockIdx.x;
+    const int h = a.hub_chunk_h[ch];
+    const int c = a.hub_chunk_c[ch];
+    const int64_t p = a.hub_pos[h];
+    const int32_t x = a.order[p];
+    const int64_t t0 = a.hub_toff[h];
+    const uint32_t cap = a.hub_tcap[h], hm = cap - 1;
+    int32_t *keys = a.hkeys + t0;
+    uint32_t *vals = a.hvals + t0;
+    int32_t *list = reinterpret_cast<int32_t *>(a.hub_lb + t0);   // occupied slots, in order of arrival
+    const int32_t cx = __ldcg(&a.nmem[x]);
+    const int64_t beg = a.off[x] + (int64_t)c * HUGE_CHUNK;
+    const int64_t end = min(a.off[x + 1], beg + HUGE_CHUNK);
+    bool bad = false;
+    if (c == 0) {
+        const int32_t *rowx = a.mem + (int64_t)x * a.K;
+        for (int j = threadIdx.x; j < cx; j += EV_THREADS)
+            if (!hub_insert(keys, vals, hm, __ldcg(&rowx[j]), 0u, true, list, &a.hub_ncand[h])) bad = true;
+    }
+    unsigned long long pb = 0;
+    for (int64_t p0 = beg + w * 32; p0 < end; p0 += EV_THREADS) {
+        const int64_t q = p0 + lane;
+        int32_t y = 0, cy = 0;
+        if (q < end) {
+            y = a.adj[q];
+            cy = __ldcg(&a.nmem[y]);
+            pb += 8ull + 4ull * (unsigned long long)cy;
+        }
+        const int32_t cmax = __reduce_max_sync(FULL, cy);
+        const int32_t *rowy = a.mem + (int64_t)y * a.K;
+        int4 r0, r1;
+        row_head(rowy, cy, r0, r1);
+        for (int s = 0; s < cmax; ++s) {
+            const int32_t C = s < cy ? row_entry(r0, r1, rowy, s) : -2 - lane;
+            const unsigned mask = __match_any_sync(FULL, C);
+            if (C >= 0 && lane == __ffs(mask) - 1)
+                if (!hub_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false, list, &a.hub_ncand[h])) bad = true;
+        }
+    }
+    if (bad) atomicOr(&a.ds->err, DERR_CHECK);   // the planned table bounds every entry: cannot happen
+    if (a.profile) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pb += __shfl_down_sync(FULL, pb, o);
+        if (lane == 0 && pb) atomicAdd(&a.ds->prof_bytes, pb);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.hub_done[h], 1u) == (unsigned)(a.hub_nch[h] - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();   // every chunk's insertions are visible from here on
+    // dense candidates: ids into the upper-bound area, counts over the slot
+    // list; the table is cleared as it is read and then holds the bounds
+    const uint32_t ncand = __ldcg(&a.hub_ncand[h]);
+    int32_t *ck = reinterpret_cast<int32_t *>(a.hub_ub + t0);
+    uint32_t *cv = reinterpret_cast<uint32_t *>(list);
+    for (uint32_t k = threadIdx.x; k < ncand; k += EV_THREADS) {
+        const int32_t sl = __ldcg(&list[k]);
+        ck[k] = __ldcg(&keys[sl]);
+        cv[k] = __ldcg(&vals[sl]);
+        keys[sl] = EMPTY_KEY;
+        vals[sl] = 0u;
+    }
+    __syncthreads();
+    huge_decide(a, (int)(p - bstart), a.deg[x], cx, ck, cv, reinterpret_cast<float *>(keys),
+                reinterpret_cast<float *>(vals), ncand, bkey[w], bval[w], bs, queue_serial(a, bidx));
+    for (uint32_t k = threadIdx.x; k < ncand; k += EV_THREADS) {   // the bounds' slots back to empty
+        keys[k] = EMPTY_KEY;
+        vals[k] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        a.hub_done[h] = 0u;
+        a.hub_ncand[h] = 0u;
     }
 }
 
@@ -901,10 +1079,6 @@ __device__ void eval_group(const RunArgs &a, int64_t bstart, int32_t blen, int b
         eval_block(a, ih, x, (int64_t)es.hub_bound[h], s_keys, s_vals, s_ub, es.bkey[w], es.bval[w], es.bs, serial);
     }
     __syncthreads();
-}
-
-__device__ __forceinline__ unsigned long long queue_serial(const RunArgs &a, int64_t bidx) {
-    return (unsigned long long)__ldcg(&a.ds->iter) * (unsigned long long)a.nbatches + (unsigned long long)bidx + 1ull;
 }
 
 __global__ void __launch_bounds__(EV_THREADS) k_eval_huge(RunArgs a, int64_t bstart, int64_t bidx) {
@@ -1434,75 +1608,231 @@ __device__ __forceinline__ bool row_has(const int32_t *row, int32_t c, int32_t C
 }
 
 // WCC-hat(P) = sum over memberships (x, C) of WCC-hat(x, C), with
-// deg(x, C) counted over x's neighbours in one pass (each neighbour's row is
-// looked up in x's own row); exact sum, so the total does not depend on the
-// order of the additions.
+// deg(x, C) counted over x's neighbours; exact sum, so the total does not
+// depend on the order of the additions.  Warps take runs of node ids from a
+// counter; a node of degree > TOT_CHUNK is counted in chunks of TOT_CHUNK
+// neighbours taken from a second counter, each chunk adding its counts to the
+// node's counters in global memory, and the warp that finishes the node's
+// last chunk evaluates its memberships (and clears the counters).
 constexpr int TOT_WARPS = 8;
-constexpr int TOT_ROW = 64;   // own rows up to this length are counted in one pass
+constexpr int TOT_ROW = 64;      // own rows up to this length are counted in one pass
+constexpr int TOT_CHUNK = 1024;  // neighbours per work unit of a high-degree node
+constexpr int TOT_BATCH = 32;    // node ids per grab
+
+// Own row of at most four communities held in registers: each lane counts
+// its neighbours' memberships against them (rows ascending, -1 past the end),
+// four neighbours per step with their loads issued together.
+__device__ __forceinline__ void tot_match(int32_t C, const int4 &rx, int &k0, int &k1, int &k2, int &k3) {
+    k0 += C == rx.x;
+    k1 += C == rx.y;
+    k2 += C == rx.z;
+    k3 += C == rx.w;
+}
+
+__device__ __forceinline__ void tot_count4(const RunArgs &a, int64_t pb, int64_t pe, const int4 &rx, int &k0, int &k1,
+                                           int &k2, int &k3) {
+    const int lane = threadIdx.x & 31;
+    constexpr int U = 4;
+    for (int64_t p0 = pb; p0 < pe; p0 += 32 * U) {
+        int32_t y[U], cy[U];
+        int4 r[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const int64_t p = p0 + j * 32 + lane;
+            y[j] = p < pe ? a.adj[p] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            cy[j] = y[j] >= 0 ? __ldcg(&a.nmem[y[j]]) : 0;
+            r[j] = y[j] >= 0 ? __ldcg(reinterpret_cast<const int4 *>(a.mem + (int64_t)y[j] * a.K))
+                             : make_int4(-1, -1, -1, -1);
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (cy[j] > 0) tot_match(r[j].x, rx, k0, k1, k2, k3);
+            if (cy[j] > 1) tot_match(r[j].y, rx, k0, k1, k2, k3);
+            if (cy[j] > 2) tot_match(r[j].z, rx, k0, k1, k2, k3);
+            if (cy[j] > 3) tot_match(r[j].w, rx, k0, k1, k2, k3);
+            for (int32_t s = 4; s < cy[j]; ++s)
+                tot_match(__ldcg(&a.mem[(int64_t)y[j] * a.K + s]), rx, k0, k1, k2, k3);
+        }
+    }
+}
+
+// Counts of the c <= TOT_ROW communities in row_s (ascending, shared) among
+// neighbours [pb, pe), added to cnt_s.
+__device__ __forceinline__ void tot_count_smem(const RunArgs &a, int64_t pb, int64_t pe, const int32_t *row_s, int c,
+                                               int32_t *cnt_s) {
+    const int lane = threadIdx.x & 31;
+    const int32_t lo = row_s[0], hi = row_s[c - 1];
+    for (int64_t p = pb + lane; p < pe; p += 32) {
+        const int32_t y = a.adj[p];
+        const int32_t cy = __ldcg(&a.nmem[y]);
+        const int32_t *ry = a.mem + (int64_t)y * a.K;
+        for (int32_t s = 0; s < cy; ++s) {
+            const int32_t C = __ldcg(&ry[s]);
+            if (C < lo) continue;
+            if (C > hi) break;
+            int l = 0, h = c - 1;
+            while (l <= h) {
+                const int mid = (l + h) >> 1;
+                const int32_t v = row_s[mid];
+                if (v == C) {
+                    atomicAdd(&cnt_s[mid], 1);
+                    break;
+                }
+                if (v < C) l = mid + 1; else h = mid - 1;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tot_member(const RunArgs &a, unsigned long long *acc, int32_t C, int64_t k,
+                                           int32_t d) {
+    const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
+    sacc_add(acc, wcchat_member(k, d, r.x, (uint32_t)r.y, a.cc));
+}
+
+// Memberships waiting for their FP64 term, per warp: evaluated 32 at a time so
+// that the (slow) double-precision pipe runs with every lane busy.
+struct TotBuf {
+    int32_t *C, *k, *d;
+    int n;
+};
+
+__device__ __forceinline__ void tot_flush(const RunArgs &a, unsigned long long *acc, TotBuf &b) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    if (lane < b.n) tot_member(a, acc, b.C[lane], b.k[lane], b.d[lane]);
+    __syncwarp();
+    b.n = 0;
+}
+
+// Warp-collective: lanes with `has` queue (C, k, d).
+__device__ __forceinline__ void tot_push(const RunArgs &a, unsigned long long *acc, TotBuf &b, bool has, int32_t C,
+                                         int32_t k, int32_t d) {
+    const unsigned m = __ballot_sync(FULL, has);
+    const int cnt = __popc(m);
+    if (cnt == 0) return;
+    if (b.n + cnt > 32) tot_flush(a, acc, b);
+    if (has) {
+        const int s = b.n + __popc(m & lanemask_lt());
+        b.C[s] = C;
+        b.k[s] = k;
+        b.d[s] = d;
+    }
+    b.n += cnt;
+}
+
+// deg(x, C) for x's memberships over neighbours [pb, pe).  whole: add the
+// node's terms to acc; otherwise add the counts to the node's global counters
+// `gcnt`.
+__device__ void tot_node(const RunArgs &a, int32_t x, int64_t pb, int64_t pe, bool whole, int32_t *gcnt,
+                         unsigned long long *acc, TotBuf &buf, int32_t *row_s, int32_t *cnt_s) {
+    const int lane = threadIdx.x & 31;
+    const int32_t c = __ldcg(&a.nmem[x]);
+    const int32_t d = a.deg[x];
+    const int32_t *row = a.mem + (int64_t)x * a.K;
+    if (c <= 4) {
+        int4 rx = __ldcg(reinterpret_cast<const int4 *>(row));
+        if (c < 2) rx.y = -3;
+        if (c < 3) rx.z = -3;
+        if (c < 4) rx.w = -3;
+        int k0 = 0, k1 = 0, k2 = 0, k3 = 0;
+        tot_count4(a, pb, pe, rx, k0, k1, k2, k3);
+        k0 = __reduce_add_sync(FULL, k0);
+        k1 = __reduce_add_sync(FULL, k1);
+        k2 = __reduce_add_sync(FULL, k2);
+        k3 = __reduce_add_sync(FULL, k3);
+        const int k = lane == 0 ? k0 : lane == 1 ? k1 : lane == 2 ? k2 : k3;
+        const int32_t C = lane == 0 ? rx.x : lane == 1 ? rx.y : lane == 2 ? rx.z : rx.w;
+        if (whole) tot_push(a, acc, buf, lane < c, C, k, d);
+        else if (lane < c && k) atomicAdd(&gcnt[lane], k);
+    } else if (c <= TOT_ROW) {
+        for (int j = lane; j < c; j += 32) {
+            row_s[j] = __ldcg(&row[j]);
+            cnt_s[j] = 0;
+        }
+        __syncwarp();
+        tot_count_smem(a, pb, pe, row_s, c, cnt_s);
+        __syncwarp();
+        for (int j0 = 0; j0 < c; j0 += 32) {
+            const int j = j0 + lane;
+            const int32_t C = j < c ? row_s[j] : 0, k = j < c ? cnt_s[j] : 0;
+            if (whole) tot_push(a, acc, buf, j < c, C, k, d);
+            else if (j < c && k) atomicAdd(&gcnt[j], k);
+        }
+        __syncwarp();
+    } else {
+        for (int32_t s = 0; s < c; ++s) {
+            const int32_t C = __ldcg(&row[s]);
+            int cnt = 0;
+            for (int64_t p = pb + lane; p < pe; p += 32) {
+                const int32_t y = a.adj[p];
+                cnt += row_has(a.mem + (int64_t)y * a.K, __ldcg(&a.nmem[y]), C);
+            }
+            cnt = __reduce_add_sync(FULL, cnt);
+            if (whole) tot_push(a, acc, buf, lane == 0, C, cnt, d);
+            else if (lane == 0 && cnt) atomicAdd(&gcnt[s], cnt);
+        }
+    }
+}
 
 __global__ void __launch_bounds__(TOT_WARPS * 32) k_total(RunArgs a, int64_t n) {
     __shared__ unsigned long long acc[SACC_CHUNKS];
     __shared__ int32_t s_row[TOT_WARPS][TOT_ROW];
     __shared__ int32_t s_cnt[TOT_WARPS][TOT_ROW];
+    __shared__ int32_t s_buf[TOT_WARPS][3][32];
     for (int s = threadIdx.x; s < SACC_CHUNKS; s += blockDim.x) acc[s] = 0ull;
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t *row_s = s_row[w], *cnt_s = s_cnt[w];
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
-        const int32_t c = a.nmem[x];
-        if (c == 0) continue;
-        const int32_t d = a.deg[x];
-        const int32_t *row = a.mem + x * a.K;
-        if (c <= TOT_ROW) {
-            for (int j = lane; j < c; j += 32) {
-                row_s[j] = row[j];
-                cnt_s[j] = 0;
-            }
-            __syncwarp();
-            const int32_t lo = row_s[0], hi = row_s[c - 1];
-            for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
-                const int32_t y = a.adj[p];
-                const int32_t cy = a.nmem[y];
-                const int32_t *ry = a.mem + (int64_t)y * a.K;
-                for (int32_t s = 0; s < cy; ++s) {
-                    const int32_t C = ry[s];
-                    if (C < lo) continue;
-                    if (C > hi) break;
-                    int l = 0, h = c - 1;   // rows are ascending
-                    while (l <= h) {
-                        const int mid = (l + h) >> 1;
-                        const int32_t v = row_s[mid];
-                        if (v == C) {
-                            atomicAdd(&cnt_s[mid], 1);
-                            break;
-                        }
-                        if (v < C) l = mid + 1; else h = mid - 1;
-                    }
-                }
-            }
-            __syncwarp();
-            for (int j = lane; j < c; j += 32) {
-                const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[row_s[j]]));
-                sacc_add(acc, wcchat_member(cnt_s[j], d, r.x, (uint32_t)r.y, a.cc));
-            }
-            __syncwarp();
-        } else {
-            for (int32_t s = 0; s < c; ++s) {
-                const int32_t C = row[s];
-                int cnt = 0;
-                for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
-                    const int32_t y = a.adj[p];
-                    cnt += row_has(a.mem + (int64_t)y * a.K, a.nmem[y], C);
-                }
-                cnt = __reduce_add_sync(FULL, cnt);
-                if (lane == 0) {
-                    const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
-                    sacc_add(acc, wcchat_member(cnt, d, r.x, (uint32_t)r.y, a.cc));
-                }
-            }
+    TotBuf buf{s_buf[w][0], s_buf[w][1], s_buf[w][2], 0};
+    // nodes of degree <= TOT_CHUNK, whole
+    for (;;) {
+        long long b0 = 0;
+        if (lane == 0) b0 = (long long)atomicAdd(&a.tot_next[0], 1u) * TOT_BATCH;
+        b0 = __shfl_sync(FULL, b0, 0);
+        if (b0 >= n) break;
+        const int64_t bend = min(n, (int64_t)b0 + TOT_BATCH);
+        for (int64_t x = b0; x < bend; ++x) {
+            if (__ldcg(&a.nmem[x]) == 0) continue;
+            const int64_t pb = a.off[x], pe = a.off[x + 1];
+            if (pe - pb > TOT_CHUNK) continue;
+            tot_node(a, (int32_t)x, pb, pe, true, nullptr, acc, buf, row_s, cnt_s);
         }
     }
+    // chunks of the larger nodes
+    for (;;) {
+        long long ch = 0;
+        if (lane == 0) ch = (long long)atomicAdd(&a.tot_next[1], 1u);
+        ch = __shfl_sync(FULL, ch, 0);
+        if (ch >= a.tot_nchunks) break;
+        const int h = a.tot_chunk_hub[ch];
+        const int32_t x = a.tot_hubs[h];
+        const int nch = a.tot_first[h + 1] - a.tot_first[h];
+        const int64_t pb = a.off[x] + (int64_t)(ch - a.tot_first[h]) * TOT_CHUNK;
+        const int64_t pe = min(a.off[x + 1], pb + TOT_CHUNK);
+        int32_t *gcnt = a.tot_cnt + (int64_t)h * a.K;
+        const int32_t c = __ldcg(&a.nmem[x]);
+        if (c > 0) tot_node(a, x, pb, pe, false, gcnt, acc, buf, row_s, cnt_s);
+        __threadfence();
+        unsigned old = 0;
+        if (lane == 0) old = atomicAdd(&a.tot_done[h], 1u);
+        old = __shfl_sync(FULL, old, 0);
+        if (old == (unsigned)(nch - 1)) {   // last chunk of x: its counts are complete
+            __threadfence();
+            const int32_t d = a.deg[x];
+            const int32_t *row = a.mem + (int64_t)x * a.K;
+            for (int j0 = 0; j0 < c; j0 += 32) {
+                const int j = j0 + lane;
+                const int32_t C = j < c ? __ldcg(&row[j]) : 0, k = j < c ? atomicExch(&gcnt[j], 0) : 0;
+                tot_push(a, acc, buf, j < c, C, k, d);
+            }
+            if (lane == 0) a.tot_done[h] = 0u;
+        }
+    }
+    if (buf.n > 0) tot_flush(a, acc, buf);
     __syncthreads();
     for (int s = threadIdx.x; s < SACC_CHUNKS; s += blockDim.x)
         if (acc[s]) atomicAdd(&a.ds->sacc[s], acc[s]);
@@ -1566,6 +1896,11 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.hvals = reinterpret_cast<uint32_t *>(g->hub_scratch + g->hub_slots);
     a.hub_ub = reinterpret_cast<float *>(g->hub_scratch + 2 * g->hub_slots);
     a.hub_lb = reinterpret_cast<float *>(g->hub_scratch + 3 * g->hub_slots);
+    a.hub_chunk_h = g->hub_chunk_h;
+    a.hub_chunk_c = g->hub_chunk_c;
+    a.hub_nch = g->hub_nch;
+    a.hub_done = g->hub_done;
+    a.hub_ncand = g->hub_ncand;
     // FP32 screen: cc must be a normal float with room to spare; delta bounds
     // 15 FP32 roundings (20 ulp) and the FP32 subtraction, the FP64 estimator's error u (m2 + 3 vol +
     // 17) with m2, vol <= 2m, the two gain subtractions, and a 2% margin.
@@ -1573,6 +1908,13 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.cc32 = (float)g->cc;
     const double u64 = 1.1102230246251565e-16, u32 = 5.960464477539063e-08;
     a.delta = (float)(1.02 * (21.0 * u32 + u64 * (200.0 + 8.0 * (double)g->m) + 2.0 * u64) + 1e-9);
+    a.tot_hubs = g->tot_hubs;
+    a.tot_chunk_hub = g->tot_chunk_hub;
+    a.tot_first = g->tot_first;
+    a.tot_cnt = g->tot_cnt;
+    a.tot_done = g->tot_done;
+    a.tot_next = g->tot_next;
+    a.tot_nchunks = g->tot_nchunks;
     return a;
 }
 
@@ -1628,9 +1970,10 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
         const int64_t bstart = b * q;
         const int32_t blen = (int32_t)std::min<int64_t>(q, g->n - bstart);
         if (prof) record_event(g, g->prof_ev[2 * b], capturing);
-        const int64_t nh = g->hub_qoff_host.empty() ? 0 : g->hub_qoff_host[(size_t)b + 1] - g->hub_qoff_host[(size_t)b];
-        if (nh > 0) {
-            k_eval_huge<<<(unsigned)nh, EV_THREADS, 0, g->stream>>>(a, bstart, b);
+        const int64_t nch =
+            g->hub_cqoff_host.empty() ? 0 : g->hub_cqoff_host[(size_t)b + 1] - g->hub_cqoff_host[(size_t)b];
+        if (nch > 0) {
+            k_huge_chunks<<<(unsigned)nch, EV_THREADS, 0, g->stream>>>(a, bstart, b, g->hub_cqoff_host[(size_t)b]);
             ++g->launches;
         }
         switch (T) {
@@ -1646,10 +1989,19 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
     LF_LAUNCHED();
 }
 
+// The WCC-hat total on a resident grid (work is handed out by counters).
+void launch_total(lf_graph *g, const RunArgs &a) {
+    static int per_sm = 0;
+    if (per_sm == 0) LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_total, TOT_WARPS * 32, 0));
+    LF_CUDA(cudaMemsetAsync(g->tot_next, 0, 2 * sizeof(uint32_t), g->stream));
+    k_total<<<num_sms() * std::max(1, per_sm), TOT_WARPS * 32, 0, g->stream>>>(a, g->n);
+    ++g->launches;
+}
+
 void launch_iteration_end(lf_graph *g, const RunArgs &a) {
     const int64_t n = g->n;
     k_prune<<<grid_for(n + g->ncomm, 256, 1 << 16), 256, 0, g->stream>>>(a, n, g->ncomm); ++g->launches;
-    k_total<<<grid_for(n * 32, TOT_WARPS * 32, 1 << 16), TOT_WARPS * 32, 0, g->stream>>>(a, n); ++g->launches;
+    launch_total(g, a);
     k_finalize<<<1, 32, 0, g->stream>>>(g->ds, device_readback(g), 1); ++g->launches;
     LF_LAUNCHED();
     LF_CUDA(cudaMemcpyAsync(g->rb, device_readback(g), sizeof(Readback), cudaMemcpyDeviceToHost, g->stream));
@@ -1748,6 +2100,14 @@ void free_hub_plan(lf_graph *g) {
     if (g->hub_toff) dfree(g, g->hub_toff);
     if (g->hub_tcap) dfree(g, g->hub_tcap);
     if (g->hub_scratch) dfree(g, g->hub_scratch);
+    if (g->hub_chunk_h) dfree(g, g->hub_chunk_h);
+    if (g->hub_chunk_c) dfree(g, g->hub_chunk_c);
+    if (g->hub_nch) dfree(g, g->hub_nch);
+    if (g->hub_done) dfree(g, g->hub_done);
+    if (g->hub_ncand) dfree(g, g->hub_ncand);
+    g->hub_chunk_h = g->hub_chunk_c = g->hub_nch = nullptr;
+    g->hub_done = g->hub_ncand = nullptr;
+    g->hub_cqoff_host.clear();
     g->hub_pos = nullptr;
     g->hub_qoff = nullptr;
     g->hub_toff = nullptr;
@@ -1775,19 +2135,26 @@ void build_hub_plan(lf_graph *g, int64_t q) {
     LF_CUDA(cudaMemcpyAsync(deg.data(), g->deg, (size_t)n * 4, cudaMemcpyDeviceToHost, g->stream));
     LF_CUDA(cudaStreamSynchronize(g->stream));
     const int64_t nb = (n + q - 1) / q;
-    std::vector<int32_t> pos;
-    std::vector<int64_t> qoff((size_t)nb + 1, 0), toff;
+    std::vector<int32_t> pos, nch, chunk_h, chunk_c;
+    std::vector<int64_t> qoff((size_t)nb + 1, 0), cqoff((size_t)nb + 1, 0), toff;
     std::vector<uint32_t> tcap;
     int64_t slots = 0;
     for (int64_t b = 0; b < nb; ++b) {
         qoff[(size_t)b] = (int64_t)pos.size();
+        cqoff[(size_t)b] = (int64_t)chunk_h.size();
         int64_t used = 0;
         for (int64_t p = b * q; p < std::min(n, (b + 1) * q); ++p) {
             const int32_t d = deg[(size_t)order[(size_t)p]];
             if (d <= HUGE_DEG) continue;
             uint64_t cap = 32;
             while (cap < 2ull * (uint64_t)(d + 1) * (uint64_t)g->K) cap <<= 1;
+            const int32_t c = (d + HUGE_CHUNK - 1) / HUGE_CHUNK;
+            for (int32_t k = 0; k < c; ++k) {
+                chunk_h.push_back((int32_t)pos.size());
+                chunk_c.push_back(k);
+            }
             pos.push_back((int32_t)p);
+            nch.push_back(c);
             toff.push_back(used);
             tcap.push_back((uint32_t)cap);
             used += (int64_t)cap;
@@ -1795,8 +2162,15 @@ void build_hub_plan(lf_graph *g, int64_t q) {
         slots = std::max(slots, used);
     }
     qoff[(size_t)nb] = (int64_t)pos.size();
+    cqoff[(size_t)nb] = (int64_t)chunk_h.size();
     g->hub_qoff_host = qoff;
+    g->hub_cqoff_host = cqoff;
     if (pos.empty()) return;
+    const int64_t NC = (int64_t)chunk_h.size();
+    g->hub_chunk_h = dalloc_n<int32_t>(g, NC);
+    g->hub_chunk_c = dalloc_n<int32_t>(g, NC);
+    LF_CUDA(cudaMemcpyAsync(g->hub_chunk_h, chunk_h.data(), (size_t)NC * 4, cudaMemcpyHostToDevice, g->stream));
+    LF_CUDA(cudaMemcpyAsync(g->hub_chunk_c, chunk_c.data(), (size_t)NC * 4, cudaMemcpyHostToDevice, g->stream));
     const int64_t H = (int64_t)pos.size();
     g->hub_pos = dalloc_n<int32_t>(g, H);
     g->hub_qoff = dalloc_n<int64_t>(g, nb + 1);
@@ -1804,10 +2178,71 @@ void build_hub_plan(lf_graph *g, int64_t q) {
     g->hub_tcap = dalloc_n<uint32_t>(g, H);
     g->hub_scratch = dalloc_n<int32_t>(g, 4 * slots);
     g->hub_slots = slots;
+    g->hub_nch = dalloc_n<int32_t>(g, H);
+    g->hub_done = dalloc_n<uint32_t>(g, H);
+    g->hub_ncand = dalloc_n<uint32_t>(g, H);
+    LF_CUDA(cudaMemcpyAsync(g->hub_nch, nch.data(), (size_t)H * 4, cudaMemcpyHostToDevice, g->stream));
+    LF_CUDA(cudaMemsetAsync(g->hub_done, 0, (size_t)H * 4, g->stream));
+    LF_CUDA(cudaMemsetAsync(g->hub_ncand, 0, (size_t)H * 4, g->stream));
+    // tables start clean (keys empty, counts zero) and are left clean after each use
+    LF_CUDA(cudaMemsetAsync(g->hub_scratch, 0xff, (size_t)slots * 4, g->stream));
+    LF_CUDA(cudaMemsetAsync(g->hub_scratch + slots, 0, (size_t)slots * 4, g->stream));
     LF_CUDA(cudaMemcpyAsync(g->hub_pos, pos.data(), (size_t)H * 4, cudaMemcpyHostToDevice, g->stream));
     LF_CUDA(cudaMemcpyAsync(g->hub_qoff, qoff.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice, g->stream));
     LF_CUDA(cudaMemcpyAsync(g->hub_toff, toff.data(), (size_t)H * 8, cudaMemcpyHostToDevice, g->stream));
     LF_CUDA(cudaMemcpyAsync(g->hub_tcap, tcap.data(), (size_t)H * 4, cudaMemcpyHostToDevice, g->stream));
+    LF_CUDA(cudaStreamSynchronize(g->stream));
+}
+
+void free_total_plan(lf_graph *g) {
+    for (int32_t **p : {&g->tot_hubs, &g->tot_chunk_hub, &g->tot_first, &g->tot_cnt})
+        if (*p) {
+            dfree(g, *p);
+            *p = nullptr;
+        }
+    if (g->tot_done) dfree(g, g->tot_done);
+    if (g->tot_next) dfree(g, g->tot_next);
+    g->tot_done = g->tot_next = nullptr;
+    g->tot_nh = g->tot_nchunks = 0;
+    g->tot_plan_K = 0;
+}
+
+// Nodes of degree > TOT_CHUNK for the WCC-hat total, largest first, with one
+// chunk per TOT_CHUNK neighbours, and their zeroed counters (K per node).
+void build_total_plan(lf_graph *g) {
+    if (g->tot_next && g->tot_plan_K == g->K) return;
+    free_total_plan(g);
+    g->tot_plan_K = g->K;
+    g->tot_next = dalloc_n<uint32_t>(g, 2);
+    const int64_t n = g->n;
+    if (n == 0 || g->max_deg <= TOT_CHUNK) return;
+    std::vector<int32_t> deg((size_t)n);
+    LF_CUDA(cudaMemcpyAsync(deg.data(), g->deg, (size_t)n * 4, cudaMemcpyDeviceToHost, g->stream));
+    LF_CUDA(cudaStreamSynchronize(g->stream));
+    std::vector<int32_t> hubs;
+    for (int64_t x = 0; x < n; ++x)
+        if (deg[(size_t)x] > TOT_CHUNK) hubs.push_back((int32_t)x);
+    std::stable_sort(hubs.begin(), hubs.end(),
+                     [&](int32_t u, int32_t v) { return deg[(size_t)u] > deg[(size_t)v]; });
+    std::vector<int32_t> first(hubs.size() + 1, 0), chunk_hub;
+    for (size_t h = 0; h < hubs.size(); ++h) {
+        const int32_t nch = (deg[(size_t)hubs[h]] + TOT_CHUNK - 1) / TOT_CHUNK;
+        first[h + 1] = first[h] + nch;
+        for (int32_t c = 0; c < nch; ++c) chunk_hub.push_back((int32_t)h);
+    }
+    const int64_t nh = (int64_t)hubs.size(), nc = (int64_t)chunk_hub.size();
+    g->tot_nh = nh;
+    g->tot_nchunks = nc;
+    g->tot_hubs = dalloc_n<int32_t>(g, nh);
+    g->tot_first = dalloc_n<int32_t>(g, nh + 1);
+    g->tot_chunk_hub = dalloc_n<int32_t>(g, nc);
+    g->tot_cnt = dalloc_n<int32_t>(g, nh * g->K);
+    g->tot_done = dalloc_n<uint32_t>(g, nh);
+    LF_CUDA(cudaMemcpyAsync(g->tot_hubs, hubs.data(), (size_t)nh * 4, cudaMemcpyHostToDevice, g->stream));
+    LF_CUDA(cudaMemcpyAsync(g->tot_first, first.data(), (size_t)(nh + 1) * 4, cudaMemcpyHostToDevice, g->stream));
+    LF_CUDA(cudaMemcpyAsync(g->tot_chunk_hub, chunk_hub.data(), (size_t)nc * 4, cudaMemcpyHostToDevice, g->stream));
+    LF_CUDA(cudaMemsetAsync(g->tot_cnt, 0, (size_t)(nh * g->K) * 4, g->stream));
+    LF_CUDA(cudaMemsetAsync(g->tot_done, 0, (size_t)nh * 4, g->stream));
     LF_CUDA(cudaStreamSynchronize(g->stream));
 }
 
@@ -1816,6 +2251,7 @@ void build_hub_plan(lf_graph *g, int64_t q) {
 void free_run_state(lf_graph *g) {
     drop_graph(g);
     free_hub_plan(g);
+    free_total_plan(g);
     if (g->qtimes) dfree(g, g->qtimes);
     g->qtimes = nullptr;
     if (g->bar_flags) dfree(g, g->bar_flags);
@@ -1865,6 +2301,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         LF_CUDA(cudaMemsetAsync(&g->ds->bar_count, 0, sizeof(unsigned), st));
         LF_CUDA(cudaStreamSynchronize(st));
     }
+    build_total_plan(g);
     RunArgs a = make_args(g, device_readback(g));
     const unsigned long long launches0 = g->launches;
     const int64_t nb_all = n > 0 ? (n + q - 1) / q : 0;
@@ -1919,7 +2356,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         dfree(g, state);
     }
     g->ncomm = k0;
-    k_total<<<grid_for(n * 32, TOT_WARPS * 32, 1 << 16), TOT_WARPS * 32, 0, st>>>(a, n); ++g->launches;
+    launch_total(g, a);
     k_finalize<<<1, 32, 0, st>>>(g->ds, device_readback(g), 0); ++g->launches;
     LF_LAUNCHED();
     LF_CUDA(cudaMemcpyAsync(g->rb, device_readback(g), sizeof(Readback), cudaMemcpyDeviceToHost, st));
@@ -1961,6 +2398,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     for (int32_t it = 1; it <= max_iters; ++it) {
         if (maxcnt + 1 > g->K) grow_rows(g, maxcnt + 1);
         build_hub_plan(g, q);
+        build_total_plan(g);
         a = make_args(g, device_readback(g));
         a.nbatches = nb;
         const bool partial = max_batches >= 0 && batches + nb > max_batches;
