@@ -307,7 +307,6 @@ def main():
     tri_gbs = statistics.median(r[2]["merge_bytes"] / (r[2]["ms_triangles"] / 1e3) / 1e9 for r in res
                                 if r[2]["ms_triangles"] > 0) if m > 0 else 0.0
     launches = sum(r[2]["num_launches"] + r[1].num_launches for r in res)
-    qpct = list(prof[-1][1].prof_queue_us) if q <= 256 else None
     # the queue kernels' launch times come from profiled steps of the same
     # workload right after the timed region (profile mode records CUDA events
     # around every such launch and counts their algorithmic bytes; it is kept
@@ -317,6 +316,7 @@ def main():
     if any(math.isnan(r[1].prof_move_ms) for r in prof):
         prof = [one_step(q, True, use_graphs=False) for _ in range(max(1, min(args.steps, 2)))]
         roofline_src = "profiled steps with direct launches right after the timed region"
+    qpct = list(prof[-1][1].prof_queue_us) if q <= 256 else None
     ev_bytes = sum(r[1].prof_move_bytes for r in prof)
     ev_ms = sum(r[1].prof_move_ms for r in prof)
     ev_launches = sum(r[1].prof_move_launches for r in prof)
@@ -330,6 +330,8 @@ def main():
                 "frac": achieved / peak, "bytes_per_launch": ev_bytes / max(1, ev_launches),
                 "mean_launch_us": 1e3 * ev_ms / max(1, ev_launches), "launches": ev_launches,
                 "traffic": traffic["bytes_per_launch"] if traffic else None, "timed_in": roofline_src}
+    if qpct:
+        roofline["queue_us_p50_p90_p99_max"] = qpct
 
     secondary = None
     if spec["q2"] and not args.no_secondary:

@@ -149,7 +149,8 @@ struct lf_graph {
     int32_t *hub_pos = nullptr;
     int64_t *hub_qoff = nullptr;
     int64_t *hub_toff = nullptr;
-    uint32_t *hub_tcap = nullptr;
+    uint32_t *hub_tcap = nullptr;      // table size used this iteration (<= hub_wcap)
+    uint32_t *hub_wcap = nullptr;      // table size planned for the worst case, (d+1) K entries
     int32_t *hub_scratch = nullptr;
     int64_t hub_slots = 0;
     std::vector<int64_t> hub_qoff_host;
@@ -160,6 +161,17 @@ struct lf_graph {
     int32_t *hub_nch = nullptr;
     uint32_t *hub_done = nullptr;
     uint32_t *hub_ncand = nullptr;      // distinct ids in each hub's table, listed in its lower-bound area
+    // hubs with many candidates are screened and evaluated by several blocks:
+    // per hub the best lower bounds (order-preserving ints), its items and
+    // items finished; per item (hub, chunk) and its best actions
+    int32_t *hub_lbj = nullptr, *hub_lbl = nullptr;
+    uint32_t *hub_item_base = nullptr, *hub_nitems = nullptr, *hub_items_done = nullptr;
+    int32_t *hub_items = nullptr;       // 2 per item
+    double *hub_item_g = nullptr;       // 2 per item (join, leave)
+    int32_t *hub_item_ck = nullptr;     // 4 per item (join id, join k, leave id, leave k)
+    int64_t hub_items_cap = 0;
+    uint32_t *hub_qctr = nullptr;       // 3 per queue: items, next to screen, next to evaluate
+    std::vector<char> hub_qbig;         // per queue: may hold a hub with more than HUGE_BIG_NCAND candidates
     std::vector<int64_t> hub_cqoff_host;
     int64_t hub_plan_q = 0;
     int32_t hub_plan_K = 0;
@@ -173,6 +185,16 @@ struct lf_graph {
     uint32_t *tot_next = nullptr;       // work counters: node runs, chunks
     int64_t tot_nh = 0, tot_nchunks = 0;
     int32_t tot_plan_K = 0;
+    // large queues: per-queue counters (next node, overflow count), overflow
+    // list (queue positions) and their histogram bounds
+    uint32_t *dyn_ctr = nullptr;
+    int64_t dyn_ctr_cap = 0;
+    int32_t *dyn_list = nullptr;
+    long long *dyn_bound = nullptr;
+    int64_t dyn_list_cap = 0;
+    // second stream: hub chunks run beside the other evaluation kernels of a queue
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace lf {

@@ -51,6 +51,7 @@ struct RunArgs {
     const int64_t *hub_qoff;
     const int64_t *hub_toff;
     const uint32_t *hub_tcap;
+    uint32_t *hub_tcap_w;   // the same array, written by k_hub_caps
     int32_t *hkeys;
     uint32_t *hvals;
     float *hub_ub;
@@ -60,6 +61,12 @@ struct RunArgs {
     const int32_t *hub_nch;
     uint32_t *hub_done;
     uint32_t *hub_ncand;
+    int32_t *hub_lbj, *hub_lbl;
+    uint32_t *hub_item_base, *hub_nitems, *hub_items_done;
+    int32_t *hub_items;
+    double *hub_item_g;
+    int32_t *hub_item_ck;
+    uint32_t *hub_qctr;   // per queue: items, next item to screen, next item to evaluate
     unsigned long long *qtimes;   // profile mode: time stamp after each queue (persistent kernel)
     int32_t screen;    // 1: rule candidates out with the FP32 bound first
     float cc32;        // cc rounded to float (screen)
@@ -824,6 +831,22 @@ __device__ void eval_huge(const RunArgs &a, int64_t bstart, int64_t b, unsigned 
     }
 }
 
+// Count `add` for key in a shared table, giving up after `probes` slots (the
+// caller then counts it elsewhere).
+__device__ __forceinline__ bool st_insert_bounded(int32_t *keys, uint32_t *vals, uint32_t hm, int32_t key,
+                                                  uint32_t add, int probes) {
+    uint32_t h = hash32((uint32_t)key) & hm;
+    for (int probe = 0; probe < probes; ++probe) {
+        const int32_t prev = atomicCAS(&keys[h], EMPTY_KEY, key);
+        if (prev == EMPTY_KEY || prev == key) {
+            atomicAdd(&vals[h], add);
+            return true;
+        }
+        h = (h + 1) & hm;
+    }
+    return false;
+}
+
 // Insert into a hub's global table; a new id also gets its slot appended to
 // the hub's list of occupied slots.  False if the table is full.
 __device__ __forceinline__ bool hub_insert(int32_t *keys, uint32_t *vals, uint32_t hm, int32_t key, uint32_t add,
@@ -842,12 +865,228 @@ __device__ __forceinline__ bool hub_insert(int32_t *keys, uint32_t *vals, uint32
     return false;
 }
 
+// Table size of every hub for this iteration: twice a bound on its entries,
+// own row + one possible join + sum over neighbours of (row length + one
+// possible join), as a power of two; never above the planned worst case.
+// Dense tables keep the random accesses of the fill and the compaction in
+// fewer sectors than the worst-case size would.
+__global__ void __launch_bounds__(EV_THREADS) k_hub_caps(RunArgs a, const uint32_t *wcap, int64_t nhubs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t h = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < nhubs; h += warps) {
+        const int32_t x = a.order[a.hub_pos[h]];
+        const int64_t beg = a.off[x], end = a.off[x + 1];
+        unsigned long long e = 0;
+        for (int64_t p = beg + lane; p < end; p += 32) e += 1ull + (unsigned long long)__ldcg(&a.nmem[a.adj[p]]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(FULL, e, o);
+        if (lane == 0) {
+            e += 1ull + (unsigned long long)__ldcg(&a.nmem[x]);
+            unsigned long long cap = 32;
+            while (cap < 2ull * e) cap <<= 1;
+            a.hub_tcap_w[h] = (uint32_t)min(cap, (unsigned long long)wcap[h]);
+        }
+    }
+}
+
+// Hubs with more than HUGE_BIG_NCAND candidates: items of HUGE_CAND_CHUNK
+// candidates.  k_huge_screen moves an item's candidates out of the table
+// (ids and counts into dense arrays in the upper- and lower-bound areas, the
+// slots cleared), computes their FP32 upper bounds and raises the hub's best
+// lower bounds; k_huge_eval evaluates the survivors in FP64 and the block
+// finishing a hub's last item records the best actions.
+constexpr uint32_t HUGE_BIG_NCAND = 8192;
+constexpr uint32_t HUGE_CAND_CHUNK = 4096;
+
+__device__ __forceinline__ int32_t f2ord(float f) {
+    const int32_t b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int32_t k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
+struct HubItem {
+    int h, j;
+    int64_t t0;
+    uint32_t cap, lo, hi;
+};
+
+__device__ __forceinline__ HubItem hub_item(const RunArgs &a, uint32_t it) {
+    HubItem r;
+    r.h = a.hub_items[2 * it];
+    r.j = a.hub_items[2 * it + 1];
+    r.t0 = a.hub_toff[r.h];
+    r.cap = a.hub_tcap[r.h];
+    const uint32_t ncand = __ldcg(&a.hub_ncand[r.h]);
+    r.lo = (uint32_t)r.j * HUGE_CAND_CHUNK;
+    r.hi = min(ncand, r.lo + HUGE_CAND_CHUNK);
+    return r;
+}
+
+__global__ void __launch_bounds__(EV_THREADS) k_huge_screen(RunArgs a, int64_t bidx) {
+    __shared__ uint32_t s_it;
+    __shared__ float s_lbj[EV_WARPS], s_lbl[EV_WARPS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *qc = a.hub_qctr + 3 * bidx;
+    const uint32_t count = __ldcg(&qc[0]);
+    for (;;) {
+        if (threadIdx.x == 0) s_it = atomicAdd(&qc[1], 1u);
+        __syncthreads();
+        const uint32_t it = s_it;
+        __syncthreads();
+        if (it >= count) break;
+        const HubItem I = hub_item(a, it);
+        int32_t *keys = a.hkeys + I.t0;
+        uint32_t *vals = a.hvals + I.t0;
+        const int32_t *list = reinterpret_cast<const int32_t *>(a.hub_lb + I.t0);
+        int32_t *ck = reinterpret_cast<int32_t *>(a.hub_ub + I.t0);
+        float *cub = a.hub_ub + I.t0 + I.cap / 2;
+        uint32_t *cv = reinterpret_cast<uint32_t *>(a.hub_lb + I.t0) + I.cap / 2;
+        const int32_t x = a.order[a.hub_pos[I.h]];
+        const int32_t d = a.deg[x];
+        float lbj = -INFINITY, lbl = -INFINITY;
+        unsigned long long pb = 0;
+        constexpr int U = 4;   // candidates per thread and step, their loads issued together
+        for (uint32_t k0 = I.lo + threadIdx.x; k0 < I.hi; k0 += U * EV_THREADS) {
+            int32_t sl[U], C[U];
+            uint32_t v[U];
+            int4 r[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t k = k0 + u * EV_THREADS;
+                sl[u] = k < I.hi ? __ldcg(&list[k]) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                C[u] = sl[u] >= 0 ? __ldcg(&keys[sl[u]]) : EMPTY_KEY;
+                v[u] = sl[u] >= 0 ? __ldcg(&vals[sl[u]]) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                r[u] = (a.screen && sl[u] >= 0) ? __ldcg(reinterpret_cast<const int4 *>(&a.comm[C[u]]))
+                                                 : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (sl[u] < 0) continue;
+                const uint32_t k = k0 + u * EV_THREADS;
+                keys[sl[u]] = EMPTY_KEY;
+                vals[sl[u]] = 0u;
+                ck[k] = C[u];
+                cv[k] = v[u];
+                float ub = INFINITY;
+                if (a.screen) {
+                    float g, e;
+                    screen_gain_rec(a, r[u], v[u], d, g, e);
+                    ub = __fadd_rn(g, e);
+                    const float l = __fsub_rn(g, e);
+                    if (v[u] & OWN_FLAG) lbl = fmaxf(lbl, l); else lbj = fmaxf(lbj, l);
+                }
+                cub[k] = ub;
+                pb += 16ull;
+            }
+        }
+        lbj = warp_max_f(lbj);
+        lbl = warp_max_f(lbl);
+        if (lane == 0) {
+            s_lbj[w] = lbj;
+            s_lbl[w] = lbl;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 1; k < EV_WARPS; ++k) {
+                lbj = fmaxf(lbj, s_lbj[k]);
+                lbl = fmaxf(lbl, s_lbl[k]);
+            }
+            atomicMax(&a.hub_lbj[I.h], f2ord(lbj));
+            atomicMax(&a.hub_lbl[I.h], f2ord(lbl));
+        }
+        if (a.profile) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pb += __shfl_down_sync(FULL, pb, o);
+            if (lane == 0 && pb) atomicAdd(&a.ds->prof_bytes, pb);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(EV_THREADS) k_huge_eval(RunArgs a, int64_t bstart, int64_t bidx) {
+    __shared__ uint32_t s_it;
+    __shared__ unsigned s_last;
+    __shared__ BlockScratch bs;
+    __shared__ int32_t bkey[EV_WARPS][32];
+    __shared__ uint32_t bval[EV_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *qc = a.hub_qctr + 3 * bidx;
+    const uint32_t count = __ldcg(&qc[0]);
+    for (;;) {
+        if (threadIdx.x == 0) s_it = atomicAdd(&qc[2], 1u);
+        __syncthreads();
+        const uint32_t it = s_it;
+        __syncthreads();
+        if (it >= count) break;
+        const HubItem I = hub_item(a, it);
+        const int32_t *ck = reinterpret_cast<const int32_t *>(a.hub_ub + I.t0);
+        const float *cub = a.hub_ub + I.t0 + I.cap / 2;
+        const uint32_t *cv = reinterpret_cast<const uint32_t *>(a.hub_lb + I.t0) + I.cap / 2;
+        const int64_t p = a.hub_pos[I.h];
+        const int32_t x = a.order[p];
+        const int32_t d = a.deg[x];
+        const float lbj = ord2f(__ldcg(&a.hub_lbj[I.h])), lbl = ord2f(__ldcg(&a.hub_lbl[I.h]));
+        const uint32_t n = I.hi - I.lo, slice = (n + EV_WARPS - 1) / EV_WARPS;
+        const uint32_t lo = min(I.hi, I.lo + (uint32_t)w * slice), hi = min(I.hi, lo + slice);
+        Best bj{0.0, -1, 0}, bl{0.0, -1, 0};
+        eval_survivors(a, ck, cv, cub, lo, hi, d, lbj, lbl, true, true, bkey[w], bval[w], bj, bl);
+        warp_best(bj);
+        warp_best(bl);
+        if (lane == 0) {
+            bs.gj[w] = bj.g; bs.cj[w] = bj.c; bs.kj[w] = bj.k;
+            bs.gl[w] = bl.g; bs.cl[w] = bl.c; bs.kl[w] = bl.k;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Best fj{0.0, -1, 0}, fl{0.0, -1, 0};
+            for (int ww = 0; ww < EV_WARPS; ++ww) {
+                if (better(bs.gj[ww], bs.cj[ww], fj.g, fj.c)) fj = Best{bs.gj[ww], bs.cj[ww], bs.kj[ww]};
+                if (better(bs.gl[ww], bs.cl[ww], fl.g, fl.c)) fl = Best{bs.gl[ww], bs.cl[ww], bs.kl[ww]};
+            }
+            a.hub_item_g[2 * it] = fj.g;
+            a.hub_item_g[2 * it + 1] = fl.g;
+            a.hub_item_ck[4 * it] = fj.c;
+            a.hub_item_ck[4 * it + 1] = fj.k;
+            a.hub_item_ck[4 * it + 2] = fl.c;
+            a.hub_item_ck[4 * it + 3] = fl.k;
+            __threadfence();
+            s_last = atomicAdd(&a.hub_items_done[I.h], 1u) == a.hub_nitems[I.h] - 1;
+        }
+        __syncthreads();
+        if (s_last && threadIdx.x == 0) {   // every item of the hub is in: its best actions
+            __threadfence();
+            const uint32_t base = a.hub_item_base[I.h], ni = a.hub_nitems[I.h];
+            Best fj{0.0, -1, 0}, fl{0.0, -1, 0};
+            for (uint32_t k = base; k < base + ni; ++k) {
+                const double gj = __ldcg(&a.hub_item_g[2 * k]), gl = __ldcg(&a.hub_item_g[2 * k + 1]);
+                const int32_t cj = __ldcg(&a.hub_item_ck[4 * k]), kj = __ldcg(&a.hub_item_ck[4 * k + 1]);
+                const int32_t cl = __ldcg(&a.hub_item_ck[4 * k + 2]), kl = __ldcg(&a.hub_item_ck[4 * k + 3]);
+                if (better(gj, cj, fj.g, fj.c)) fj = Best{gj, cj, kj};
+                if (better(gl, cl, fl.g, fl.c)) fl = Best{gl, cl, kl};
+            }
+            write_action(a, (int)(p - bstart), fj, fl, queue_serial(a, bidx));
+            if (a.profile) atomicAdd(&a.ds->prof_bytes, 44ull + 4ull * (unsigned long long)__ldcg(&a.nmem[x]));
+            a.hub_items_done[I.h] = 0u;
+            a.hub_ncand[I.h] = 0u;
+            a.hub_lbj[I.h] = f2ord(-INFINITY);
+            a.hub_lbl[I.h] = f2ord(-INFINITY);
+        }
+        __syncthreads();
+    }
+}
+
 // Per-queue launches: one block per chunk of HUGE_CHUNK neighbours of a hub.
 // Each block adds its neighbours' memberships to the hub's table in global
 // memory (the first chunk also the hub's own row); the block that finishes
 // the hub's last chunk screens and evaluates the candidates, records the
 // actions and clears the table.
-constexpr int HUGE_CHUNK = 2048;
+constexpr int HUGE_CHUNK = 1024;
+constexpr int HUGE_ROUNDS = HUGE_CHUNK / EV_THREADS;   // neighbours per thread
+constexpr uint32_t HUGE_SH = 8192;   // shared-memory table of a chunk block (keys and counts: 64 KiB)
 
 __device__ void huge_decide(const RunArgs &a, int i, int32_t d, int32_t cx, const int32_t *keys, const uint32_t *vals,
                             float *ubs, float *lbs, uint32_t H, int32_t *bkey, uint32_t *bval, BlockScratch &bs,
@@ -899,6 +1138,7 @@ __device__ void huge_decide(const RunArgs &a, int i, int32_t d, int32_t cx, cons
 }
 
 __global__ void __launch_bounds__(EV_THREADS) k_huge_chunks(RunArgs a, int64_t bstart, int64_t bidx, int64_t cbase) {
+    extern __shared__ int32_t hs_dyn[];   // HUGE_SH keys, HUGE_SH counts
     __shared__ BlockScratch bs;
     __shared__ int32_t bkey[EV_WARPS][32];
     __shared__ uint32_t bval[EV_WARPS][32];
@@ -923,15 +1163,43 @@ __global__ void __launch_bounds__(EV_THREADS) k_huge_chunks(RunArgs a, int64_t b
         for (int j = threadIdx.x; j < cx; j += EV_THREADS)
             if (!hub_insert(keys, vals, hm, __ldcg(&rowx[j]), 0u, true, list, &a.hub_ncand[h])) bad = true;
     }
+    // the chunk's memberships are first counted in a shared table, then each
+    // distinct id goes to the hub's table once (entries the shared table
+    // cannot take go there directly)
+    // the shared table is sized for this chunk's entries (twice, pow2, at most HUGE_SH)
+    __shared__ unsigned s_ent[EV_WARPS];
+    int32_t ys[HUGE_ROUNDS], cys[HUGE_ROUNDS];
+    unsigned ent = 0;
+#pragma unroll
+    for (int r = 0; r < HUGE_ROUNDS; ++r) {
+        const int64_t q = beg + r * EV_THREADS + w * 32 + lane;
+        ys[r] = q < end ? a.adj[q] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < HUGE_ROUNDS; ++r) {
+        const int64_t q = beg + r * EV_THREADS + w * 32 + lane;
+        cys[r] = q < end ? __ldcg(&a.nmem[ys[r]]) : 0;
+        ent += (unsigned)cys[r];
+    }
+    ent = __reduce_add_sync(FULL, ent);
+    if (lane == 0) s_ent[w] = ent;
+    __syncthreads();
+    ent = 0;
+    for (int k = 0; k < EV_WARPS; ++k) ent += s_ent[k];
+    uint32_t SH = 256;
+    while (SH < 2u * ent && SH < HUGE_SH) SH <<= 1;
+    int32_t *skeys = hs_dyn;
+    uint32_t *svals = reinterpret_cast<uint32_t *>(hs_dyn + HUGE_SH);
+    for (uint32_t sl = threadIdx.x; sl < SH; sl += EV_THREADS) {
+        skeys[sl] = EMPTY_KEY;
+        svals[sl] = 0u;
+    }
+    __syncthreads();
     unsigned long long pb = 0;
-    for (int64_t p0 = beg + w * 32; p0 < end; p0 += EV_THREADS) {
-        const int64_t q = p0 + lane;
-        int32_t y = 0, cy = 0;
-        if (q < end) {
-            y = a.adj[q];
-            cy = __ldcg(&a.nmem[y]);
-            pb += 8ull + 4ull * (unsigned long long)cy;
-        }
+#pragma unroll
+    for (int r = 0; r < HUGE_ROUNDS; ++r) {
+        const int32_t y = ys[r], cy = cys[r];
+        if (beg + r * EV_THREADS + w * 32 + lane < end) pb += 8ull + 4ull * (unsigned long long)cy;
         const int32_t cmax = __reduce_max_sync(FULL, cy);
         const int32_t *rowy = a.mem + (int64_t)y * a.K;
         int4 r0, r1;
@@ -940,7 +1208,19 @@ __global__ void __launch_bounds__(EV_THREADS) k_huge_chunks(RunArgs a, int64_t b
             const int32_t C = s < cy ? row_entry(r0, r1, rowy, s) : -2 - lane;
             const unsigned mask = __match_any_sync(FULL, C);
             if (C >= 0 && lane == __ffs(mask) - 1)
-                if (!hub_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false, list, &a.hub_ncand[h])) bad = true;
+                if (!st_insert_bounded(skeys, svals, SH - 1, C, (uint32_t)__popc(mask), 32))
+                    if (!hub_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false, list, &a.hub_ncand[h]))
+                        bad = true;
+        }
+    }
+    __syncthreads();
+    for (uint32_t s0 = threadIdx.x; s0 < SH; s0 += 4 * EV_THREADS) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t sl = s0 + u * EV_THREADS;
+            const int32_t C = sl < SH ? skeys[sl] : EMPTY_KEY;
+            if (C != EMPTY_KEY)
+                if (!hub_insert(keys, vals, hm, C, svals[sl], false, list, &a.hub_ncand[h])) bad = true;
         }
     }
     if (bad) atomicOr(&a.ds->err, DERR_CHECK);   // the planned table bounds every entry: cannot happen
@@ -955,9 +1235,23 @@ __global__ void __launch_bounds__(EV_THREADS) k_huge_chunks(RunArgs a, int64_t b
     __syncthreads();
     if (!s_last) return;
     __threadfence();   // every chunk's insertions are visible from here on
+    const uint32_t ncand = __ldcg(&a.hub_ncand[h]);
+    if (ncand > HUGE_BIG_NCAND) {   // screened and evaluated by k_huge_screen / k_huge_eval
+        if (threadIdx.x == 0) {
+            const uint32_t ni = (ncand + HUGE_CAND_CHUNK - 1) / HUGE_CAND_CHUNK;
+            const uint32_t base = atomicAdd(&a.hub_qctr[3 * bidx], ni);
+            a.hub_item_base[h] = base;
+            a.hub_nitems[h] = ni;
+            a.hub_done[h] = 0u;
+            for (uint32_t j = 0; j < ni; ++j) {
+                a.hub_items[2 * (base + j)] = h;
+                a.hub_items[2 * (base + j) + 1] = (int32_t)j;
+            }
+        }
+        return;
+    }
     // dense candidates: ids into the upper-bound area, counts over the slot
     // list; the table is cleared as it is read and then holds the bounds
-    const uint32_t ncand = __ldcg(&a.hub_ncand[h]);
     int32_t *ck = reinterpret_cast<int32_t *>(a.hub_ub + t0);
     uint32_t *cv = reinterpret_cast<uint32_t *>(list);
     for (uint32_t k = threadIdx.x; k < ncand; k += EV_THREADS) {
@@ -1087,6 +1381,124 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval_huge(RunArgs a, int64_t bst
     __shared__ uint32_t bval[EV_WARPS][32];
     const int w = threadIdx.x >> 5;
     eval_huge(a, bstart, bidx, queue_serial(a, bidx), bkey[w], bval[w], bs);
+}
+
+// Large queues: a resident grid whose warps take the queue's nodes one at a
+// time from a counter, so that no warp waits at a block-wide barrier for the
+// others' nodes.  Nodes whose histogram does not fit a warp's table are
+// listed (position and entry count) for k_eval_blocks; hubs are left to
+// k_huge_chunks.
+__global__ void __launch_bounds__(EV_THREADS) k_eval_dyn(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx,
+                                                         uint32_t *ctr, int32_t *list, long long *lbound) {
+    extern __shared__ int32_t ev_dyn[];   // per warp: HW keys, HW counts, HW upper and HW lower bounds
+    __shared__ TeamScratch ts;
+    __shared__ int32_t bkey[EV_WARPS][32];
+    __shared__ uint32_t bval[EV_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t *keys = ev_dyn + w * HW;
+    uint32_t *vals = reinterpret_cast<uint32_t *>(ev_dyn + HB) + w * HW;
+    float *ubs = reinterpret_cast<float *>(ev_dyn + 2 * HB) + w * HW;
+    const unsigned long long serial = queue_serial(a, bidx);
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = (int)atomicAdd(&ctr[0], 1u);
+        i = __shfl_sync(FULL, i, 0);
+        if (i >= blen) break;
+        const int32_t x = a.order[bstart + i];
+        const int32_t d = a.deg[x];
+        if (d > a.huge_deg) continue;   // evaluated by k_huge_chunks
+        const int64_t beg = a.off[x], end = a.off[x + 1];
+        int32_t y0 = 0, c0 = 0;
+        long long entries = 0;
+        for (int64_t p0 = beg; p0 < end; p0 += 32) {
+            const int64_t p = p0 + lane;
+            int32_t y = 0, cy = 0;
+            if (p < end) {
+                y = a.adj[p];
+                cy = __ldcg(&a.nmem[y]);
+            }
+            if (p0 == beg) {
+                y0 = y;
+                c0 = cy;
+            }
+            entries += cy;
+        }
+        entries = __reduce_add_sync(FULL, (unsigned)entries);
+        entries += __ldcg(&a.nmem[x]);
+        if (d <= a.warp_max_deg && entries <= HW / 2) {
+            eval_team<1>(a, i, x, d, beg, end, entries, y0, c0, keys, vals, ubs, bkey[w], bval[w], ts, w, 0, serial);
+        } else if (lane == 0) {
+            const uint32_t k = atomicAdd(&ctr[1], 1u);
+            list[k] = i;
+            lbound[k] = entries;
+        }
+    }
+}
+
+// Teams of T warps take listed nodes (queue position and entry count) from a
+// counter; a node whose entries exceed the team's table goes on to the next
+// list.  in_ctr: [count, next]; out_ctr: [count].
+template <int T>
+__global__ void __launch_bounds__(EV_THREADS) k_eval_tdyn(RunArgs a, int64_t bstart, int64_t bidx, uint32_t *in_ctr,
+                                                          const int32_t *in_list, const long long *in_bound,
+                                                          uint32_t *out_ctr, int32_t *out_list,
+                                                          long long *out_bound) {
+    extern __shared__ int32_t ev_dyn[];
+    __shared__ TeamScratch ts;
+    __shared__ int32_t bkey[EV_WARPS][32];
+    __shared__ uint32_t bval[EV_WARPS][32];
+    __shared__ uint32_t s_k[EV_WARPS / T];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tm = w / T, w_in = w % T;
+    int32_t *keys = ev_dyn + tm * T * HW;
+    uint32_t *vals = reinterpret_cast<uint32_t *>(ev_dyn + HB) + tm * T * HW;
+    float *ubs = reinterpret_cast<float *>(ev_dyn + 2 * HB) + tm * T * HW;
+    const uint32_t count = __ldcg(&in_ctr[0]);
+    const unsigned long long serial = queue_serial(a, bidx);
+    for (;;) {
+        if (w_in == 0 && lane == 0) s_k[tm] = atomicAdd(&in_ctr[1], 1u);
+        team_sync<T>(tm);
+        const uint32_t k = s_k[tm];
+        team_sync<T>(tm);   // the slot is rewritten only after every warp of the team has read it
+        if (k >= count) break;
+        const int i = in_list[k];
+        const long long entries = in_bound[k];
+        const int32_t x = a.order[bstart + i];
+        const int32_t d = a.deg[x];
+        if (entries > (long long)T * HW / 2) {
+            if (w_in == 0 && lane == 0) {
+                const uint32_t o = atomicAdd(&out_ctr[0], 1u);
+                out_list[o] = i;
+                out_bound[o] = entries;
+            }
+            continue;
+        }
+        const int64_t beg = a.off[x], end = a.off[x + 1];
+        const int64_t p = beg + w_in * 32 + lane;
+        const int32_t y0 = p < end ? a.adj[p] : 0;
+        const int32_t c0 = p < end ? __ldcg(&a.nmem[y0]) : 0;
+        eval_team<T>(a, i, x, d, beg, end, entries, y0, c0, keys, vals, ubs, bkey[w], bval[w], ts, tm, w_in, serial);
+    }
+}
+
+// The nodes k_eval_dyn listed, one block each (shared-memory table, several
+// passes over hash parts when it does not fit).
+__global__ void __launch_bounds__(EV_THREADS) k_eval_blocks(RunArgs a, int64_t bstart, int64_t bidx,
+                                                            const uint32_t *cnt, const int32_t *list,
+                                                            const long long *lbound) {
+    extern __shared__ int32_t ev_dyn[];
+    __shared__ BlockScratch bs;
+    __shared__ int32_t bkey[EV_WARPS][32];
+    __shared__ uint32_t bval[EV_WARPS][32];
+    const int w = threadIdx.x >> 5;
+    const uint32_t count = __ldcg(cnt);
+    const unsigned long long serial = queue_serial(a, bidx);
+    for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
+        const int i = list[k];
+        const int32_t x = a.order[bstart + i];
+        eval_block(a, i, x, (int64_t)lbound[k], ev_dyn, reinterpret_cast<uint32_t *>(ev_dyn + HB),
+                   reinterpret_cast<float *>(ev_dyn + 2 * HB), bkey[w], bval[w], bs, serial);
+    }
 }
 
 template <int T>
@@ -1892,6 +2304,7 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.hub_qoff = g->hub_qoff;
     a.hub_toff = g->hub_toff;
     a.hub_tcap = g->hub_tcap;
+    a.hub_tcap_w = g->hub_tcap;
     a.hkeys = g->hub_scratch;
     a.hvals = reinterpret_cast<uint32_t *>(g->hub_scratch + g->hub_slots);
     a.hub_ub = reinterpret_cast<float *>(g->hub_scratch + 2 * g->hub_slots);
@@ -1901,6 +2314,15 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.hub_nch = g->hub_nch;
     a.hub_done = g->hub_done;
     a.hub_ncand = g->hub_ncand;
+    a.hub_lbj = g->hub_lbj;
+    a.hub_lbl = g->hub_lbl;
+    a.hub_item_base = g->hub_item_base;
+    a.hub_nitems = g->hub_nitems;
+    a.hub_items_done = g->hub_items_done;
+    a.hub_items = g->hub_items;
+    a.hub_item_g = g->hub_item_g;
+    a.hub_item_ck = g->hub_item_ck;
+    a.hub_qctr = g->hub_qctr;
     // FP32 screen: cc must be a normal float with room to spare; delta bounds
     // 15 FP32 roundings (20 ulp) and the FP32 subtraction, the FP64 estimator's error u (m2 + 3 vol +
     // 17) with m2, vol <= 2m, the two gain subtractions, and a 2% margin.
@@ -1959,11 +2381,73 @@ void set_eval_attrs() {
     LF_CUDA(cudaFuncSetAttribute(k_eval<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
     LF_CUDA(cudaFuncSetAttribute(k_eval<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
     LF_CUDA(cudaFuncSetAttribute(k_eval<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_eval_dyn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_eval_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_eval_tdyn<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_huge_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(HUGE_SH * 8)));
+}
+
+void drop_graph(lf_graph *g) {
+    if (g->iter_exec) {
+        cudaGraphExecDestroy(g->iter_exec);
+        g->iter_exec = nullptr;
+    }
+}
+
+// Queues at least this large are evaluated by k_eval_dyn (one warp per node,
+// nodes handed out by a counter) and k_eval_blocks.
+constexpr int64_t DYN_MIN_Q = 4096;
+
+bool use_dyn(lf_graph *g, int64_t q) { return q >= DYN_MIN_Q && choose_team(g, q) == 1; }
+
+void ensure_side(lf_graph *g) {
+    if (g->side) return;
+    LF_CUDA(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+    LF_CUDA(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+    LF_CUDA(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+}
+
+// Four counters per queue: next node, list-1 count, list-1 next, list-2
+// count; two lists of up to q entries (positions, then entry counts).
+void ensure_dyn(lf_graph *g, int64_t q, int64_t nb) {
+    if (g->dyn_ctr_cap < 4 * nb) {
+        if (g->dyn_ctr) dfree(g, g->dyn_ctr);
+        g->dyn_ctr = dalloc_n<uint32_t>(g, 4 * nb);
+        g->dyn_ctr_cap = 4 * nb;
+        drop_graph(g);
+    }
+    if (g->dyn_list_cap < q) {
+        if (g->dyn_list) dfree(g, g->dyn_list);
+        if (g->dyn_bound) dfree(g, g->dyn_bound);
+        g->dyn_list = dalloc_n<int32_t>(g, 2 * q);
+        g->dyn_bound = dalloc_n<long long>(g, 2 * q);
+        g->dyn_list_cap = q;
+        drop_graph(g);
+    }
 }
 
 void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int64_t count,
                     bool capturing = false) {
     const int T = choose_team(g, q);
+    const bool dyn = use_dyn(g, q);
+    const int64_t nhubs = g->hub_qoff_host.empty() ? 0 : g->hub_qoff_host.back();
+    if (nhubs > 0 && first == 0) {
+        k_hub_caps<<<grid_for(nhubs * 32, EV_THREADS, 4096), EV_THREADS, 0, g->stream>>>(a, g->hub_wcap, nhubs);
+        ++g->launches;
+    }
+    int dyn_grid = 0, blk_grid = 0;
+    if (dyn) {
+        static int per_sm = 0, per_sm_blk = 0;
+        if (per_sm == 0) {
+            LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_dyn, EV_THREADS, EV_DYN_SMEM));
+            LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blk, k_eval_blocks, EV_THREADS,
+                                                                  EV_DYN_SMEM));
+        }
+        dyn_grid = num_sms() * std::max(1, per_sm);
+        blk_grid = num_sms() * std::max(1, per_sm_blk);
+        LF_CUDA(cudaMemsetAsync(g->dyn_ctr + 4 * first, 0, (size_t)(4 * count) * sizeof(uint32_t), g->stream));
+        ensure_side(g);
+    }
 
     const bool prof = g->profile && (int64_t)g->prof_ev.size() >= 2 * (first + count);
     for (int64_t b = first; b < first + count; ++b) {
@@ -1972,17 +2456,47 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
         if (prof) record_event(g, g->prof_ev[2 * b], capturing);
         const int64_t nch =
             g->hub_cqoff_host.empty() ? 0 : g->hub_cqoff_host[(size_t)b + 1] - g->hub_cqoff_host[(size_t)b];
+        const bool fork = dyn && nch > 0;   // hub chunks on the second stream, beside the warps
+        if (fork) {
+            LF_CUDA(cudaEventRecord(g->ev_fork, g->stream));
+            LF_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
+        }
         if (nch > 0) {
-            k_huge_chunks<<<(unsigned)nch, EV_THREADS, 0, g->stream>>>(a, bstart, b, g->hub_cqoff_host[(size_t)b]);
+            cudaStream_t hs = fork ? g->side : g->stream;
+            const bool big = !g->hub_qbig.empty() && g->hub_qbig[(size_t)b];
+            if (big) LF_CUDA(cudaMemsetAsync(g->hub_qctr + 3 * b, 0, 3 * sizeof(uint32_t), hs));
+            k_huge_chunks<<<(unsigned)nch, EV_THREADS, (size_t)HUGE_SH * 8, hs>>>(a, bstart, b,
+                                                                                g->hub_cqoff_host[(size_t)b]);
+            ++g->launches;
+            if (big) {
+                k_huge_screen<<<(unsigned)(6 * num_sms()), EV_THREADS, 0, hs>>>(a, b);
+                k_huge_eval<<<(unsigned)(3 * num_sms()), EV_THREADS, 0, hs>>>(a, bstart, b);
+                g->launches += 2;
+            }
+        }
+        if (fork) LF_CUDA(cudaEventRecord(g->ev_join, g->side));
+        if (dyn) {
+            uint32_t *ctr = g->dyn_ctr + 4 * b;
+            const int64_t L = g->dyn_list_cap;
+            const unsigned grid = (unsigned)std::min<int64_t>(dyn_grid, (blen + EV_WARPS - 1) / EV_WARPS);
+            k_eval_dyn<<<grid, EV_THREADS, EV_DYN_SMEM, g->stream>>>(a, bstart, blen, b, ctr, g->dyn_list,
+                                                                      g->dyn_bound);
+            k_eval_tdyn<4><<<(unsigned)blk_grid, EV_THREADS, EV_DYN_SMEM, g->stream>>>(
+                a, bstart, b, ctr + 1, g->dyn_list, g->dyn_bound, ctr + 3, g->dyn_list + L, g->dyn_bound + L);
+            k_eval_blocks<<<(unsigned)blk_grid, EV_THREADS, EV_DYN_SMEM, g->stream>>>(a, bstart, b, ctr + 3,
+                                                                                     g->dyn_list + L,
+                                                                                     g->dyn_bound + L);
+            g->launches += 3;
+            if (fork) LF_CUDA(cudaStreamWaitEvent(g->stream, g->ev_join, 0));
+        } else {
+            switch (T) {
+            case 1: launch_eval<1>(g, a, bstart, blen, b); break;
+            case 2: launch_eval<2>(g, a, bstart, blen, b); break;
+            case 4: launch_eval<4>(g, a, bstart, blen, b); break;
+            default: launch_eval<8>(g, a, bstart, blen, b); break;
+            }
             ++g->launches;
         }
-        switch (T) {
-        case 1: launch_eval<1>(g, a, bstart, blen, b); break;
-        case 2: launch_eval<2>(g, a, bstart, blen, b); break;
-        case 4: launch_eval<4>(g, a, bstart, blen, b); break;
-        default: launch_eval<8>(g, a, bstart, blen, b); break;
-        }
-        ++g->launches;
         if (prof) record_event(g, g->prof_ev[2 * b + 1], capturing);
         k_apply<<<grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30), AP_THREADS, 0, g->stream>>>(a, bstart, blen, b); ++g->launches;
     }
@@ -2005,13 +2519,6 @@ void launch_iteration_end(lf_graph *g, const RunArgs &a) {
     k_finalize<<<1, 32, 0, g->stream>>>(g->ds, device_readback(g), 1); ++g->launches;
     LF_LAUNCHED();
     LF_CUDA(cudaMemcpyAsync(g->rb, device_readback(g), sizeof(Readback), cudaMemcpyDeviceToHost, g->stream));
-}
-
-void drop_graph(lf_graph *g) {
-    if (g->iter_exec) {
-        cudaGraphExecDestroy(g->iter_exec);
-        g->iter_exec = nullptr;
-    }
 }
 
 void ensure_capacity(lf_graph *g, int64_t q) {
@@ -2099,6 +2606,8 @@ void free_hub_plan(lf_graph *g) {
     if (g->hub_qoff) dfree(g, g->hub_qoff);
     if (g->hub_toff) dfree(g, g->hub_toff);
     if (g->hub_tcap) dfree(g, g->hub_tcap);
+    if (g->hub_wcap) dfree(g, g->hub_wcap);
+    g->hub_wcap = nullptr;
     if (g->hub_scratch) dfree(g, g->hub_scratch);
     if (g->hub_chunk_h) dfree(g, g->hub_chunk_h);
     if (g->hub_chunk_c) dfree(g, g->hub_chunk_c);
@@ -2107,6 +2616,20 @@ void free_hub_plan(lf_graph *g) {
     if (g->hub_ncand) dfree(g, g->hub_ncand);
     g->hub_chunk_h = g->hub_chunk_c = g->hub_nch = nullptr;
     g->hub_done = g->hub_ncand = nullptr;
+    for (int32_t **pp : {&g->hub_lbj, &g->hub_lbl, &g->hub_items, &g->hub_item_ck})
+        if (*pp) {
+            dfree(g, *pp);
+            *pp = nullptr;
+        }
+    for (uint32_t **pp : {&g->hub_item_base, &g->hub_nitems, &g->hub_items_done, &g->hub_qctr})
+        if (*pp) {
+            dfree(g, *pp);
+            *pp = nullptr;
+        }
+    if (g->hub_item_g) dfree(g, g->hub_item_g);
+    g->hub_item_g = nullptr;
+    g->hub_items_cap = 0;
+    g->hub_qbig.clear();
     g->hub_cqoff_host.clear();
     g->hub_pos = nullptr;
     g->hub_qoff = nullptr;
@@ -2138,11 +2661,12 @@ void build_hub_plan(lf_graph *g, int64_t q) {
     std::vector<int32_t> pos, nch, chunk_h, chunk_c;
     std::vector<int64_t> qoff((size_t)nb + 1, 0), cqoff((size_t)nb + 1, 0), toff;
     std::vector<uint32_t> tcap;
-    int64_t slots = 0;
+    std::vector<char> qbig((size_t)nb, 0);
+    int64_t slots = 0, items_cap = 0;
     for (int64_t b = 0; b < nb; ++b) {
         qoff[(size_t)b] = (int64_t)pos.size();
         cqoff[(size_t)b] = (int64_t)chunk_h.size();
-        int64_t used = 0;
+        int64_t used = 0, items = 0;
         for (int64_t p = b * q; p < std::min(n, (b + 1) * q); ++p) {
             const int32_t d = deg[(size_t)order[(size_t)p]];
             if (d <= HUGE_DEG) continue;
@@ -2158,9 +2682,15 @@ void build_hub_plan(lf_graph *g, int64_t q) {
             toff.push_back(used);
             tcap.push_back((uint32_t)cap);
             used += (int64_t)cap;
+            if (cap / 2 > HUGE_BIG_NCAND) {   // candidates <= cap / 2
+                qbig[(size_t)b] = 1;
+                items += (int64_t)((cap / 2 + HUGE_CAND_CHUNK - 1) / HUGE_CAND_CHUNK);
+            }
         }
         slots = std::max(slots, used);
+        items_cap = std::max(items_cap, items);
     }
+    g->hub_qbig = qbig;
     qoff[(size_t)nb] = (int64_t)pos.size();
     cqoff[(size_t)nb] = (int64_t)chunk_h.size();
     g->hub_qoff_host = qoff;
@@ -2184,6 +2714,25 @@ void build_hub_plan(lf_graph *g, int64_t q) {
     LF_CUDA(cudaMemcpyAsync(g->hub_nch, nch.data(), (size_t)H * 4, cudaMemcpyHostToDevice, g->stream));
     LF_CUDA(cudaMemsetAsync(g->hub_done, 0, (size_t)H * 4, g->stream));
     LF_CUDA(cudaMemsetAsync(g->hub_ncand, 0, (size_t)H * 4, g->stream));
+    g->hub_lbj = dalloc_n<int32_t>(g, H);
+    g->hub_lbl = dalloc_n<int32_t>(g, H);
+    g->hub_item_base = dalloc_n<uint32_t>(g, H);
+    g->hub_nitems = dalloc_n<uint32_t>(g, H);
+    g->hub_items_done = dalloc_n<uint32_t>(g, H);
+    {
+        const int32_t neg_inf_ord = (int32_t)(0xff800000u ^ 0x7fffffffu);   // -inf, order-preserving
+        std::vector<int32_t> ninf((size_t)H, neg_inf_ord);
+        LF_CUDA(cudaMemcpyAsync(g->hub_lbj, ninf.data(), (size_t)H * 4, cudaMemcpyHostToDevice, g->stream));
+        LF_CUDA(cudaMemcpyAsync(g->hub_lbl, ninf.data(), (size_t)H * 4, cudaMemcpyHostToDevice, g->stream));
+        LF_CUDA(cudaStreamSynchronize(g->stream));
+    }
+    LF_CUDA(cudaMemsetAsync(g->hub_items_done, 0, (size_t)H * 4, g->stream));
+    g->hub_qctr = dalloc_n<uint32_t>(g, 3 * nb);
+    LF_CUDA(cudaMemsetAsync(g->hub_qctr, 0, (size_t)(3 * nb) * 4, g->stream));
+    g->hub_items_cap = std::max<int64_t>(1, items_cap);
+    g->hub_items = dalloc_n<int32_t>(g, 2 * g->hub_items_cap);
+    g->hub_item_g = dalloc_n<double>(g, 2 * g->hub_items_cap);
+    g->hub_item_ck = dalloc_n<int32_t>(g, 4 * g->hub_items_cap);
     // tables start clean (keys empty, counts zero) and are left clean after each use
     LF_CUDA(cudaMemsetAsync(g->hub_scratch, 0xff, (size_t)slots * 4, g->stream));
     LF_CUDA(cudaMemsetAsync(g->hub_scratch + slots, 0, (size_t)slots * 4, g->stream));
@@ -2191,6 +2740,8 @@ void build_hub_plan(lf_graph *g, int64_t q) {
     LF_CUDA(cudaMemcpyAsync(g->hub_qoff, qoff.data(), (size_t)(nb + 1) * 8, cudaMemcpyHostToDevice, g->stream));
     LF_CUDA(cudaMemcpyAsync(g->hub_toff, toff.data(), (size_t)H * 8, cudaMemcpyHostToDevice, g->stream));
     LF_CUDA(cudaMemcpyAsync(g->hub_tcap, tcap.data(), (size_t)H * 4, cudaMemcpyHostToDevice, g->stream));
+    g->hub_wcap = dalloc_n<uint32_t>(g, H);
+    LF_CUDA(cudaMemcpyAsync(g->hub_wcap, tcap.data(), (size_t)H * 4, cudaMemcpyHostToDevice, g->stream));
     LF_CUDA(cudaStreamSynchronize(g->stream));
 }
 
@@ -2252,6 +2803,21 @@ void free_run_state(lf_graph *g) {
     drop_graph(g);
     free_hub_plan(g);
     free_total_plan(g);
+    if (g->side) {
+        cudaStreamSynchronize(g->side);
+        cudaStreamDestroy(g->side);
+        cudaEventDestroy(g->ev_fork);
+        cudaEventDestroy(g->ev_join);
+        g->side = nullptr;
+        g->ev_fork = g->ev_join = nullptr;
+    }
+    if (g->dyn_ctr) dfree(g, g->dyn_ctr);
+    if (g->dyn_list) dfree(g, g->dyn_list);
+    if (g->dyn_bound) dfree(g, g->dyn_bound);
+    g->dyn_ctr = nullptr;
+    g->dyn_list = nullptr;
+    g->dyn_bound = nullptr;
+    g->dyn_ctr_cap = g->dyn_list_cap = 0;
     if (g->qtimes) dfree(g, g->qtimes);
     g->qtimes = nullptr;
     if (g->bar_flags) dfree(g, g->bar_flags);
@@ -2367,6 +2933,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     g->ran = true;
 
     const int64_t nb = n > 0 ? (n + q - 1) / q : 0;
+    if (use_dyn(g, q)) ensure_dyn(g, q, nb);
     // measured on GB300: the persistent loop wins for small queues (grid
     // barriers over few blocks), launches per queue for large ones
     const bool persistent = g->per_queue == 0 || (g->per_queue < 0 && q <= 256);

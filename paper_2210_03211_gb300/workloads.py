@@ -363,3 +363,22 @@ def wide_fan(spokes: int = 2100, leaves: int = 20000, leaf_degree: int = 252, ch
     src = np.concatenate([centre, leaf, ca])
     dst = np.concatenate([sp, pick, cb])
     return EdgeList(src.astype(np.int32), dst.astype(np.int32), f"wide_fan_{spokes}_{leaves}x{leaf_degree}")
+
+
+def hub_of_triangles(triangles: int = 10000, extra: int = 2, hub_links: int = 2, seed: int = 0) -> EdgeList:
+    """A hub joined to `hub_links` corners of each of `triangles` disjoint
+    triangles (and, from each first corner, to `extra` random other first
+    corners), so that the hub's neighbours bring one distinct community per
+    triangle: a hub with more candidate communities than one block evaluates
+    at once."""
+    s = Stream(seed, 29)
+    t = np.arange(triangles, dtype=np.int64)
+    a, b, c = 1 + 3 * t, 2 + 3 * t, 3 + 3 * t
+    zero = np.zeros(triangles, np.int64)
+    src = [a, b, a, zero] + ([zero] if hub_links > 1 else [])
+    dst = [b, c, c, a] + ([b] if hub_links > 1 else [])
+    if extra:
+        src.append(np.repeat(a, extra))
+        dst.append(1 + 3 * s.integers(0, triangles, triangles * extra))
+    return EdgeList(np.concatenate(src).astype(np.int32), np.concatenate(dst).astype(np.int32),
+                    f"hub_of_{triangles}_triangles")

@@ -297,6 +297,20 @@ def test_triangle_tiers_parity(lf, oracle_lib, spokes, leaves, leaf_degree):
         compare_state(g, og)
 
 
+@pytest.mark.parametrize("q", [4096, 1 << 30])
+def test_hub_with_many_candidates(lf, oracle_lib, q):
+    """A hub whose neighbours bring over 10,000 distinct communities: its
+    candidates are screened and evaluated by several blocks.  Every output
+    equal to the oracle's."""
+    el = W.hub_of_triangles(12000, extra=2, seed=3)
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(q, -math.inf, 3)
+    with lf.Graph(el.src, el.dst) as g:
+        compare_preprocessing(g, og)
+        compare_run(g.run(q, -math.inf, 3), ref)
+        compare_state(g, og)
+
+
 @pytest.mark.parametrize("q", [1024, 65536])
 def test_large_shape_scaled_parity(lf, oracle_lib, q):
     """The 3.07M-node workload's shape (Chung-Lu exponent 2.2, community sizes
