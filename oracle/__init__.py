@@ -59,6 +59,7 @@ def lib():
             "og_get_state": (None, [_P, _I64P, _I32P, _I64P, _I64P, _I64P]),
             "og_get_run": (None, [_P, _I32P, _I32P, _F64P, _F64P, _I64P, _I64P, C.c_int32]),
             "og_set_check_invariants": (None, [_P, C.c_int]),
+            "og_set_partition": (C.c_int, [_P, _I64P, _I32P, C.c_int64]),
             "og_invariant_failures": (C.c_int, [_P]),
             "og_evaluate": (None, [_P, C.c_int32, _I32P, _I32P, _I64P, _I64P, _F64P, _F64P]),
             "og_total": (C.c_double, [_P]),
@@ -161,6 +162,21 @@ class OracleGraph:
     def init_clustering(self):
         if lib().og_init_clustering(self._h):
             raise RuntimeError("order not computed")
+
+    def set_partition(self, communities):
+        """Insert a division (list of arrays of original ids) that replaces the
+        initial clustering of the following runs; None removes it."""
+        if communities is None:
+            lib().og_set_partition(self._h, None, None, -1)
+            return
+        sizes = np.array([len(c) for c in communities], dtype=np.int64)
+        off = np.zeros(len(communities) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=off[1:])
+        mem = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int32) for c in communities])
+                                   if communities else np.zeros(1, dtype=np.int32))
+        st = lib().og_set_partition(self._h, _ptr(off, C.c_int64), _ptr(mem, C.c_int32), len(communities))
+        if st:
+            raise ValueError(f"og_set_partition failed {st}")
 
     def set_check_invariants(self, on: bool):
         lib().og_set_check_invariants(self._h, 1 if on else 0)

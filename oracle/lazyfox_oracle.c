@@ -74,6 +74,12 @@ typedef struct og_graph {
     int32_t hist_cap;
     int check_invariants;  /* recount aggregates after every batch */
     int invariant_failures;
+    /* an inserted division replacing the initial clustering (Methods,
+     * Initial Clustering): community c holds part_mem[part_off[c] .. part_off[c+1])
+     * (dense ids); part_k < 0 = none */
+    int64_t part_k;
+    int64_t *part_off;
+    int32_t *part_mem;
 } og_graph;
 
 /* ------------------------------------------------------------------------ */
@@ -165,6 +171,7 @@ og_graph *og_create(const int32_t *src, const int32_t *dst, int64_t num_edges, i
     *status = OG_OK;
     og_graph *g = (og_graph *)calloc(1, sizeof(og_graph));
     if (!g) { *status = OG_ERR_OOM; return NULL; }
+    g->part_k = -1;
     for (int64_t e = 0; e < num_edges; ++e) {
         if (src[e] < 0 || dst[e] < 0) { *status = OG_ERR_INVALID; free(g); return NULL; }
     }
@@ -500,6 +507,73 @@ int og_init_clustering(og_graph *g)
     return OG_OK;
 }
 
+/* Initial state from an inserted division (Methods, Initial Clustering: an
+ * existing division may replace the initial clustering step).  Community ids
+ * are the division's indices, in its order; aggregates counted from scratch:
+ * n_C members, m_C edges with both ends in C, vol_C the members' degrees. */
+static int init_from_partition(og_graph *g)
+{
+    free_state(g);
+    int64_t n = g->n, k = g->part_k;
+    g->mem = (int32_t **)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t *));
+    g->nmem = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    g->capmem = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    g->ncomm = k;
+    g->cn = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
+    g->cm = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
+    g->cvol = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
+    for (int64_t c = 0; c < k; ++c)
+        for (int64_t i = g->part_off[c]; i < g->part_off[c + 1]; ++i) {
+            int32_t x = g->part_mem[i];
+            mem_insert(g, x, (int32_t)c);
+            g->cn[c]++;
+            g->cvol[c] += deg(g, x);
+        }
+    for (int64_t x = 0; x < n; ++x)
+        for (int32_t j = 0; j < g->nmem[x]; ++j) {
+            int32_t c = g->mem[x][j];
+            for (int64_t p = g->off[x]; p < g->off[x + 1]; ++p)
+                if (g->adj[p] > x && mem_has(g, g->adj[p], c)) g->cm[c]++;
+        }
+    return OG_OK;
+}
+
+/* Insert a division: community c holds original ids members[off[c] ..
+ * off[c+1]).  k < 0 removes it.  OG_ERR_INVALID for offsets that do not start
+ * at 0 or decrease, ids not in the graph, or an id twice in one community. */
+int og_set_partition(og_graph *g, const int64_t *off, const int32_t *members, int64_t k)
+{
+    free(g->part_off); free(g->part_mem);
+    g->part_off = NULL; g->part_mem = NULL; g->part_k = -1;
+    if (k < 0) return OG_OK;
+    if (off[0] != 0) return OG_ERR_INVALID;
+    for (int64_t c = 0; c < k; ++c)
+        if (off[c + 1] < off[c]) return OG_ERR_INVALID;
+    int64_t total = off[k];
+    int64_t *po = (int64_t *)malloc((size_t)(k + 1) * sizeof(int64_t));
+    int32_t *pm = (int32_t *)malloc((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
+    for (int64_t c = 0; c <= k; ++c) po[c] = off[c];
+    for (int64_t i = 0; i < total; ++i) {
+        int32_t x = dense_id(g->labels, g->n, members[i]);
+        if (x < 0) { free(po); free(pm); return OG_ERR_INVALID; }
+        pm[i] = x;
+    }
+    for (int64_t c = 0; c < k; ++c) {   /* an id at most once per community */
+        int64_t len = po[c + 1] - po[c];
+        int32_t *tmp = (int32_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int32_t));
+        memcpy(tmp, pm + po[c], (size_t)len * sizeof(int32_t));
+        qsort(tmp, (size_t)len, sizeof(int32_t), cmp_i32);
+        int dup = 0;
+        for (int64_t i = 1; i < len; ++i) dup |= tmp[i] == tmp[i - 1];
+        free(tmp);
+        if (dup) { free(po); free(pm); return OG_ERR_INVALID; }
+    }
+    g->part_off = po;
+    g->part_mem = pm;
+    g->part_k = k;
+    return OG_OK;
+}
+
 /* \wcchat(P): sum over every (node, community) membership of the per-node
  * estimator, added with the correctly rounded sum. */
 double og_total(const og_graph *g)
@@ -642,7 +716,7 @@ static void prune(og_graph *g)
 int og_run(og_graph *g, int32_t queue_size, double threshold, int32_t max_iters, int64_t max_batches)
 {
     if (queue_size < 1 || max_iters < 0) return OG_ERR_INVALID;
-    int st = og_init_clustering(g);
+    int st = g->part_k >= 0 ? init_from_partition(g) : og_init_clustering(g);
     if (st) return st;
     free(g->T_hist); free(g->joins_hist); free(g->leaves_hist);
     g->hist_cap = max_iters > 0 ? max_iters : 1;
@@ -781,6 +855,7 @@ void og_destroy(og_graph *g)
 {
     if (!g) return;
     free_state(g);
+    free(g->part_off); free(g->part_mem);
     free(g->labels); free(g->off); free(g->adj); free(g->t); free(g->vt); free(g->order);
     free(g->T_hist); free(g->joins_hist); free(g->leaves_hist);
     free(g);

@@ -1,0 +1,101 @@
+"""Pins of the oracle's inserted division (Methods, Initial Clustering: an
+existing division may replace the initial clustering) and of resuming from
+the communities saved after an iteration (the per-iteration results the paper
+writes to disk on Friendster)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2210_03211_gb300 import workloads as W
+
+
+def _recount(og, comms):
+    """n_C, internal edges m_C and vol_C of a cover, by brute force."""
+    off, adj, labels = og.csr()
+    deg = np.diff(off)
+    pos = {int(l): i for i, l in enumerate(labels)}
+    out = []
+    for c in comms:
+        xs = sorted(pos[int(v)] for v in c)
+        S = set(xs)
+        m = sum(1 for x in xs for y in adj[off[x]:off[x + 1]] if y > x and int(y) in S)
+        out.append((len(xs), m, int(sum(deg[x] for x in xs))))
+    return out
+
+
+def test_inserted_initial_clustering_reproduces_the_run(oracle_lib):
+    """The initial clustering, taken out and inserted again, gives the same run
+    bit for bit (so the inserted state is exactly the one the clustering
+    builds: same ids, same aggregates)."""
+    el = W.eu_core_like()
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    g.run(16, 0.01, 0)
+    init = g.communities()
+    ref = g.run(16, 0.01, 50)
+    ref_state = g.state()
+    g2 = oracle_lib.OracleGraph(el.src, el.dst)
+    g2.set_partition(init)
+    out = g2.run(16, 0.01, 50)
+    assert out["T0"] == ref["T0"] and out["iterations"] == ref["iterations"]
+    assert np.array_equal(out["T"], ref["T"])
+    assert np.array_equal(out["joins"], ref["joins"]) and np.array_equal(out["leaves"], ref["leaves"])
+    s = g2.state()
+    for key in ("mem_off", "mem_ids", "n", "m", "vol"):
+        assert np.array_equal(s[key], ref_state[key]), key
+
+
+@pytest.mark.parametrize("q,a,b", [(1, 2, 3), (64, 1, 4), (1 << 20, 3, 2)])
+def test_resume_from_saved_communities_equals_one_run(oracle_lib, q, a, b):
+    """Run a iterations, save the communities, insert them and run b more: the
+    same totals, moves and final communities as a + b iterations in one run."""
+    el = W.random_graph(n=300, m=1800, seed=7, hubs=2, hub_degree=60)
+    full = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = full.run(q, -math.inf, a + b)
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    first = g.run(q, -math.inf, a)
+    saved = g.communities()
+    g.set_partition(saved)
+    second = g.run(q, -math.inf, b)
+    assert second["T0"] == first["T"][-1] == ref["T"][a - 1]
+    assert np.array_equal(np.concatenate([first["T"], second["T"]]), ref["T"])
+    assert np.array_equal(np.concatenate([first["joins"], second["joins"]]), ref["joins"])
+    assert np.array_equal(np.concatenate([first["leaves"], second["leaves"]]), ref["leaves"])
+    assert [c.tolist() for c in g.communities()] == [c.tolist() for c in full.communities()]
+
+
+def test_inserted_cover_aggregates_equal_brute_force(oracle_lib):
+    """An overlapping cover (the planted one, plus a community spanning
+    several of them): n_C, m_C, vol_C equal a brute-force recount, and every
+    node's row lists its communities in ascending id."""
+    el = W.eu_core_like()
+    comms = [np.asarray(c, dtype=np.int32) for c in el.planted]
+    comms.append(np.unique(np.concatenate([comms[0][:5], comms[1][:5], comms[2][:5]])))
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    _, _, labels = g.csr()
+    comms = [c[np.isin(c, labels)] for c in comms]
+    g.set_partition(comms)
+    g.run(1, 0.01, 0)
+    s = g.state()
+    want = _recount(g, comms)
+    assert [(int(s["n"][c]), int(s["m"][c]), int(s["vol"][c])) for c in range(len(comms))] == want
+    for x in range(g.n):
+        row = s["mem_ids"][s["mem_off"][x]:s["mem_off"][x + 1]]
+        assert np.all(np.diff(row) > 0)
+    g.set_check_invariants(True)
+    g.run(1, 0.01, 3)
+    assert g.invariant_failures() == 0
+
+
+def test_invalid_divisions_are_rejected(oracle_lib):
+    el = W.from_pairs(W.clique(4) + [(3, 10)], "k4_tail")
+    g = oracle_lib.OracleGraph(el.src, el.dst)
+    with pytest.raises(ValueError):
+        g.set_partition([np.array([0, 1, 99], dtype=np.int32)])   # 99 is not a node
+    with pytest.raises(ValueError):
+        g.set_partition([np.array([0, 1, 1], dtype=np.int32)])    # 1 twice in one community
+    g.set_partition([np.array([0, 1], dtype=np.int32), np.array([1, 2, 3, 10], dtype=np.int32)])
+    g.set_partition(None)   # back to the initial clustering
+    a = g.run(1, 0.01, 5)
+    b = oracle_lib.OracleGraph(el.src, el.dst).run(1, 0.01, 5)
+    assert np.array_equal(a["T"], b["T"])
