@@ -237,6 +237,40 @@ lf_status lf_get_state(lf_graph *g, int64_t *mem_offsets, int32_t *mem_ids,
                        int64_t *num_memberships, int64_t *num_comm_ids);
 
 /*
+ * lf_set_partition -- insert an existing division that replaces the initial
+ * clustering of the following lf_run calls (Methods, Initial Clustering: an
+ * existing division can be inserted instead of the greedy clustering).
+ * Community c (0 <= c < num_communities) holds the original node ids
+ * members[offsets[c] .. offsets[c+1]); communities may overlap; community ids
+ * in the run are the indices c, so ties between communities are broken in
+ * the given order.  Passing the communities that lf_get_communities returned
+ * after iteration k of a run, and running again, continues that run exactly
+ * (the same totals, moves and communities as one longer run).
+ * offsets: host, num_communities + 1 entries, offsets[0] = 0, non-decreasing.
+ * members: host, offsets[num_communities] entries; copied.
+ * num_communities < 0 (pointers ignored) removes the division: lf_run goes back
+ * to the initial clustering.
+ * Errors: LF_ERR_INVALID for bad offsets, an id that is not a node of the graph
+ *         or an id twice in one community; LF_ERR_CAPACITY for more
+ *         communities than nodes.  On error the previous division is kept.
+ */
+lf_status lf_set_partition(lf_graph *g, const int64_t *offsets, const int32_t *members,
+                           int64_t num_communities);
+
+/*
+ * lf_set_iteration_callback -- cb(g, iteration, wcc, ctx) is called by lf_run
+ * after every iteration, once the iteration's pruning and WCC-hat(P) total
+ * (wcc) are done and before the stopping test.  Inside it lf_get_communities
+ * and the other getters may be called on g (to save the intermediate
+ * communities, as the paper does after each iteration on Friendster); lf_run
+ * and lf_set_partition may not.  A nonzero return ends the run after this
+ * iteration (stats->converged stays 0).  cb = NULL removes it.  Host code,
+ * called on the thread that called lf_run.
+ */
+typedef int (*lf_iteration_fn)(lf_graph *g, int32_t iteration, double wcc, void *ctx);
+lf_status lf_set_iteration_callback(lf_graph *g, lf_iteration_fn cb, void *ctx);
+
+/*
  * lf_run_partial -- lf_run that stops after max_batches queues in total
  * (iteration ends run only for completed iterations), for per-queue parity
  * checks.  max_batches < 0 behaves like lf_run.

@@ -1,4 +1,5 @@
 // C ABI entry points, error plumbing, device memory, and result extraction.
+#include <algorithm>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -221,7 +222,74 @@ lf_status lf_run(lf_graph *g, int32_t queue_size, double wcc_threshold, int32_t 
         set_error(LF_ERR_INVALID, "graph is NULL");
         return LF_ERR_INVALID;
     }
+    if (g->in_callback) {
+        set_error(LF_ERR_STATE, "lf_run inside an iteration callback");
+        return LF_ERR_STATE;
+    }
     return call_guarded([&] { run_impl(g, queue_size, wcc_threshold, max_iters, -1, stats); });
+}
+
+lf_status lf_set_partition(lf_graph *g, const int64_t *offsets, const int32_t *members, int64_t num_communities) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    if (g->in_callback) {
+        set_error(LF_ERR_STATE, "lf_set_partition inside an iteration callback");
+        return LF_ERR_STATE;
+    }
+    return call_guarded([&] {
+        if (num_communities < 0) {
+            g->part_k = -1;
+            g->part_off.clear();
+            g->part_mem.clear();
+            g->part_maxcnt = 0;
+            return;
+        }
+        if (!offsets) lf::fail(LF_ERR_INVALID, "offsets is NULL");
+        if (num_communities > g->n)
+            lf::fail(LF_ERR_CAPACITY, "%lld communities for %lld nodes", (long long)num_communities, (long long)g->n);
+        if (offsets[0] != 0) lf::fail(LF_ERR_INVALID, "offsets[0] = %lld, not 0", (long long)offsets[0]);
+        for (int64_t c = 0; c < num_communities; ++c)
+            if (offsets[c + 1] < offsets[c]) lf::fail(LF_ERR_INVALID, "offsets decrease at community %lld", (long long)c);
+        const int64_t total = offsets[num_communities];
+        if (total > 0 && !members) lf::fail(LF_ERR_INVALID, "members is NULL");
+        // original ids -> dense ids through the (ascending) label table
+        std::vector<int32_t> labels((size_t)g->n);
+        if (g->n > 0) {
+            LF_CUDA(cudaMemcpyAsync(labels.data(), g->labels, (size_t)g->n * 4, cudaMemcpyDeviceToHost, g->stream));
+            LF_CUDA(cudaStreamSynchronize(g->stream));
+        }
+        std::vector<int32_t> dense((size_t)total), cnt((size_t)g->n, 0);
+        for (int64_t i = 0; i < total; ++i) {
+            const auto it = std::lower_bound(labels.begin(), labels.end(), members[i]);
+            if (it == labels.end() || *it != members[i])
+                lf::fail(LF_ERR_INVALID, "id %d is not a node of the graph", members[i]);
+            dense[(size_t)i] = (int32_t)(it - labels.begin());
+        }
+        int32_t maxcnt = 0;
+        for (int64_t c = 0; c < num_communities; ++c) {
+            std::vector<int32_t> row(dense.begin() + offsets[c], dense.begin() + offsets[c + 1]);
+            std::sort(row.begin(), row.end());
+            if (std::adjacent_find(row.begin(), row.end()) != row.end())
+                lf::fail(LF_ERR_INVALID, "a node appears twice in community %lld", (long long)c);
+            for (int32_t x : row) maxcnt = std::max(maxcnt, ++cnt[(size_t)x]);
+        }
+        g->part_off.assign(offsets, offsets + num_communities + 1);
+        g->part_mem = std::move(dense);
+        g->part_k = num_communities;
+        g->part_maxcnt = maxcnt;
+    });
+}
+
+lf_status lf_set_iteration_callback(lf_graph *g, lf_iteration_fn cb, void *ctx) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    g->it_cb = cb;
+    g->it_ctx = ctx;
+    return LF_OK;
 }
 
 lf_status lf_run_partial(lf_graph *g, int32_t queue_size, double wcc_threshold, int32_t max_iters,
@@ -229,6 +297,10 @@ lf_status lf_run_partial(lf_graph *g, int32_t queue_size, double wcc_threshold, 
     if (!g) {
         set_error(LF_ERR_INVALID, "graph is NULL");
         return LF_ERR_INVALID;
+    }
+    if (g->in_callback) {
+        set_error(LF_ERR_STATE, "lf_run inside an iteration callback");
+        return LF_ERR_STATE;
     }
     return call_guarded([&] { run_impl(g, queue_size, wcc_threshold, max_iters, max_batches, stats); });
 }

@@ -130,6 +130,14 @@ struct lf_graph {
     // run state
     bool ran = false;
     int64_t ncomm = 0;            // community ids 0..ncomm-1
+    // inserted division (dense ids), replacing the initial clustering; part_k < 0 = none
+    int64_t part_k = -1;
+    std::vector<int64_t> part_off;
+    std::vector<int32_t> part_mem;
+    int32_t part_maxcnt = 0;      // most communities of one node in it
+    lf_iteration_fn it_cb = nullptr;
+    void *it_ctx = nullptr;
+    bool in_callback = false;
     lf::CommRec *comm = nullptr;  // n records (ncomm used)
     unsigned long long *stamp = nullptr;  // n words
     int32_t K = 0;                // row capacity

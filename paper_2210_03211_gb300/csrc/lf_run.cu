@@ -154,6 +154,60 @@ __global__ void k_init_rows(RunArgs a, const int32_t *comm_of, int64_t n) {
     }
 }
 
+__device__ __forceinline__ bool row_has_c(const int32_t *row, int32_t cnt, int32_t c) {
+    int lo = 0, hi = cnt - 1;   // rows are ascending
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int32_t v = row[mid];
+        if (v == c) return true;
+        if (v < c) lo = mid + 1; else hi = mid - 1;
+    }
+    return false;
+}
+
+// An inserted division as the initial state: entries x << 32 | c sorted
+// ascending, so x's communities are a run of ascending ids.  Rows, member
+// counts and degree sums here; internal edges in k_part_m2.
+__global__ void k_part_rows(RunArgs a, const unsigned long long *keys, int64_t E, int32_t maxcnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = keys[i];
+        const int64_t x = (int64_t)(key >> 32);
+        const int32_t c = (int32_t)(key & 0xffffffffull);
+        int64_t lo = 0, hi = i;   // first entry of x's run
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)(keys[mid] >> 32) < x) lo = mid + 1; else hi = mid;
+        }
+        a.mem[x * a.K + (i - lo)] = c;
+        atomicAdd(&a.comm[c].n, 1);
+        atomicAdd(&a.comm[c].vol, (uint32_t)a.deg[x]);
+        if (i + 1 == E || (int64_t)(keys[i + 1] >> 32) != x) a.nmem[x] = (int32_t)(i - lo + 1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ds->maxcnt = maxcnt;
+        a.ds->memberships = (unsigned long long)E;
+    }
+}
+
+// 2m_C of the inserted division: for each membership (x, C), the neighbours of
+// x that are in C (one warp per membership).
+__global__ void k_part_m2(RunArgs a, const unsigned long long *keys, int64_t E) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < E; i += warps) {
+        const unsigned long long key = keys[i];
+        const int64_t x = (int64_t)(key >> 32);
+        const int32_t c = (int32_t)(key & 0xffffffffull);
+        int cnt = 0;
+        for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
+            const int32_t y = a.adj[p];
+            cnt += row_has_c(a.mem + (int64_t)y * a.K, a.nmem[y], c);
+        }
+        cnt = __reduce_add_sync(FULL, cnt);
+        if (lane == 0 && cnt) atomicAdd(&a.comm[c].m2, (uint32_t)cnt);
+    }
+}
+
 __global__ void k_init_m2(RunArgs a, const int32_t *comm_of, int64_t n) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -2887,9 +2941,35 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         g->qtimes = dalloc_n<unsigned long long>(g, nb_all + 1);
     }
 
-    // ---- a6: initial clustering
+    // ---- a6: initial clustering, or an inserted division
     int64_t k0 = 0;
-    if (n > 0) {
+    if (n > 0 && g->part_k >= 0) {
+        if (g->part_maxcnt + 1 > g->K) {
+            grow_rows(g, g->part_maxcnt + 1);
+            a = make_args(g, device_readback(g));
+        }
+        const int64_t E = (int64_t)g->part_mem.size();
+        if (E > 0) {
+            std::vector<unsigned long long> hk((size_t)E);
+            for (int64_t c = 0; c < g->part_k; ++c)
+                for (int64_t i = g->part_off[(size_t)c]; i < g->part_off[(size_t)c + 1]; ++i)
+                    hk[(size_t)i] = ((unsigned long long)g->part_mem[(size_t)i] << 32) | (unsigned long long)c;
+            unsigned long long *keys = dalloc_n<unsigned long long>(g, E);
+            LF_CUDA(cudaMemcpyAsync(keys, hk.data(), (size_t)E * 8, cudaMemcpyHostToDevice, st));
+            std::vector<int> shifts;
+            const int bc = bits_for((unsigned long long)std::max<int64_t>(g->part_k - 1, 0));
+            const int bx = bits_for((unsigned long long)(n - 1));
+            for (int b = 0; b < bc; b += 8) shifts.push_back(b);
+            for (int b = 0; b < bx; b += 8) shifts.push_back(32 + b);
+            radix_sort(g, keys, nullptr, E, shifts);
+            k_part_rows<<<grid_for(E, 256, 1 << 16), 256, 0, st>>>(a, keys, E, g->part_maxcnt); ++g->launches;
+            k_part_m2<<<grid_for(E * 32, 256, 1 << 16), 256, 0, st>>>(a, keys, E); ++g->launches;
+            LF_LAUNCHED();
+            LF_CUDA(cudaStreamSynchronize(st));
+            dfree(g, keys);
+        }
+        k0 = g->part_k;
+    } else if (n > 0) {
         int32_t *state = dalloc_n<int32_t>(g, n);
         int32_t *und = dalloc_n<int32_t>(g, 1);
         LF_CUDA(cudaMemsetAsync(state, 0, (size_t)n * 4, st));
@@ -3053,6 +3133,18 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             if (stats->leaves_history) stats->leaves_history[it - 1] = (int64_t)rb.leaves;
         }
         const double T = rb.total;
+        if (g->it_cb) {   // the caller may read the communities of this iteration
+            g->in_callback = true;
+            int halt = 0;
+            try {
+                halt = g->it_cb(g, it, T, g->it_ctx);
+            } catch (...) {
+                g->in_callback = false;
+                throw;
+            }
+            g->in_callback = false;
+            if (halt) break;
+        }
         bool stop;
         if (prev == 0.0) stop = (T == 0.0);
         else stop = ((T - prev) / prev) < thr;

@@ -24,7 +24,7 @@ _STATUS = {1: "LF_ERR_INVALID", 2: "LF_ERR_OOM", 3: "LF_ERR_CUDA", 4: "LF_ERR_CA
 ABI_FUNCTIONS = ("lf_graph_create", "lf_run", "lf_run_partial", "lf_get_communities",
                  "lf_get_node_stats", "lf_get_sizes", "lf_get_create_stats", "lf_get_csr",
                  "lf_get_oriented", "lf_get_order", "lf_get_state", "lf_graph_destroy",
-                 "lf_last_error", "lf_triangles_noalloc")
+                 "lf_last_error", "lf_triangles_noalloc", "lf_set_partition", "lf_set_iteration_callback")
 
 
 class LazyFoxError(RuntimeError):
@@ -35,6 +35,7 @@ class LazyFoxError(RuntimeError):
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 _FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_ITER_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.c_double, C.c_void_p)
 
 
 class Options(C.Structure):
@@ -94,6 +95,8 @@ def load_library(path: str | None = None) -> C.CDLL:
         "lf_graph_destroy": (None, [P]),
         "lf_last_error": (C.c_char_p, []),
         "lf_triangles_noalloc": (C.c_int, [P, P, C.c_int64, C.c_int64, P, P, P]),
+        "lf_set_partition": (C.c_int, [P, i64p, i32p, C.c_int64]),
+        "lf_set_iteration_callback": (C.c_int, [P, _ITER_FN, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -244,8 +247,54 @@ class Graph:
         self.close()
 
     # -- the method -----------------------------------------------------------
+    def set_partition(self, communities):
+        """Insert a division that replaces the initial clustering of the next
+        runs: a list of arrays of original node ids (may overlap), or an
+        (offsets, members) pair as `communities()` returns; None removes it."""
+        if communities is None:
+            _check(self._L, self._L.lf_set_partition(self._h, None, None, -1))
+            return
+        if isinstance(communities, tuple) and len(communities) == 2 and np.ndim(communities[0]) == 1 \
+                and np.asarray(communities[0]).dtype.kind == "i" and not isinstance(communities[0], list):
+            off = np.ascontiguousarray(communities[0], dtype=np.int64)
+            mem = np.ascontiguousarray(communities[1], dtype=np.int32)
+        else:
+            sizes = np.array([len(c) for c in communities], dtype=np.int64)
+            off = np.zeros(sizes.shape[0] + 1, dtype=np.int64)
+            np.cumsum(sizes, out=off[1:])
+            mem = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int32) for c in communities])
+                                       if len(communities) else np.zeros(0, np.int32))
+        if mem.shape[0] == 0:
+            mem = np.zeros(1, np.int32)
+        _check(self._L, self._L.lf_set_partition(self._h, _ptr(off, C.c_int64), _ptr(mem, C.c_int32),
+                                                 off.shape[0] - 1))
+
     def run(self, queue_size: int, wcc_threshold: float = 0.01, max_iters: int = 50,
-            max_batches: int | None = None) -> RunStats:
+            max_batches: int | None = None, on_iteration=None) -> RunStats:
+        """on_iteration(iteration, wcc) is called after every iteration; it may
+        call communities() (the intermediate result) and returns True to stop."""
+        cb = None
+        if on_iteration is not None:
+            def _tramp(_g, it, wcc, _ctx):
+                try:
+                    return 1 if on_iteration(int(it), float(wcc)) else 0
+                except Exception:  # noqa: BLE001 - stop the run; the error is re-raised below
+                    import sys
+                    self._cb_error = sys.exc_info()[1]
+                    return 1
+            cb = _ITER_FN(_tramp)
+            self._cb_error = None
+            _check(self._L, self._L.lf_set_iteration_callback(self._h, cb, None))
+        try:
+            return self._run(queue_size, wcc_threshold, max_iters, max_batches)
+        finally:
+            if cb is not None:
+                self._L.lf_set_iteration_callback(self._h, _ITER_FN(), None)
+                if self._cb_error is not None:
+                    err, self._cb_error = self._cb_error, None
+                    raise err
+
+    def _run(self, queue_size, wcc_threshold, max_iters, max_batches) -> RunStats:
         cap = max(1, max_iters)
         T = np.zeros(cap, np.float64)
         J = np.zeros(cap, np.int64)
