@@ -271,6 +271,52 @@ typedef int (*lf_iteration_fn)(lf_graph *g, int32_t iteration, double wcc, void 
 lf_status lf_set_iteration_callback(lf_graph *g, lf_iteration_fn cb, void *ctx);
 
 /*
+ * lf_batch_create -- many independent graphs in one handle, run together:
+ * every kernel launch of lf_run covers all of them (SURVEY's batched
+ * configuration; the paper runs one graph at a time).  Graph i is the edge
+ * list src/dst[edge_offsets[i] .. edge_offsets[i+1]) with its own ids (>= 0);
+ * each graph is treated exactly as lf_graph_create + lf_run would treat it
+ * alone: its own node order, global clustering coefficient cc, initial
+ * clustering, queues of queue_size of its nodes, WCC-hat(P) and stopping test
+ * (a graph that stops leaves the later queues).  Internally the graphs form
+ * one disjoint union (ids shifted per graph; queue j holds the j-th
+ * queue_size nodes of every active graph).
+ * src, dst    : host, edge_offsets[num_graphs] entries each.
+ * edge_offsets: host, num_graphs + 1 entries, [0] = 0, non-decreasing.
+ * Errors: LF_ERR_INVALID (bad offsets, negative ids), LF_ERR_CAPACITY (the
+ *         shifted ids or the edges exceed 2^31-1), LF_ERR_CUDA, LF_ERR_OOM.
+ * The handle takes lf_run (not lf_run_partial or lf_set_partition), the
+ * getters of one graph (over the union), and the lf_batch_get_* calls.
+ */
+lf_status lf_batch_create(const int32_t *src, const int32_t *dst, const int64_t *edge_offsets,
+                          int64_t num_graphs, const lf_options *opt, lf_graph **out);
+
+/*
+ * lf_batch_get_info -- per graph of a batch (host arrays, any may be NULL):
+ * node_offsets (num_graphs + 1: graph i's nodes are the union's dense ids
+ * [node_offsets[i], node_offsets[i+1])), iterations run, converged (1/0),
+ * WCC-hat(P) after the initial clustering and at the end, and cc.
+ * LF_ERR_STATE if g is not a batch.
+ */
+lf_status lf_batch_get_info(lf_graph *g, int64_t *num_graphs, int64_t *node_offsets, int32_t *iterations,
+                            int32_t *converged, double *wcc_initial, double *wcc_final, double *cc);
+
+/* WCC-hat(P) after each iteration of one graph of a batch: *count values, at
+ * most cap written to wcc. */
+lf_status lf_batch_get_history(lf_graph *g, int64_t graph, double *wcc, int32_t cap, int32_t *count);
+
+/*
+ * lf_batch_get_communities -- lf_get_communities of a batch, with the members
+ * in their own graph's ids and graph_offsets (num_graphs + 1 entries; may be
+ * NULL) telling which communities belong to which graph: graph i's are
+ * [graph_offsets[i], graph_offsets[i+1]).  Size queries as in
+ * lf_get_communities.
+ */
+lf_status lf_batch_get_communities(lf_graph *g, int64_t *graph_offsets, int64_t *offsets, int64_t offsets_cap,
+                                   int32_t *members, int64_t members_cap, int64_t *num_communities,
+                                   int64_t *num_members);
+
+/*
  * lf_run_partial -- lf_run that stops after max_batches queues in total
  * (iteration ends run only for completed iterations), for per-queue parity
  * checks.  max_batches < 0 behaves like lf_run.

@@ -137,6 +137,8 @@ void release_all(lf_graph *g) {
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->rb) cudaFreeHost(g->rb);
     g->rb = nullptr;
+    if (g->gT_host) cudaFreeHost(g->gT_host);
+    g->gT_host = nullptr;
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     g->stream = nullptr;
 }
@@ -151,12 +153,12 @@ const char *lf_last_error(void) {
     return copy.c_str();
 }
 
-lf_status lf_graph_create(const int32_t *src, const int32_t *dst, int64_t num_edges, const lf_options *opt,
-                          lf_graph **out) {
-    if (!out) {
-        set_error(LF_ERR_INVALID, "out is NULL");
-        return LF_ERR_INVALID;
-    }
+namespace {
+// Shared by lf_graph_create and lf_batch_create: the handle, its options and
+// stream, then the preprocessing.  batch_base: for a batch, the id shift of
+// every graph (ngraphs + 1 entries), else empty.
+lf_status create_handle(const int32_t *src, const int32_t *dst, int64_t num_edges, const lf_options *opt,
+                        const std::vector<int64_t> &batch_base, lf_graph **out) {
     *out = nullptr;
     lf_graph *g = nullptr;
     lf_status st = call_guarded([&] {
@@ -164,6 +166,10 @@ lf_status lf_graph_create(const int32_t *src, const int32_t *dst, int64_t num_ed
         if (num_edges > 0 && (!src || !dst)) fail(LF_ERR_INVALID, "src/dst is NULL");
         if (num_edges >= (1ll << 31)) fail(LF_ERR_CAPACITY, "more than 2^31-1 input edges");
         g = new lf_graph();
+        if (!batch_base.empty()) {
+            g->ngraphs = (int64_t)batch_base.size() - 1;
+            g->gbase = batch_base;
+        }
         if (opt) {
             g->stream = static_cast<cudaStream_t>(opt->stream);
             g->alloc_cb = opt->alloc;
@@ -195,7 +201,7 @@ lf_status lf_graph_create(const int32_t *src, const int32_t *dst, int64_t num_ed
         std::memset(g->rb, 0, sizeof(lf::Readback));
         g->ds = static_cast<lf::DevScalars *>(dalloc(g, sizeof(lf::DevScalars) + sizeof(lf::Readback)));
         LF_CUDA(cudaMemsetAsync(g->ds, 0, sizeof(lf::DevScalars) + sizeof(lf::Readback), g->stream));
-        build_graph(g, src, dst, num_edges, opt && opt->edges_on_device);
+        build_graph(g, src, dst, num_edges, batch_base.empty() && opt && opt->edges_on_device);
     });
     if (st != LF_OK) {
         if (g) {
@@ -205,6 +211,138 @@ lf_status lf_graph_create(const int32_t *src, const int32_t *dst, int64_t num_ed
         return st;
     }
     *out = g;
+    return LF_OK;
+}
+}  // namespace
+
+lf_status lf_graph_create(const int32_t *src, const int32_t *dst, int64_t num_edges, const lf_options *opt,
+                          lf_graph **out) {
+    if (!out) {
+        set_error(LF_ERR_INVALID, "out is NULL");
+        return LF_ERR_INVALID;
+    }
+    return create_handle(src, dst, num_edges, opt, std::vector<int64_t>(), out);
+}
+
+lf_status lf_batch_create(const int32_t *src, const int32_t *dst, const int64_t *edge_offsets, int64_t num_graphs,
+                          const lf_options *opt, lf_graph **out) {
+    if (!out) {
+        set_error(LF_ERR_INVALID, "out is NULL");
+        return LF_ERR_INVALID;
+    }
+    *out = nullptr;
+    std::vector<int32_t> s2, d2;
+    std::vector<int64_t> base;
+    lf_status st = call_guarded([&] {
+        if (num_graphs < 1) fail(LF_ERR_INVALID, "num_graphs must be >= 1");
+        if (!edge_offsets) fail(LF_ERR_INVALID, "edge_offsets is NULL");
+        if (edge_offsets[0] != 0) fail(LF_ERR_INVALID, "edge_offsets[0] must be 0");
+        for (int64_t i = 0; i < num_graphs; ++i)
+            if (edge_offsets[i + 1] < edge_offsets[i]) fail(LF_ERR_INVALID, "edge_offsets decrease at graph %lld", (long long)i);
+        const int64_t E = edge_offsets[num_graphs];
+        if (E > 0 && (!src || !dst)) fail(LF_ERR_INVALID, "src/dst is NULL");
+        if (E >= (1ll << 31)) fail(LF_ERR_CAPACITY, "more than 2^31-1 input edges");
+        // each graph's ids shifted past the previous graphs' largest id: one
+        // disjoint union whose dense ids keep the graphs apart and in order
+        base.assign((size_t)num_graphs + 1, 0);
+        for (int64_t i = 0; i < num_graphs; ++i) {
+            int64_t mx = -1;
+            for (int64_t e = edge_offsets[i]; e < edge_offsets[i + 1]; ++e) {
+                if (src[e] < 0 || dst[e] < 0) fail(LF_ERR_INVALID, "negative node id in graph %lld", (long long)i);
+                mx = std::max<int64_t>(mx, std::max(src[e], dst[e]));
+            }
+            base[(size_t)i + 1] = base[(size_t)i] + mx + 1;
+            if (base[(size_t)i + 1] >= (1ll << 31)) fail(LF_ERR_CAPACITY, "shifted node ids exceed 2^31-1");
+        }
+        s2.resize((size_t)E);
+        d2.resize((size_t)E);
+        for (int64_t i = 0; i < num_graphs; ++i)
+            for (int64_t e = edge_offsets[i]; e < edge_offsets[i + 1]; ++e) {
+                s2[(size_t)e] = (int32_t)(src[e] + base[(size_t)i]);
+                d2[(size_t)e] = (int32_t)(dst[e] + base[(size_t)i]);
+            }
+    });
+    if (st != LF_OK) return st;
+    lf_options o{};
+    if (opt) o = *opt;
+    o.edges_on_device = 0;
+    return create_handle(s2.data(), d2.data(), (int64_t)s2.size(), &o, base, out);
+}
+
+lf_status lf_batch_get_info(lf_graph *g, int64_t *num_graphs, int64_t *node_offsets, int32_t *iterations,
+                            int32_t *converged, double *wcc_initial, double *wcc_final, double *cc) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    if (g->ngraphs == 0) {
+        set_error(LF_ERR_STATE, "not a batch");
+        return LF_ERR_STATE;
+    }
+    const int64_t G = g->ngraphs;
+    if (num_graphs) *num_graphs = G;
+    if (node_offsets)
+        for (int64_t i = 0; i <= G; ++i) node_offsets[i] = g->gnoff[(size_t)i];
+    if (cc)
+        for (int64_t i = 0; i < G; ++i) cc[i] = g->gcc_host[(size_t)i];
+    const bool ran = g->ran && (int64_t)g->g_iters.size() == G;
+    for (int64_t i = 0; i < G; ++i) {
+        if (iterations) iterations[i] = ran ? g->g_iters[(size_t)i] : 0;
+        if (converged) converged[i] = ran ? g->g_conv[(size_t)i] : 0;
+        if (wcc_initial) wcc_initial[i] = ran ? g->g_T0[(size_t)i] : 0.0;
+        if (wcc_final)
+            wcc_final[i] = !ran ? 0.0 : (g->g_hist[(size_t)i].empty() ? g->g_T0[(size_t)i] : g->g_hist[(size_t)i].back());
+    }
+    return LF_OK;
+}
+
+lf_status lf_batch_get_history(lf_graph *g, int64_t graph, double *wcc, int32_t cap, int32_t *count) {
+    if (!g || g->ngraphs == 0 || graph < 0 || graph >= g->ngraphs) {
+        set_error(LF_ERR_INVALID, "not a batch, or graph index out of range");
+        return LF_ERR_INVALID;
+    }
+    if (!g->ran || (int64_t)g->g_hist.size() != g->ngraphs) {
+        set_error(LF_ERR_STATE, "no run yet");
+        return LF_ERR_STATE;
+    }
+    const auto &h = g->g_hist[(size_t)graph];
+    if (count) *count = (int32_t)h.size();
+    if (wcc)
+        for (int32_t i = 0; i < cap && i < (int32_t)h.size(); ++i) wcc[i] = h[(size_t)i];
+    return LF_OK;
+}
+
+lf_status lf_batch_get_communities(lf_graph *g, int64_t *graph_offsets, int64_t *offsets, int64_t offsets_cap,
+                                   int32_t *members, int64_t members_cap, int64_t *num_communities,
+                                   int64_t *num_members) {
+    if (!g || g->ngraphs == 0) {
+        set_error(LF_ERR_INVALID, "not a batch");
+        return LF_ERR_INVALID;
+    }
+    int64_t nc = 0, nm = 0;
+    lf_status st = lf_get_communities(g, offsets, offsets_cap, members, members_cap, &nc, &nm);
+    if (num_communities) *num_communities = nc;
+    if (num_members) *num_members = nm;
+    if (st != LF_OK || !offsets || !members) return st;
+    // community ids follow the graph-by-graph node order, so each graph's
+    // communities are one run; members back to the graph's own ids
+    const int64_t G = g->ngraphs;
+    int64_t gi = 0;
+    if (graph_offsets) graph_offsets[0] = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t first = offsets[c], last = offsets[c + 1];
+        const int32_t id0 = last > first ? members[first] : 0;
+        const int64_t gc = (int64_t)(std::upper_bound(g->gbase.begin(), g->gbase.end(), (int64_t)id0) - g->gbase.begin()) - 1;
+        while (gi < gc) {
+            ++gi;
+            if (graph_offsets) graph_offsets[gi] = c;
+        }
+        for (int64_t i = first; i < last; ++i) members[i] = (int32_t)(members[i] - g->gbase[(size_t)gc]);
+    }
+    while (gi < G) {
+        ++gi;
+        if (graph_offsets) graph_offsets[gi] = nc;
+    }
     return LF_OK;
 }
 
@@ -236,6 +374,10 @@ lf_status lf_set_partition(lf_graph *g, const int64_t *offsets, const int32_t *m
     }
     if (g->in_callback) {
         set_error(LF_ERR_STATE, "lf_set_partition inside an iteration callback");
+        return LF_ERR_STATE;
+    }
+    if (g->ngraphs > 0) {
+        set_error(LF_ERR_STATE, "lf_set_partition on a batch of graphs");
         return LF_ERR_STATE;
     }
     return call_guarded([&] {

@@ -8,6 +8,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <algorithm>
+
 #include "lf_internal.cuh"
 
 namespace lf {
@@ -1275,6 +1277,42 @@ __global__ void k_cc_final(DevScalars *ds, int64_t n) {
     ds->cc = n > 0 ? __ddiv_rn(s, (double)n) : 0.0;
 }
 
+// ---- batches of graphs -----------------------------------------------------
+// Graph of each node: its dense id falls in [gnoff[i], gnoff[i+1]).
+__global__ void k_fill_gid(const int64_t *gnoff, int64_t G, int64_t n, int32_t *gid) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = G - 1;   // last i with gnoff[i] <= x
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (gnoff[mid] <= x) lo = mid; else hi = mid - 1;
+        }
+        gid[x] = (int32_t)lo;
+    }
+}
+
+__global__ void k_gid_keys(const uint32_t *vals, const int32_t *gid, int64_t n, unsigned long long *keys) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = (unsigned long long)gid[vals[i]];
+}
+
+// cc of every graph of a batch: RN(exact sum of RN(CC_i) over its nodes) / n_i.
+__global__ void k_cc_sum_batch(const unsigned long long *tri, const int32_t *deg, const int32_t *gid, int64_t n,
+                               unsigned long long *gsacc) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        sacc_add(gsacc + (int64_t)gid[x] * SACC_CHUNKS, local_cc((long long)tri[x], deg[x]));
+}
+
+__global__ void k_cc_final_batch(unsigned long long *gsacc, const int64_t *gnoff, int64_t G, double *gcc,
+                                 float *gcc32) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < G; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ni = gnoff[i + 1] - gnoff[i];
+        const double s = sacc_round_and_clear(gsacc + i * SACC_CHUNKS);
+        const double c = ni > 0 ? __ddiv_rn(s, (double)ni) : 0.0;
+        gcc[i] = c;
+        gcc32[i] = c >= 1e-30 ? (float)c : 0.f;   // 0 turns the FP32 screen off for the graph
+    }
+}
+
 template <typename T>
 T read_scalar(lf_graph *g, const T *dptr) {
     T v;
@@ -1446,6 +1484,28 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
     // ---- a5: order and cc
     g->order = dalloc_n<int32_t>(g, n);
     g->pos = dalloc_n<int32_t>(g, n);
+    int64_t *gnoff_d = nullptr;
+    if (g->ngraphs > 0) {   // a batch: the graph of every node, from the shifted label ranges
+        const int64_t G = g->ngraphs;
+        std::vector<int32_t> lab((size_t)n);
+        if (n > 0) LF_CUDA(cudaMemcpyAsync(lab.data(), g->labels, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+        LF_CUDA(cudaStreamSynchronize(st));
+        g->gnoff.assign((size_t)G + 1, n);
+        for (int64_t i = 0; i < G; ++i)
+            g->gnoff[(size_t)i] = std::lower_bound(lab.begin(), lab.end(), (int32_t)g->gbase[(size_t)i]) - lab.begin();
+        gnoff_d = dalloc_n<int64_t>(g, G + 1);
+        LF_CUDA(cudaMemcpyAsync(gnoff_d, g->gnoff.data(), (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, st));
+        g->gid = dalloc_n<int32_t>(g, std::max<int64_t>(n, 1));
+        if (n > 0) {
+            k_fill_gid<<<grid_for(n, 256, 8192), 256, 0, st>>>(gnoff_d, G, n, g->gid); ++g->launches;
+            LF_LAUNCHED();
+        }
+        g->gcc = dalloc_n<double>(g, G);
+        g->gcc32 = dalloc_n<float>(g, G);
+        g->gT = dalloc_n<double>(g, G);
+        g->gsacc = dalloc_n<unsigned long long>(g, G * SACC_CHUNKS);
+        LF_CUDA(cudaMemsetAsync(g->gsacc, 0, (size_t)(G * SACC_CHUNKS) * 8, st));
+    }
     if (n > 0) {
         unsigned long long *keys = dalloc_n<unsigned long long>(g, n);
         uint32_t *vals = dalloc_n<uint32_t>(g, n);
@@ -1466,12 +1526,32 @@ void build_graph(lf_graph *g, const int32_t *src, const int32_t *dst, int64_t E,
             k_order_fix<<<1, 1, 0, st>>>(keys, vals, utri, g->deg, n); ++g->launches;
             LF_LAUNCHED();
         }
+        if (g->ngraphs > 0) {   // graph by graph: a stable pass on the graph index keeps each graph's order
+            k_gid_keys<<<grid_for(n, 256, 8192), 256, 0, st>>>(vals, g->gid, n, keys); ++g->launches;
+            LF_LAUNCHED();
+            std::vector<int> gs;
+            for (int s = 0; s < bits_for((unsigned long long)(g->ngraphs - 1)); s += 8) gs.push_back(s);
+            radix_sort(g, keys, vals, n, gs);
+        }
         k_positions<<<grid_for(n, 256, 8192), 256, 0, st>>>(vals, n, g->order, g->pos); ++g->launches;
         LF_LAUNCHED();
         dfree(g, vals);
         dfree(g, keys);
-        k_cc_sum<<<grid_for(n, 256, 1024), 256, 0, st>>>(utri, g->deg, n, ds); ++g->launches;
+        if (g->ngraphs > 0) {
+            k_cc_sum_batch<<<grid_for(n, 256, 8192), 256, 0, st>>>(utri, g->deg, g->gid, n, g->gsacc); ++g->launches;
+        } else {
+            k_cc_sum<<<grid_for(n, 256, 1024), 256, 0, st>>>(utri, g->deg, n, ds); ++g->launches;
+        }
         LF_LAUNCHED();
+    }
+    if (g->ngraphs > 0) {
+        k_cc_final_batch<<<grid_for(g->ngraphs, 256, 1024), 256, 0, st>>>(g->gsacc, gnoff_d, g->ngraphs, g->gcc,
+                                                                          g->gcc32); ++g->launches;
+        LF_LAUNCHED();
+        g->gcc_host.assign((size_t)g->ngraphs, 0.0);
+        LF_CUDA(cudaMemcpyAsync(g->gcc_host.data(), g->gcc, (size_t)g->ngraphs * 8, cudaMemcpyDeviceToHost, st));
+        LF_CUDA(cudaStreamSynchronize(st));
+        dfree(g, gnoff_d);
     }
     k_cc_final<<<1, 32, 0, st>>>(ds, n); ++g->launches;
     LF_LAUNCHED();

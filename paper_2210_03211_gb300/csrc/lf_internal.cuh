@@ -48,7 +48,7 @@ struct __align__(16) CommRec {
     int32_t n;
     uint32_t m2;
     uint32_t vol;
-    int32_t pad;
+    int32_t gid;   // graph of the community in a batch of graphs (0 for one graph)
 };
 
 // Small device-resident scalars of one graph.
@@ -138,6 +138,26 @@ struct lf_graph {
     lf_iteration_fn it_cb = nullptr;
     void *it_ctx = nullptr;
     bool in_callback = false;
+    // a batch of independent graphs held as one disjoint union (ngraphs > 0):
+    // graph i's nodes are the dense ids [gnoff[i], gnoff[i+1]), its original
+    // ids were shifted by gbase[i]; per-graph cc, WCC-hat sums and stop tests
+    int64_t ngraphs = 0;
+    std::vector<int64_t> gnoff, gbase;
+    int32_t *gid = nullptr;                 // graph of each node
+    double *gcc = nullptr;                  // per-graph cc
+    float *gcc32 = nullptr;                 // per-graph cc rounded to float
+    unsigned long long *gsacc = nullptr;    // per-graph exact sums (SACC_CHUNKS words each)
+    double *gT = nullptr;                   // per-graph WCC-hat(P) of the last iteration end
+    double *gT_host = nullptr;              // its pinned host copy
+    std::vector<double> gcc_host;
+    std::vector<int32_t> g_iters, g_conv;   // per graph: iterations run, converged
+    std::vector<double> g_T0;
+    std::vector<std::vector<double>> g_hist;
+    // queue schedule of a batch: queue b holds qorder[sched[b] .. sched[b+1])
+    int32_t *qorder = nullptr;
+    int32_t *qpos = nullptr;                // position of every node in qorder (-1: not queued)
+    std::vector<int64_t> sched;
+    int64_t sched_version = 0, graph_sched = -1, hub_plan_sched = -1;
     lf::CommRec *comm = nullptr;  // n records (ncomm used)
     unsigned long long *stamp = nullptr;  // n words
     int32_t K = 0;                // row capacity

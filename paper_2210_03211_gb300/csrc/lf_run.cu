@@ -71,6 +71,12 @@ struct RunArgs {
     int32_t screen;    // 1: rule candidates out with the FP32 bound first
     float cc32;        // cc rounded to float (screen)
     float delta;       // relative error bound of the screen (see score32)
+    // a batch of graphs: per-graph cc (indexed by a community record's gid)
+    // and per-graph exact sums; null for one graph
+    const double *gcc;
+    const float *gcc32;
+    unsigned long long *gsacc;
+    const int32_t *gid;
     // WCC-hat total: nodes of degree > TOT_CHUNK are counted in chunks
     const int32_t *tot_hubs;
     const int32_t *tot_chunk_hub;
@@ -145,6 +151,7 @@ __global__ void k_init_rows(RunArgs a, const int32_t *comm_of, int64_t n) {
         int32_t c = comm_of[x];
         a.mem[x * a.K] = c;
         a.nmem[x] = 1;
+        if (a.gid) a.comm[c].gid = a.gid[x];   // every member is in the same graph
         atomicAdd(&a.comm[c].n, 1);
         atomicAdd(&a.comm[c].vol, (uint32_t)a.deg[x]);
     }
@@ -276,12 +283,13 @@ __device__ __forceinline__ void eval_candidate(const RunArgs &a, int32_t C, uint
     const int64_t k = (int64_t)(v & ~OWN_FLAG);
     const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
     const int64_t n = r.x, m2 = (uint32_t)r.y, vol = (uint32_t)r.z;
-    const double before = community_score(n, m2, vol, a.cc);
+    const double cc = a.gcc ? a.gcc[r.w] : a.cc;   // the community's graph
+    const double before = community_score(n, m2, vol, cc);
     if (own) {
-        double g = __dsub_rn(community_score(n - 1, m2 - 2 * k, vol - d, a.cc), before);
+        double g = __dsub_rn(community_score(n - 1, m2 - 2 * k, vol - d, cc), before);
         if (g > 0.0 && better(g, C, bl.g, bl.c)) bl = Best{g, C, (int32_t)k};
     } else {
-        double g = __dsub_rn(community_score(n + 1, m2 + 2 * k, vol + d, a.cc), before);
+        double g = __dsub_rn(community_score(n + 1, m2 + 2 * k, vol + d, cc), before);
         if (g > 0.0 && better(g, C, bj.g, bj.c)) bj = Best{g, C, (int32_t)k};
     }
 }
@@ -314,8 +322,9 @@ __device__ __forceinline__ void screen_gain_rec(const RunArgs &a, const int4 &r,
     const bool own = (v & OWN_FLAG) != 0;
     const int64_t k = (int64_t)(v & ~OWN_FLAG);
     const int64_t n = r.x, m2 = (uint32_t)r.y, vol = (uint32_t)r.z;
-    const float so = score32(n, m2, vol, a.cc32);
-    const float sn = own ? score32(n - 1, m2 - 2 * k, vol - d, a.cc32) : score32(n + 1, m2 + 2 * k, vol + d, a.cc32);
+    const float cc32 = a.gcc32 ? a.gcc32[r.w] : a.cc32;
+    const float so = score32(n, m2, vol, cc32);
+    const float sn = own ? score32(n - 1, m2 - 2 * k, vol - d, cc32) : score32(n + 1, m2 + 2 * k, vol + d, cc32);
     if (!(isfinite(sn) && isfinite(so))) {   // out of float range: keep the candidate, bound nothing
         g = 0.f;
         err = INFINITY;
@@ -2156,7 +2165,10 @@ __device__ __forceinline__ void tot_count_smem(const RunArgs &a, int64_t pb, int
 __device__ __forceinline__ void tot_member(const RunArgs &a, unsigned long long *acc, int32_t C, int64_t k,
                                            int32_t d) {
     const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
-    sacc_add(acc, wcchat_member(k, d, r.x, (uint32_t)r.y, a.cc));
+    if (a.gsacc)   // a batch: the sum of the community's graph
+        sacc_add(a.gsacc + (int64_t)r.w * SACC_CHUNKS, wcchat_member(k, d, r.x, (uint32_t)r.y, a.gcc[r.w]));
+    else
+        sacc_add(acc, wcchat_member(k, d, r.x, (uint32_t)r.y, a.cc));
 }
 
 // Memberships waiting for their FP64 term, per warp: evaluated 32 at a time so
@@ -2304,6 +2316,13 @@ __global__ void __launch_bounds__(TOT_WARPS * 32) k_total(RunArgs a, int64_t n) 
         if (acc[s]) atomicAdd(&a.ds->sacc[s], acc[s]);
 }
 
+// Per-graph totals of a batch (one thread per graph); the shared counters
+// are finalised by k_finalize as for one graph.
+__global__ void k_finalize_batch(unsigned long long *gsacc, int64_t G, double *gT) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < G; i += (int64_t)gridDim.x * blockDim.x)
+        gT[i] = sacc_round_and_clear(gsacc + i * SACC_CHUNKS);
+}
+
 __global__ void k_finalize(DevScalars *ds, Readback *rbd, int advance) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     const double T = sacc_round_and_clear(ds->sacc);
@@ -2384,6 +2403,15 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.cc32 = (float)g->cc;
     const double u64 = 1.1102230246251565e-16, u32 = 5.960464477539063e-08;
     a.delta = (float)(1.02 * (21.0 * u32 + u64 * (200.0 + 8.0 * (double)g->m) + 2.0 * u64) + 1e-9);
+    a.gcc = g->ngraphs > 0 ? g->gcc : nullptr;
+    a.gcc32 = g->ngraphs > 0 ? g->gcc32 : nullptr;
+    a.gsacc = g->ngraphs > 0 ? g->gsacc : nullptr;
+    a.gid = g->ngraphs > 0 ? g->gid : nullptr;
+    if (g->ngraphs > 0) {
+        a.order = g->qorder ? g->qorder : g->order;   // the queue schedule of the active graphs
+        a.pos = g->qpos ? g->qpos : g->pos;
+        a.screen = g->screen ? 1 : 0;                 // per graph: cc32 = 0 keeps every candidate
+    }
     a.tot_hubs = g->tot_hubs;
     a.tot_chunk_hub = g->tot_chunk_hub;
     a.tot_first = g->tot_first;
@@ -2411,6 +2439,30 @@ int num_sms() {
     LF_CUDA(cudaGetDevice(&dev));
     LF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     return std::max(1, sms);
+}
+
+// Queue b: positions [start, start + len) of the order the kernels read (the
+// batch schedule when there is one).
+void queue_bounds(const lf_graph *g, int64_t q, int64_t b, int64_t &start, int32_t &len) {
+    if (!g->sched.empty()) {
+        start = g->sched[(size_t)b];
+        len = (int32_t)(g->sched[(size_t)b + 1] - start);
+    } else {
+        start = b * q;
+        len = (int32_t)std::min<int64_t>(q, g->n - start);
+    }
+}
+
+int64_t num_queues(const lf_graph *g, int64_t q) {
+    if (!g->sched.empty()) return (int64_t)g->sched.size() - 1;
+    return g->n > 0 ? (g->n + q - 1) / q : 0;
+}
+
+int64_t max_queue(const lf_graph *g, int64_t q) {
+    if (g->sched.empty()) return q;
+    int64_t m = 1;
+    for (size_t b = 0; b + 1 < g->sched.size(); ++b) m = std::max(m, g->sched[b + 1] - g->sched[b]);
+    return m;
 }
 
 // Warps per node: as many as keep q x T warps within about 16 per SM, so that
@@ -2482,15 +2534,16 @@ void ensure_dyn(lf_graph *g, int64_t q, int64_t nb) {
 
 void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int64_t count,
                     bool capturing = false) {
-    const int T = choose_team(g, q);
-    const bool dyn = use_dyn(g, q);
+    const bool sched = !g->sched.empty();
+    const int T0 = choose_team(g, q);
+    const bool any_dyn = sched ? use_dyn(g, max_queue(g, q)) : use_dyn(g, q);
     const int64_t nhubs = g->hub_qoff_host.empty() ? 0 : g->hub_qoff_host.back();
     if (nhubs > 0 && first == 0) {
         k_hub_caps<<<grid_for(nhubs * 32, EV_THREADS, 4096), EV_THREADS, 0, g->stream>>>(a, g->hub_wcap, nhubs);
         ++g->launches;
     }
     int dyn_grid = 0, blk_grid = 0;
-    if (dyn) {
+    if (any_dyn) {
         static int per_sm = 0, per_sm_blk = 0;
         if (per_sm == 0) {
             LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_dyn, EV_THREADS, EV_DYN_SMEM));
@@ -2505,8 +2558,11 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
 
     const bool prof = g->profile && (int64_t)g->prof_ev.size() >= 2 * (first + count);
     for (int64_t b = first; b < first + count; ++b) {
-        const int64_t bstart = b * q;
-        const int32_t blen = (int32_t)std::min<int64_t>(q, g->n - bstart);
+        int64_t bstart;
+        int32_t blen;
+        queue_bounds(g, q, b, bstart, blen);
+        const int T = sched ? choose_team(g, blen) : T0;
+        const bool dyn = sched ? (blen >= DYN_MIN_Q && T == 1) : any_dyn;
         if (prof) record_event(g, g->prof_ev[2 * b], capturing);
         const int64_t nch =
             g->hub_cqoff_host.empty() ? 0 : g->hub_cqoff_host[(size_t)b + 1] - g->hub_cqoff_host[(size_t)b];
@@ -2557,6 +2613,67 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
     LF_LAUNCHED();
 }
 
+// Queue order of a batch: segments (source position in the graph-by-graph
+// order, destination, length) copied one warp each.
+__global__ void k_gather_order(const int32_t *order, const long long *seg, int64_t nseg, int32_t *qorder,
+                               int32_t *qpos) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nseg; s += warps) {
+        const long long src = seg[3 * s], dst = seg[3 * s + 1], len = seg[3 * s + 2];
+        for (long long i = lane; i < len; i += 32) {
+            const int32_t x = order[src + i];
+            qorder[dst + i] = x;
+            qpos[x] = (int32_t)(dst + i);
+        }
+    }
+}
+
+// The queues of a batch iteration: queue j holds the j-th q nodes (in node
+// order) of every active graph, graph by graph.  Graphs do not interact, so
+// each graph sees exactly the queues it would have alone.
+void build_schedule(lf_graph *g, int64_t q, const std::vector<char> &active) {
+    const int64_t G = g->ngraphs;
+    int64_t J = 0;
+    for (int64_t i = 0; i < G; ++i)
+        if (active[(size_t)i]) J = std::max(J, (g->gnoff[(size_t)i + 1] - g->gnoff[(size_t)i] + q - 1) / q);
+    std::vector<long long> seg;
+    std::vector<int64_t> sched(1, 0);
+    int64_t cur = 0;
+    for (int64_t j = 0; j < J; ++j) {
+        for (int64_t i = 0; i < G; ++i) {
+            if (!active[(size_t)i]) continue;
+            const int64_t ni = g->gnoff[(size_t)i + 1] - g->gnoff[(size_t)i];
+            const int64_t len = std::min(q, ni - j * q);
+            if (len <= 0) continue;
+            seg.push_back(g->gnoff[(size_t)i] + j * q);
+            seg.push_back(cur);
+            seg.push_back(len);
+            cur += len;
+        }
+        sched.push_back(cur);
+    }
+    if (!g->qorder) {
+        g->qorder = dalloc_n<int32_t>(g, std::max<int64_t>(g->n, 1));
+        g->qpos = dalloc_n<int32_t>(g, std::max<int64_t>(g->n, 1));
+    }
+    // nodes of stopped graphs are in no queue (position -1)
+    LF_CUDA(cudaMemsetAsync(g->qpos, 0xff, (size_t)std::max<int64_t>(g->n, 1) * 4, g->stream));
+    const int64_t nseg = (int64_t)seg.size() / 3;
+    if (nseg > 0) {
+        long long *d = dalloc_n<long long>(g, 3 * nseg);
+        LF_CUDA(cudaMemcpyAsync(d, seg.data(), (size_t)(3 * nseg) * 8, cudaMemcpyHostToDevice, g->stream));
+        k_gather_order<<<grid_for(nseg * 32, 256, 1 << 16), 256, 0, g->stream>>>(g->order, d, nseg, g->qorder,
+                                                                                   g->qpos);
+        ++g->launches;
+        LF_LAUNCHED();
+        LF_CUDA(cudaStreamSynchronize(g->stream));
+        dfree(g, d);
+    }
+    g->sched = sched;
+    ++g->sched_version;
+}
+
 // The WCC-hat total on a resident grid (work is handed out by counters).
 void launch_total(lf_graph *g, const RunArgs &a) {
     static int per_sm = 0;
@@ -2573,6 +2690,12 @@ void launch_iteration_end(lf_graph *g, const RunArgs &a) {
     k_finalize<<<1, 32, 0, g->stream>>>(g->ds, device_readback(g), 1); ++g->launches;
     LF_LAUNCHED();
     LF_CUDA(cudaMemcpyAsync(g->rb, device_readback(g), sizeof(Readback), cudaMemcpyDeviceToHost, g->stream));
+    if (g->ngraphs > 0) {
+        k_finalize_batch<<<grid_for(g->ngraphs, 256, 1024), 256, 0, g->stream>>>(g->gsacc, g->ngraphs, g->gT);
+        ++g->launches;
+        LF_LAUNCHED();
+        LF_CUDA(cudaMemcpyAsync(g->gT_host, g->gT, (size_t)g->ngraphs * 8, cudaMemcpyDeviceToHost, g->stream));
+    }
 }
 
 void ensure_capacity(lf_graph *g, int64_t q) {
@@ -2701,17 +2824,21 @@ void free_hub_plan(lf_graph *g) {
 // (d+1) K bounds the entries).  Queues run one after the other, so the
 // tables of every queue share one scratch area.
 void build_hub_plan(lf_graph *g, int64_t q) {
-    if (g->hub_plan_q == q && g->hub_plan_K == g->K) return;
+    if (g->hub_plan_q == q && g->hub_plan_K == g->K && g->hub_plan_sched == g->sched_version) return;
     free_hub_plan(g);
     g->hub_plan_q = q;
     g->hub_plan_K = g->K;
+    g->hub_plan_sched = g->sched_version;
     const int64_t n = g->n;
     if (n == 0 || g->max_deg <= HUGE_DEG) return;
-    std::vector<int32_t> order((size_t)n), deg((size_t)n);
-    LF_CUDA(cudaMemcpyAsync(order.data(), g->order, (size_t)n * 4, cudaMemcpyDeviceToHost, g->stream));
+    const int64_t len = g->sched.empty() ? n : g->sched.back();   // positions in the order the kernels read
+    std::vector<int32_t> order((size_t)std::max<int64_t>(len, 1)), deg((size_t)n);
+    if (len > 0)
+        LF_CUDA(cudaMemcpyAsync(order.data(), g->sched.empty() ? g->order : g->qorder, (size_t)len * 4,
+                                cudaMemcpyDeviceToHost, g->stream));
     LF_CUDA(cudaMemcpyAsync(deg.data(), g->deg, (size_t)n * 4, cudaMemcpyDeviceToHost, g->stream));
     LF_CUDA(cudaStreamSynchronize(g->stream));
-    const int64_t nb = (n + q - 1) / q;
+    const int64_t nb = num_queues(g, q);
     std::vector<int32_t> pos, nch, chunk_h, chunk_c;
     std::vector<int64_t> qoff((size_t)nb + 1, 0), cqoff((size_t)nb + 1, 0), toff;
     std::vector<uint32_t> tcap;
@@ -2721,7 +2848,10 @@ void build_hub_plan(lf_graph *g, int64_t q) {
         qoff[(size_t)b] = (int64_t)pos.size();
         cqoff[(size_t)b] = (int64_t)chunk_h.size();
         int64_t used = 0, items = 0;
-        for (int64_t p = b * q; p < std::min(n, (b + 1) * q); ++p) {
+        int64_t qs;
+        int32_t ql;
+        queue_bounds(g, q, b, qs, ql);
+        for (int64_t p = qs; p < qs + ql; ++p) {
             const int32_t d = deg[(size_t)order[(size_t)p]];
             if (d <= HUGE_DEG) continue;
             uint64_t cap = 32;
@@ -2896,8 +3026,30 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = g->stream;
     const int64_t n = g->n;
-    const int64_t q = std::max<int64_t>(1, std::min<int64_t>(q_in, std::max<int64_t>(n, 1)));
-    ensure_capacity(g, q);
+    const bool batch = g->ngraphs > 0;
+    if (batch && max_batches >= 0) fail(LF_ERR_INVALID, "lf_run_partial is not available for a batch of graphs");
+    int64_t q = std::max<int64_t>(1, std::min<int64_t>(q_in, std::max<int64_t>(n, 1)));
+    std::vector<char> gactive;
+    if (batch) {   // every graph with nodes starts active; queues from the schedule
+        const int64_t G = g->ngraphs;
+        int64_t nmax = 1;
+        gactive.assign((size_t)G, 0);
+        for (int64_t i = 0; i < G; ++i) {
+            const int64_t ni = g->gnoff[(size_t)i + 1] - g->gnoff[(size_t)i];
+            gactive[(size_t)i] = ni > 0;
+            nmax = std::max(nmax, ni);
+        }
+        q = std::max<int64_t>(1, std::min<int64_t>(q_in, nmax));
+        if (!g->gT_host) LF_CUDA(cudaMallocHost(&g->gT_host, (size_t)G * 8));
+        LF_CUDA(cudaMemsetAsync(g->gsacc, 0, (size_t)(G * SACC_CHUNKS) * 8, g->stream));
+        g->g_iters.assign((size_t)G, 0);
+        g->g_conv.assign((size_t)G, 0);
+        g->g_T0.assign((size_t)G, 0.0);
+        g->g_hist.assign((size_t)G, std::vector<double>());
+        g->sched.clear();
+        if (n > 0) build_schedule(g, q, gactive);
+    }
+    ensure_capacity(g, batch ? max_queue(g, q) : q);
     set_eval_attrs();
     cudaEvent_t ev[3];
     for (auto &e : ev) LF_CUDA(cudaEventCreate(&e));
@@ -3006,17 +3158,29 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     k_finalize<<<1, 32, 0, st>>>(g->ds, device_readback(g), 0); ++g->launches;
     LF_LAUNCHED();
     LF_CUDA(cudaMemcpyAsync(g->rb, device_readback(g), sizeof(Readback), cudaMemcpyDeviceToHost, st));
+    if (batch) {   // every graph's T0
+        k_finalize_batch<<<grid_for(g->ngraphs, 256, 1024), 256, 0, st>>>(g->gsacc, g->ngraphs, g->gT);
+        ++g->launches;
+        LF_LAUNCHED();
+        LF_CUDA(cudaMemcpyAsync(g->gT_host, g->gT, (size_t)g->ngraphs * 8, cudaMemcpyDeviceToHost, st));
+    }
     LF_CUDA(cudaEventRecord(ev[1], st));
     LF_CUDA(cudaStreamSynchronize(st));
     const double T0 = g->rb->total;
     int32_t maxcnt = g->rb->maxcnt;
     g->ran = true;
+    std::vector<double> gprev;
+    if (batch) {
+        gprev.assign(g->gT_host, g->gT_host + g->ngraphs);
+        g->g_T0 = gprev;
+    }
 
-    const int64_t nb = n > 0 ? (n + q - 1) / q : 0;
-    if (use_dyn(g, q)) ensure_dyn(g, q, nb);
+    int64_t nb = num_queues(g, q);
+    if (batch) ensure_dyn(g, max_queue(g, q), nb);
+    else if (use_dyn(g, q)) ensure_dyn(g, q, nb);
     // measured on GB300: the persistent loop wins for small queues (grid
     // barriers over few blocks), launches per queue for large ones
-    const bool persistent = g->per_queue == 0 || (g->per_queue < 0 && q <= 256);
+    const bool persistent = !batch && (g->per_queue == 0 || (g->per_queue < 0 && q <= 256));
     const int team = choose_team(g, q);
     const int grid_max = persistent ? persistent_grid_max(g, team) : 0;
     if (persistent) {
@@ -3043,6 +3207,14 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     double prev = T0;
     unsigned long long last_live = (unsigned long long)k0, last_memb = (unsigned long long)n;
     for (int32_t it = 1; it <= max_iters; ++it) {
+        if (batch) {   // graphs that stopped leave the queues
+            if (std::find(gactive.begin(), gactive.end(), (char)1) == gactive.end()) break;
+            if (it > 1) {
+                build_schedule(g, q, gactive);
+                nb = num_queues(g, q);
+                ensure_dyn(g, max_queue(g, q), nb);
+            }
+        }
         if (maxcnt + 1 > g->K) grow_rows(g, maxcnt + 1);
         build_hub_plan(g, q);
         build_total_plan(g);
@@ -3063,7 +3235,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             launch_persistent(g, a, q, 0, nb, grid_max, team, pev[0], pev[1]);
             launch_iteration_end(g, a);
         } else if (g->use_graphs > 0 && max_batches < 0) {
-            if (!g->iter_exec || g->graph_q != q || g->graph_K != g->K) {
+            if (!g->iter_exec || g->graph_q != q || g->graph_K != g->K || g->graph_sched != g->sched_version) {
                 drop_graph(g);
                 cudaGraph_t graph;
                 const unsigned long long before = g->launches;
@@ -3085,6 +3257,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
                 LF_CUDA(e);
                 g->graph_q = (int32_t)q;
                 g->graph_K = g->K;
+                g->graph_sched = g->sched_version;
             }
             LF_CUDA(cudaGraphLaunch(g->iter_exec, st));
             g->launches += g->graph_kernels;
@@ -3132,6 +3305,21 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             if (stats->joins_history) stats->joins_history[it - 1] = (int64_t)rb.joins;
             if (stats->leaves_history) stats->leaves_history[it - 1] = (int64_t)rb.leaves;
         }
+        if (batch) {   // each graph's own stopping test
+            for (int64_t i = 0; i < g->ngraphs; ++i) {
+                if (!gactive[(size_t)i]) continue;
+                const double Ti = g->gT_host[i], Pi = gprev[(size_t)i];
+                g->g_hist[(size_t)i].push_back(Ti);
+                g->g_iters[(size_t)i] = it;
+                const bool stop_i = Pi == 0.0 ? (Ti == 0.0) : ((Ti - Pi) / Pi) < thr;
+                gprev[(size_t)i] = Ti;
+                if (stop_i) {
+                    gactive[(size_t)i] = 0;
+                    g->g_conv[(size_t)i] = 1;
+                }
+            }
+            continue;
+        }
         const double T = rb.total;
         if (g->it_cb) {   // the caller may read the communities of this iteration
             g->in_callback = true;
@@ -3156,6 +3344,11 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     }
     LF_CUDA(cudaEventRecord(ev[2], st));
     LF_CUDA(cudaStreamSynchronize(st));
+    if (batch) {   // converged when every graph did
+        converged = 1;
+        for (int64_t i = 0; i < g->ngraphs; ++i)
+            if (g->gnoff[(size_t)i + 1] > g->gnoff[(size_t)i] && !g->g_conv[(size_t)i]) converged = 0;
+    }
     if (stats) {
         stats->iterations = iters;
         stats->converged = converged;

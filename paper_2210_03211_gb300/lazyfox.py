@@ -24,7 +24,8 @@ _STATUS = {1: "LF_ERR_INVALID", 2: "LF_ERR_OOM", 3: "LF_ERR_CUDA", 4: "LF_ERR_CA
 ABI_FUNCTIONS = ("lf_graph_create", "lf_run", "lf_run_partial", "lf_get_communities",
                  "lf_get_node_stats", "lf_get_sizes", "lf_get_create_stats", "lf_get_csr",
                  "lf_get_oriented", "lf_get_order", "lf_get_state", "lf_graph_destroy",
-                 "lf_last_error", "lf_triangles_noalloc", "lf_set_partition", "lf_set_iteration_callback")
+                 "lf_last_error", "lf_triangles_noalloc", "lf_set_partition", "lf_set_iteration_callback",
+                 "lf_batch_create", "lf_batch_get_info", "lf_batch_get_history", "lf_batch_get_communities")
 
 
 class LazyFoxError(RuntimeError):
@@ -97,6 +98,10 @@ def load_library(path: str | None = None) -> C.CDLL:
         "lf_triangles_noalloc": (C.c_int, [P, P, C.c_int64, C.c_int64, P, P, P]),
         "lf_set_partition": (C.c_int, [P, i64p, i32p, C.c_int64]),
         "lf_set_iteration_callback": (C.c_int, [P, _ITER_FN, P]),
+        "lf_batch_create": (C.c_int, [P, P, i64p, C.c_int64, C.POINTER(Options), C.POINTER(P)]),
+        "lf_batch_get_info": (C.c_int, [P, i64p, i64p, i32p, i32p, f64p, f64p, f64p]),
+        "lf_batch_get_history": (C.c_int, [P, C.c_int64, f64p, C.c_int32, i32p]),
+        "lf_batch_get_communities": (C.c_int, [P, i64p, i64p, C.c_int64, i32p, C.c_int64, i64p, i64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -170,7 +175,7 @@ class Graph:
                  warp_max_degree: int = 0, use_graphs: bool = True, profile: bool = False,
                  exhaustive_fp64: bool = False, per_queue_launches: bool | None = None,
                  barrier_timeout_ms: int = 0, inject_barrier_stall: bool = False, barrier_mode: int = 0,
-                 warps_per_node: int = 0, device=None):
+                 warps_per_node: int = 0, device=None, edge_offsets=None):
         import torch
         self._L = load_library()
         self._h = C.c_void_p()
@@ -222,7 +227,14 @@ class Graph:
             ps, pd = C.c_void_p(src.ctypes.data), C.c_void_p(dst.ctypes.data)
             keep = (src, dst)
         self._opt = opt
-        _check(self._L, self._L.lf_graph_create(ps, pd, E, C.byref(opt), C.byref(self._h)))
+        if edge_offsets is None:
+            _check(self._L, self._L.lf_graph_create(ps, pd, E, C.byref(opt), C.byref(self._h)))
+        else:   # a batch of graphs (host edge lists only)
+            if opt.edges_on_device:
+                raise TypeError("a batch takes host edge lists")
+            eo = np.ascontiguousarray(edge_offsets, dtype=np.int64)
+            _check(self._L, self._L.lf_batch_create(ps, pd, _ptr(eo, C.c_int64), eo.shape[0] - 1, C.byref(opt),
+                                                    C.byref(self._h)))
         del keep
         n, m = C.c_int64(), C.c_int64()
         _check(self._L, self._L.lf_get_sizes(self._h, C.byref(n), C.byref(m)))
@@ -387,3 +399,57 @@ def run_lazyfox(src, dst, queue_size: int, wcc_threshold: float = 0.01, max_iter
 
 def infinity_threshold() -> float:
     return -math.inf
+
+
+class Batch(Graph):
+    """Many independent graphs run together (``lf_batch_create``): every launch
+    of a run covers all of them, and each graph gets exactly the result it
+    would get alone.  ``graphs``: a list of (src, dst) int32 host arrays or of
+    objects with ``src``/``dst``.  Other keywords as for :class:`Graph`."""
+
+    def __init__(self, graphs, **kw):
+        pairs = [(g.src, g.dst) if hasattr(g, "src") else g for g in graphs]
+        sizes = np.array([len(p[0]) for p in pairs], dtype=np.int64)
+        off = np.zeros(len(pairs) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=off[1:])
+        src = np.concatenate([np.asarray(p[0], dtype=np.int32) for p in pairs]) if pairs else np.zeros(0, np.int32)
+        dst = np.concatenate([np.asarray(p[1], dtype=np.int32) for p in pairs]) if pairs else np.zeros(0, np.int32)
+        self.num_graphs = len(pairs)
+        super().__init__(src, dst, edge_offsets=off, **kw)
+
+    def info(self):
+        """Per graph: node offsets in the union, iterations, converged,
+        WCC-hat after the initial clustering and at the end, cc."""
+        G = self.num_graphs
+        ng = C.c_int64()
+        noff = np.zeros(G + 1, np.int64)
+        it = np.zeros(G, np.int32)
+        conv = np.zeros(G, np.int32)
+        t0 = np.zeros(G, np.float64)
+        tf = np.zeros(G, np.float64)
+        cc = np.zeros(G, np.float64)
+        _check(self._L, self._L.lf_batch_get_info(self._h, C.byref(ng), _ptr(noff, C.c_int64), _ptr(it, C.c_int32),
+                                                  _ptr(conv, C.c_int32), _ptr(t0, C.c_double),
+                                                  _ptr(tf, C.c_double), _ptr(cc, C.c_double)))
+        return dict(node_offsets=noff, iterations=it, converged=conv.astype(bool), wcc_initial=t0,
+                    wcc_final=tf, cc=cc)
+
+    def history(self, graph: int):
+        cnt = C.c_int32()
+        _check(self._L, self._L.lf_batch_get_history(self._h, int(graph), None, 0, C.byref(cnt)))
+        h = np.zeros(max(1, cnt.value), np.float64)
+        _check(self._L, self._L.lf_batch_get_history(self._h, int(graph), _ptr(h, C.c_double), h.shape[0],
+                                                     C.byref(cnt)))
+        return h[:cnt.value]
+
+    def graph_communities(self):
+        """For every graph, its communities as arrays of its own node ids."""
+        nc, nm = C.c_int64(), C.c_int64()
+        _check(self._L, self._L.lf_batch_get_communities(self._h, None, None, 0, None, 0, C.byref(nc), C.byref(nm)))
+        goff = np.zeros(self.num_graphs + 1, np.int64)
+        off = np.zeros(nc.value + 1, np.int64)
+        mem = np.zeros(max(1, nm.value), np.int32)
+        _check(self._L, self._L.lf_batch_get_communities(self._h, _ptr(goff, C.c_int64), _ptr(off, C.c_int64),
+                                                         off.shape[0], _ptr(mem, C.c_int32), mem.shape[0],
+                                                         C.byref(nc), C.byref(nm)))
+        return [[mem[off[c]:off[c + 1]] for c in range(goff[i], goff[i + 1])] for i in range(self.num_graphs)]

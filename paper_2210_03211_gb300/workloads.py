@@ -382,3 +382,23 @@ def hub_of_triangles(triangles: int = 10000, extra: int = 2, hub_links: int = 2,
         dst.append(1 + 3 * s.integers(0, triangles, triangles * extra))
     return EdgeList(np.concatenate(src).astype(np.int32), np.concatenate(dst).astype(np.int32),
                     f"hub_of_{triangles}_triangles")
+
+
+def batched_planted(count: int = 4096, seed: int = 5, n_lo: int = 200, n_hi: int = 20000,
+                    deg_lo: float = 8.0, deg_hi: float = 40.0) -> list:
+    """The batched workload: `count` independent planted graphs with node
+    counts log-uniform in [n_lo, n_hi] and average degree uniform in
+    [deg_lo, deg_hi], planted overlapping communities as in `planted_er`
+    (sizes 20-150, 1-3 per node, 2% background).  With 2 memberships per node
+    on average and communities of ~85 nodes, p_in = degree / 170 gives the
+    requested average degree."""
+    s = Stream(seed, 31)
+    ln = s.uniform(count) * (np.log(n_hi) - np.log(n_lo)) + np.log(n_lo)
+    ns = np.maximum(n_lo, np.round(np.exp(ln))).astype(np.int64)
+    degs = deg_lo + s.uniform(count) * (deg_hi - deg_lo)
+    out = []
+    for i in range(count):
+        n = int(ns[i])
+        out.append(planted_er(n=n, num_comms=max(2, int(round(2 * n / 85))), p_in=min(1.0, float(degs[i]) / 170.0),
+                              seed=seed * 100003 + i))
+    return out

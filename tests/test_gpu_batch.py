@@ -1,0 +1,81 @@
+"""Batches of independent graphs (lf_batch_create): one run covers all of
+them, and every graph must come out bit for bit as it does alone, against the
+oracle run on that graph alone (same totals per iteration, iterations,
+stopping, final communities)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2210_03211_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2210_03211_gb300 import build
+    build.build()
+    from paper_2210_03211_gb300 import lazyfox
+    lazyfox.load_library()
+    return lazyfox
+
+
+def mixed_graphs():
+    gs = [W.eu_core_like(seed=s) for s in range(2)]
+    gs += [W.random_graph(n=300, m=1500, seed=11, hubs=3, hub_degree=250),
+           W.random_graph(n=3000, m=9000, seed=12, hubs=2, hub_degree=2600),
+           W.from_pairs(W.path(5), "path5"),                    # no triangle: cc = 0
+           W.from_pairs(W.clique(5) + W.clique(4, 10) + [(3, 10)], "two_cliques"),
+           W.from_pairs([(7, 9)], "one_edge"),
+           W.from_pairs(W.star(40), "star40")]
+    gs += W.batched_planted(8, seed=3, n_lo=200, n_hi=3000)
+    return gs
+
+
+def check_batch(lf, oracle_lib, graphs, q, thr, max_iters):
+    with lf.Batch(graphs) as b:
+        b.run(q, thr, max_iters)
+        info = b.info()
+        comms = b.graph_communities()
+        for i, el in enumerate(graphs):
+            og = oracle_lib.OracleGraph(el.src, el.dst)
+            ref = og.run(q, thr, max_iters)
+            assert info["cc"][i] == og.cc, i
+            assert info["iterations"][i] == ref["iterations"], i
+            assert bool(info["converged"][i]) == ref["converged"], i
+            assert info["wcc_initial"][i] == ref["T0"], i
+            h = b.history(i)
+            assert np.array_equal(h, ref["T"]), i
+            assert [c.tolist() for c in comms[i]] == [c.tolist() for c in og.communities()], i
+
+
+@pytest.mark.parametrize("q", [1, 64, 256, 1 << 20])
+def test_batch_equals_each_graph_alone(lf, oracle_lib, q):
+    check_batch(lf, oracle_lib, mixed_graphs(), q, 0.01, 50)
+
+
+def test_batch_fixed_iterations(lf, oracle_lib):
+    check_batch(lf, oracle_lib, mixed_graphs(), 256, -math.inf, 4)
+
+
+def test_batch_of_the_batched_shape(lf, oracle_lib):
+    """The batched workload's shape (log-uniform sizes, degree 8-40) at 48
+    graphs of 200-5,000 nodes, queue size 256."""
+    check_batch(lf, oracle_lib, W.batched_planted(48, seed=9, n_lo=200, n_hi=5000), 256, 0.01, 50)
+
+
+def test_batch_matches_single_graph_gpu_runs(lf):
+    graphs = W.batched_planted(6, seed=4, n_lo=500, n_hi=4000)
+    with lf.Batch(graphs) as b:
+        b.run(256, 0.01, 50)
+        comms = b.graph_communities()
+        info = b.info()
+    for i, el in enumerate(graphs):
+        with lf.Graph(el.src, el.dst) as g:
+            st = g.run(256, 0.01, 50)
+            assert st.iterations == info["iterations"][i]
+            assert [c.tolist() for c in g.community_list()] == [c.tolist() for c in comms[i]]
