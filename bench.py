@@ -53,6 +53,10 @@ WORKLOADS = {
     # 3.07M nodes, Chung-Lu gamma 2.2, max degree ~33k, 20 iterations
     "large": dict(name="large_like_3.07M_nodes", gen=("large_like", {}), q=65536, q2=1024,
                   threshold=-math.inf, max_iters=20),
+    # 4,096 planted graphs, nodes log-uniform 200-20k, average degree 8-40,
+    # one batch per step against one graph per call
+    "batched": dict(name="batched_planted_graphs_200-20k_nodes_deg_8-40", gen=None, q=256, q2=0,
+                    threshold=0.01, max_iters=50),
 }
 
 
@@ -67,6 +71,9 @@ def parse_args():
     ap.add_argument("--no-secondary", action="store_true", help="skip the second queue size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs per batch (batched workload)")
+    ap.add_argument("--plain-sample", type=int, default=256,
+                    help="graphs run one per call for the plain comparison (batched workload)")
     return ap.parse_args()
 
 
@@ -207,6 +214,23 @@ def run_reference(args, spec, q):
     rank, world, _ = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
     if rank != 0:
         return 0
+    if spec["gen"] is None:   # batched: the oracle on a sample of the graphs, one after another
+        from paper_2210_03211_gb300 import workloads as W
+        graphs = W.batched_planted(min(args.batch_graphs, 32), seed=5)
+        secs = 0.0
+        for el in graphs:
+            _, dt, _ = time_oracle(el, q, spec["threshold"], spec["max_iters"])
+            secs += dt
+        value = len(graphs) / secs
+        line = {"metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": args.gpus, "steps": 1,
+                "warmup": 0, "ms_per_step": 1e3 * secs, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": spec["name"], "graphs": len(graphs), "queue_size": q},
+                "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"the first {len(graphs)} graphs of the batch, one after another"},
+                "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     el = make_workload(spec)
     for _ in range(args.warmup):
         time_oracle(el, q, spec["threshold"], spec["max_iters"])
@@ -232,12 +256,120 @@ def run_reference(args, spec, q):
     return 0
 
 
+def run_batched(args, spec, q):
+    """Graphs per second of one batch (lf_batch_create + lf_run + the
+    communities of every graph) against the same graphs one per call
+    (lf_graph_create + lf_run + lf_get_communities); latency percentiles of
+    the plain calls and of the batch (every graph of a batch finishes with it)."""
+    import numpy as np
+    import torch
+
+    from paper_2210_03211_gb300 import build as lf_build
+    from paper_2210_03211_gb300 import lazyfox
+    from paper_2210_03211_gb300 import workloads as W
+
+    rank, world, local = dist_setup(torch.cuda.is_available())
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU: the library has no CPU path")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        lf_build.build()
+    barrier(world)
+    lazyfox.load_library()
+    graphs = W.batched_planted(args.batch_graphs, seed=5 + rank)
+    G = len(graphs)
+    edges = sum(int(g.src.shape[0]) for g in graphs)
+    stream = torch.cuda.Stream(dev)
+    # the launch shape, chosen once by the library's autotuner on this batch
+    with lazyfox.Batch(graphs, stream=stream) as b:
+        tune = b.autotune(q, 1)
+    shape = dict(warps_per_node=tune["warps_per_node"], warp_max_degree=tune["warp_max_degree"])
+
+    def batch_step():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with lazyfox.Batch(graphs, stream=stream, **shape) as b:
+            b.run(q, spec["threshold"], spec["max_iters"])
+            comms = b.graph_communities()
+            it = b.info()["iterations"]
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1), comms, it
+
+    for _ in range(args.warmup):
+        batch_step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks_s = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    clocks_s.start()
+    res = [batch_step() for _ in range(args.steps)]
+    clocks = clocks_s.stop()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    local_ms = sum(r[0] for r in res)
+    total_ms = reduce_max(local_ms, world, dev)
+    value = reduce_sum(G * len(res), world, dev) / (total_ms / 1e3)
+    # plain: one graph per call, on a sample of the same graphs
+    sample = graphs[:max(1, min(args.plain_sample, G))]
+    lat = []
+    for el in sample[:2]:   # warm-up
+        with lazyfox.Graph(el.src, el.dst, stream=stream) as g:
+            g.run(q, spec["threshold"], spec["max_iters"])
+            g.communities()
+    for el in sample:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with lazyfox.Graph(el.src, el.dst, stream=stream) as g:
+            g.run(q, spec["threshold"], spec["max_iters"])
+            g.communities()
+            e1.record(stream)
+        stream.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    lat = np.array(lat)
+    plain_gps = len(lat) / (lat.sum() / 1e3)
+    # the sampled graphs' results, alone and in the batch, must agree
+    same = True
+    for i, el in enumerate(sample[:32]):
+        with lazyfox.Graph(el.src, el.dst, stream=stream) as g:
+            g.run(q, spec["threshold"], spec["max_iters"])
+            same &= [c.tolist() for c in g.community_list()] == [c.tolist() for c in res[-1][1][i]]
+    if rank == 0:
+        batch_ms = np.array([r[0] for r in res])
+        line = {
+            "metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
+            "config": {"workload": spec["name"], "graphs": G, "edges": edges, "queue_size": q,
+                       "threshold": spec["threshold"], "max_iters": spec["max_iters"],
+                       "iterations_max": int(max(res[-1][2])), "parallelism": f"replicas x{world}",
+                       "timed": "lf_batch_create (host edge lists, copied in) + lf_run + communities of every graph",
+                       "l2": "inputs (~GB) larger than L2"},
+            "autotune": tune,
+            "plain": {"graphs_per_s": plain_gps, "sample": len(lat), "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)),
+                      "timed": "lf_graph_create + lf_run + lf_get_communities, one graph per call"},
+            "batched": {"graphs_per_s": value, "p50_ms": float(np.percentile(batch_ms, 50)),
+                        "p99_ms": float(np.percentile(batch_ms, 99)), "speedup_vs_plain": value / plain_gps},
+            "results_equal_alone_and_batched": bool(same),
+            "clocks": clocks,
+            "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": int(8 * edges),
+                    "d2h_bytes_per_step": None, "note": "the batched step already starts from host edge lists"},
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     spec = WORKLOADS[args.workload]
     q = args.queue_size or spec["q"]
     if args.impl == "reference":
         return run_reference(args, spec, q)
+    if args.workload == "batched":
+        return run_batched(args, spec, q)
 
     import numpy as np
     import torch

@@ -317,6 +317,27 @@ lf_status lf_batch_get_communities(lf_graph *g, int64_t *graph_offsets, int64_t 
                                    int64_t *num_members);
 
 /*
+ * lf_autotune -- choose the launch shape of g's later runs by timing short
+ * runs: warps per evaluated node (1, 2, 4 or the automatic choice) and the
+ * degree above which a node is evaluated by a whole block instead of warps
+ * (no limit, 96 or 192).  Every candidate computes the same result (the shape
+ * changes only which threads do the work), so the choice affects speed only.
+ * queue_size: the queue size the later runs will use; trial_iters (>= 1)
+ * iterations per trial.  result (may be NULL): the chosen shape, its time and
+ * the time of the default shape.  The state of g afterwards is that of the
+ * last trial (run lf_run again for a result).
+ */
+typedef struct lf_tune_result {
+    int32_t warps_per_node;    /* 0 = automatic */
+    int32_t warp_max_degree;   /* 0 = no limit */
+    int32_t trials;
+    int32_t pad;
+    double best_ms;            /* device time of the chosen shape's trial */
+    double default_ms;         /* device time of the default shape's trial */
+} lf_tune_result;
+lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_tune_result *result);
+
+/*
  * lf_run_partial -- lf_run that stops after max_batches queues in total
  * (iteration ends run only for completed iterations), for per-queue parity
  * checks.  max_batches < 0 behaves like lf_run.

@@ -1,5 +1,6 @@
 // C ABI entry points, error plumbing, device memory, and result extraction.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -421,6 +422,73 @@ lf_status lf_set_partition(lf_graph *g, const int64_t *offsets, const int32_t *m
         g->part_mem = std::move(dense);
         g->part_k = num_communities;
         g->part_maxcnt = maxcnt;
+    });
+}
+
+lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_tune_result *result) {
+    if (!g) {
+        set_error(LF_ERR_INVALID, "graph is NULL");
+        return LF_ERR_INVALID;
+    }
+    if (g->in_callback) {
+        set_error(LF_ERR_STATE, "lf_autotune inside an iteration callback");
+        return LF_ERR_STATE;
+    }
+    if (trial_iters < 1 || queue_size < 1) {
+        set_error(LF_ERR_INVALID, "queue_size and trial_iters must be >= 1");
+        return LF_ERR_INVALID;
+    }
+    return call_guarded([&] {
+        const int32_t teams[4] = {0, 1, 2, 4};
+        const int32_t limits[3] = {0, 96, 192};
+        const int32_t keep_t = g->warps_per_node, keep_l = g->warp_max_degree;
+        lf_iteration_fn keep_cb = g->it_cb;
+        g->it_cb = nullptr;   // trials run without the caller's callback
+        double best = 0.0, dflt = 0.0;
+        int32_t bt = keep_t, bl = keep_l, trials = 0;
+        cudaEvent_t e0, e1;
+        LF_CUDA(cudaEventCreate(&e0));
+        LF_CUDA(cudaEventCreate(&e1));
+        try {
+            for (int32_t T : teams)
+                for (int32_t L : limits) {
+                    g->warps_per_node = T;
+                    g->warp_max_degree = L;
+                    LF_CUDA(cudaEventRecord(e0, g->stream));
+                    run_impl(g, queue_size, -INFINITY, trial_iters, -1, nullptr);
+                    LF_CUDA(cudaEventRecord(e1, g->stream));
+                    LF_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    LF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (T == 0 && L == 0) dflt = ms;
+                    if (trials == 0 || ms < best) {
+                        best = ms;
+                        bt = T;
+                        bl = L;
+                    }
+                    ++trials;
+                }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            g->warps_per_node = keep_t;
+            g->warp_max_degree = keep_l;
+            g->it_cb = keep_cb;
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        g->warps_per_node = bt;
+        g->warp_max_degree = bl;
+        g->it_cb = keep_cb;
+        if (result) {
+            result->warps_per_node = bt;
+            result->warp_max_degree = bl;
+            result->trials = trials;
+            result->pad = 0;
+            result->best_ms = best;
+            result->default_ms = dflt;
+        }
     });
 }
 

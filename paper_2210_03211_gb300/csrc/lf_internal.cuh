@@ -158,6 +158,7 @@ struct lf_graph {
     int32_t *qpos = nullptr;                // position of every node in qorder (-1: not queued)
     std::vector<int64_t> sched;
     int64_t sched_version = 0, graph_sched = -1, hub_plan_sched = -1;
+    int32_t graph_wpn = -1, graph_wmd = -1;   // launch shape the captured iteration was made with
     lf::CommRec *comm = nullptr;  // n records (ncomm used)
     unsigned long long *stamp = nullptr;  // n words
     int32_t K = 0;                // row capacity

@@ -3235,7 +3235,8 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             launch_persistent(g, a, q, 0, nb, grid_max, team, pev[0], pev[1]);
             launch_iteration_end(g, a);
         } else if (g->use_graphs > 0 && max_batches < 0) {
-            if (!g->iter_exec || g->graph_q != q || g->graph_K != g->K || g->graph_sched != g->sched_version) {
+            if (!g->iter_exec || g->graph_q != q || g->graph_K != g->K || g->graph_sched != g->sched_version ||
+                g->graph_wpn != g->warps_per_node || g->graph_wmd != g->warp_max_degree) {
                 drop_graph(g);
                 cudaGraph_t graph;
                 const unsigned long long before = g->launches;
@@ -3258,6 +3259,8 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
                 g->graph_q = (int32_t)q;
                 g->graph_K = g->K;
                 g->graph_sched = g->sched_version;
+                g->graph_wpn = g->warps_per_node;
+                g->graph_wmd = g->warp_max_degree;
             }
             LF_CUDA(cudaGraphLaunch(g->iter_exec, st));
             g->launches += g->graph_kernels;

@@ -25,7 +25,8 @@ ABI_FUNCTIONS = ("lf_graph_create", "lf_run", "lf_run_partial", "lf_get_communit
                  "lf_get_node_stats", "lf_get_sizes", "lf_get_create_stats", "lf_get_csr",
                  "lf_get_oriented", "lf_get_order", "lf_get_state", "lf_graph_destroy",
                  "lf_last_error", "lf_triangles_noalloc", "lf_set_partition", "lf_set_iteration_callback",
-                 "lf_batch_create", "lf_batch_get_info", "lf_batch_get_history", "lf_batch_get_communities")
+                 "lf_batch_create", "lf_batch_get_info", "lf_batch_get_history", "lf_batch_get_communities",
+                 "lf_autotune")
 
 
 class LazyFoxError(RuntimeError):
@@ -58,6 +59,11 @@ class RunStatsC(C.Structure):
                 ("leaves_history", C.POINTER(C.c_int64)), ("num_launches", C.c_int64),
                 ("prof_move_launches", C.c_int64), ("prof_move_ms", C.c_double),
                 ("prof_move_bytes", C.c_int64), ("prof_queue_us", C.c_double * 4)]
+
+
+class TuneResultC(C.Structure):
+    _fields_ = [("warps_per_node", C.c_int32), ("warp_max_degree", C.c_int32), ("trials", C.c_int32),
+                ("pad", C.c_int32), ("best_ms", C.c_double), ("default_ms", C.c_double)]
 
 
 class CreateStatsC(C.Structure):
@@ -102,6 +108,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "lf_batch_get_info": (C.c_int, [P, i64p, i64p, i32p, i32p, f64p, f64p, f64p]),
         "lf_batch_get_history": (C.c_int, [P, C.c_int64, f64p, C.c_int32, i32p]),
         "lf_batch_get_communities": (C.c_int, [P, i64p, i64p, C.c_int64, i32p, C.c_int64, i64p, i64p]),
+        "lf_autotune": (C.c_int, [P, C.c_int32, C.c_int32, C.POINTER(TuneResultC)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -259,6 +266,14 @@ class Graph:
         self.close()
 
     # -- the method -----------------------------------------------------------
+    def autotune(self, queue_size: int, trial_iters: int = 1) -> dict:
+        """Choose the launch shape of the later runs by timing short runs
+        (lf_autotune); returns the choice and the trial times."""
+        r = TuneResultC()
+        _check(self._L, self._L.lf_autotune(self._h, int(queue_size), int(trial_iters), C.byref(r)))
+        return dict(warps_per_node=r.warps_per_node, warp_max_degree=r.warp_max_degree, trials=r.trials,
+                    best_ms=r.best_ms, default_ms=r.default_ms)
+
     def set_partition(self, communities):
         """Insert a division that replaces the initial clustering of the next
         runs: a list of arrays of original node ids (may overlap), or an

@@ -53,6 +53,7 @@ def test_struct_layouts_match_header():
     # lf_options: 4 pointers + 11 int32 (+4 padding) = 80 bytes on LP64
     assert C.sizeof(lazyfox.Options) == 4 * 8 + 11 * 4 + 4
     assert C.sizeof(lazyfox.CreateStatsC) == 3 * 8 + 5 * 8 + 8 + 8
+    assert C.sizeof(lazyfox.TuneResultC) == 4 * 4 + 2 * 8
     assert C.sizeof(lazyfox.RunStatsC) == 4 + 4 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 3 * 8 + 4 * 8 + 4 * 8
 
 

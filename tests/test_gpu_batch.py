@@ -79,3 +79,19 @@ def test_batch_matches_single_graph_gpu_runs(lf):
             st = g.run(256, 0.01, 50)
             assert st.iterations == info["iterations"][i]
             assert [c.tolist() for c in g.community_list()] == [c.tolist() for c in comms[i]]
+
+
+def test_autotuned_shape_gives_the_same_result(lf):
+    """lf_autotune only changes which threads do the work: the tuned run equals
+    the default one bit for bit."""
+    graphs = W.batched_planted(12, seed=6, n_lo=300, n_hi=6000)
+    with lf.Batch(graphs) as b:
+        b.run(256, 0.01, 50)
+        ref = b.graph_communities()
+        ref_hist = [b.history(i) for i in range(len(graphs))]
+        tune = b.autotune(256, 1)
+        assert tune["trials"] == 12 and tune["best_ms"] > 0
+        b.run(256, 0.01, 50)
+        got = b.graph_communities()
+        assert all(np.array_equal(b.history(i), ref_hist[i]) for i in range(len(graphs)))
+        assert [[c.tolist() for c in gc] for gc in got] == [[c.tolist() for c in gc] for gc in ref]
