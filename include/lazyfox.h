@@ -338,6 +338,54 @@ typedef struct lf_tune_result {
 lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_tune_result *result);
 
 /*
+ * Serving -- a request loop with continuous batching (SURVEY's serving
+ * configuration; not in the paper).  Jobs (one graph each, with its queue
+ * size, threshold and iteration limit) are submitted at any time; up to
+ * max_active worker threads admit them in arrival order while the device
+ * memory estimated for the admitted jobs (from their edge counts) stays
+ * within hbm_budget_bytes (a job larger than the budget runs alone), keep each
+ * job's graph and community state resident on the device for its whole run,
+ * and run the jobs side by side on their own streams, so their iterations
+ * overlap on the device.  A job's communities are those lf_graph_create +
+ * lf_run + lf_get_communities give for it alone.
+ *   lf_server_create : opt may be NULL (defaults below).
+ *   lf_server_submit : copies the edge list; *job_id identifies the job.
+ *   lf_server_wait   : blocks until the job finished (timeout_s < 0: no limit,
+ *                      else LF_ERR_TIMEOUT when it runs out); returns the job's
+ *                      own status, with its result in *res (may be NULL).
+ *   lf_server_get_communities: as lf_get_communities, for a finished job.
+ *   lf_server_release: forgets a finished job's result.
+ *   lf_server_destroy: drops the jobs not yet admitted, waits for the running
+ *                      ones, frees everything.
+ * Times in lf_job_result are milliseconds since the server was created.
+ */
+typedef struct lf_server lf_server;
+typedef struct lf_server_options {
+    int64_t hbm_budget_bytes;   /* <= 0: half of the device memory free at creation */
+    int32_t max_active;         /* jobs resident and running at once; < 1: 4 */
+    int32_t pad;
+} lf_server_options;
+typedef struct lf_job_result {
+    int32_t status;             /* lf_status of the job */
+    int32_t iterations;
+    int32_t converged;
+    int32_t pad;
+    double wcc_initial, wcc_final;
+    int64_t num_nodes, num_edges, num_communities;
+    int64_t est_bytes;          /* device memory the admission reserved for it */
+    double t_submit_ms, t_admit_ms, t_done_ms;
+} lf_job_result;
+lf_status lf_server_create(const lf_server_options *opt, lf_server **out);
+lf_status lf_server_submit(lf_server *s, const int32_t *src, const int32_t *dst, int64_t num_edges,
+                           int32_t queue_size, double wcc_threshold, int32_t max_iters, int64_t *job_id);
+lf_status lf_server_wait(lf_server *s, int64_t job_id, double timeout_s, lf_job_result *res);
+lf_status lf_server_get_communities(lf_server *s, int64_t job_id, int64_t *offsets, int64_t offsets_cap,
+                                    int32_t *members, int64_t members_cap, int64_t *num_communities,
+                                    int64_t *num_members);
+lf_status lf_server_release(lf_server *s, int64_t job_id);
+void lf_server_destroy(lf_server *s);
+
+/*
  * lf_run_partial -- lf_run that stops after max_batches queues in total
  * (iteration ends run only for completed iterations), for per-queue parity
  * checks.  max_batches < 0 behaves like lf_run.

@@ -26,7 +26,8 @@ ABI_FUNCTIONS = ("lf_graph_create", "lf_run", "lf_run_partial", "lf_get_communit
                  "lf_get_oriented", "lf_get_order", "lf_get_state", "lf_graph_destroy",
                  "lf_last_error", "lf_triangles_noalloc", "lf_set_partition", "lf_set_iteration_callback",
                  "lf_batch_create", "lf_batch_get_info", "lf_batch_get_history", "lf_batch_get_communities",
-                 "lf_autotune")
+                 "lf_autotune", "lf_server_create", "lf_server_submit", "lf_server_wait",
+                 "lf_server_get_communities", "lf_server_release", "lf_server_destroy")
 
 
 class LazyFoxError(RuntimeError):
@@ -64,6 +65,17 @@ class RunStatsC(C.Structure):
 class TuneResultC(C.Structure):
     _fields_ = [("warps_per_node", C.c_int32), ("warp_max_degree", C.c_int32), ("trials", C.c_int32),
                 ("pad", C.c_int32), ("best_ms", C.c_double), ("default_ms", C.c_double)]
+
+
+class ServerOptionsC(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_active", C.c_int32), ("pad", C.c_int32)]
+
+
+class JobResultC(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("converged", C.c_int32), ("pad", C.c_int32),
+                ("wcc_initial", C.c_double), ("wcc_final", C.c_double), ("num_nodes", C.c_int64),
+                ("num_edges", C.c_int64), ("num_communities", C.c_int64), ("est_bytes", C.c_int64),
+                ("t_submit_ms", C.c_double), ("t_admit_ms", C.c_double), ("t_done_ms", C.c_double)]
 
 
 class CreateStatsC(C.Structure):
@@ -109,6 +121,12 @@ def load_library(path: str | None = None) -> C.CDLL:
         "lf_batch_get_history": (C.c_int, [P, C.c_int64, f64p, C.c_int32, i32p]),
         "lf_batch_get_communities": (C.c_int, [P, i64p, i64p, C.c_int64, i32p, C.c_int64, i64p, i64p]),
         "lf_autotune": (C.c_int, [P, C.c_int32, C.c_int32, C.POINTER(TuneResultC)]),
+        "lf_server_create": (C.c_int, [C.POINTER(ServerOptionsC), C.POINTER(P)]),
+        "lf_server_submit": (C.c_int, [P, P, P, C.c_int64, C.c_int32, C.c_double, C.c_int32, i64p]),
+        "lf_server_wait": (C.c_int, [P, C.c_int64, C.c_double, C.POINTER(JobResultC)]),
+        "lf_server_get_communities": (C.c_int, [P, C.c_int64, i64p, C.c_int64, i32p, C.c_int64, i64p, i64p]),
+        "lf_server_release": (C.c_int, [P, C.c_int64]),
+        "lf_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -468,3 +486,59 @@ class Batch(Graph):
                                                          off.shape[0], _ptr(mem, C.c_int32), mem.shape[0],
                                                          C.byref(nc), C.byref(nm)))
         return [[mem[off[c]:off[c + 1]] for c in range(goff[i], goff[i + 1])] for i in range(self.num_graphs)]
+
+
+class Server:
+    """Serving with continuous batching (``lf_server_*``): submit graphs at any
+    time; admitted jobs stay resident and run side by side on the device."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_active: int = 4):
+        self._L = load_library()
+        self._h = C.c_void_p()
+        opt = ServerOptionsC(int(hbm_budget_bytes), int(max_active), 0)
+        _check(self._L, self._L.lf_server_create(C.byref(opt), C.byref(self._h)))
+
+    def submit(self, src, dst, queue_size: int, wcc_threshold: float = 0.01, max_iters: int = 50) -> int:
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        jid = C.c_int64()
+        _check(self._L, self._L.lf_server_submit(self._h, C.c_void_p(src.ctypes.data), C.c_void_p(dst.ctypes.data),
+                                                 src.shape[0], int(queue_size), float(wcc_threshold),
+                                                 int(max_iters), C.byref(jid)))
+        return jid.value
+
+    def wait(self, job: int, timeout_s: float = -1.0) -> dict:
+        r = JobResultC()
+        _check(self._L, self._L.lf_server_wait(self._h, int(job), float(timeout_s), C.byref(r)))
+        return {k: getattr(r, k) for k, _ in JobResultC._fields_ if k != "pad"}
+
+    def community_list(self, job: int):
+        nc, nm = C.c_int64(), C.c_int64()
+        _check(self._L, self._L.lf_server_get_communities(self._h, int(job), None, 0, None, 0, C.byref(nc),
+                                                          C.byref(nm)))
+        off = np.zeros(nc.value + 1, np.int64)
+        mem = np.zeros(max(1, nm.value), np.int32)
+        _check(self._L, self._L.lf_server_get_communities(self._h, int(job), _ptr(off, C.c_int64), off.shape[0],
+                                                          _ptr(mem, C.c_int32), mem.shape[0], C.byref(nc),
+                                                          C.byref(nm)))
+        return [mem[off[i]:off[i + 1]] for i in range(nc.value)]
+
+    def release(self, job: int):
+        _check(self._L, self._L.lf_server_release(self._h, int(job)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.lf_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

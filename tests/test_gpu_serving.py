@@ -1,0 +1,85 @@
+"""Serving with continuous batching (lf_server_*): jobs submitted while others
+run are admitted as slots and the memory budget allow, run side by side, and
+each job's result is the one the same graph gives alone."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2210_03211_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2210_03211_gb300 import build
+    build.build()
+    from paper_2210_03211_gb300 import lazyfox
+    lazyfox.load_library()
+    return lazyfox
+
+
+def jobs():
+    gs = W.batched_planted(10, seed=13, n_lo=500, n_hi=20000)
+    gs.append(W.random_graph(n=3000, m=9000, seed=12, hubs=2, hub_degree=2600))
+    gs.append(W.dblp_like(seed=3, scale=0.03))
+    return gs
+
+
+def alone(lf, el, q, thr, it):
+    with lf.Graph(el.src, el.dst) as g:
+        g.run(q, thr, it)
+        return [c.tolist() for c in g.community_list()]
+
+
+@pytest.mark.parametrize("q", [64, 256])
+def test_results_in_the_mix_equal_alone(lf, q):
+    graphs = jobs()
+    with lf.Server(hbm_budget_bytes=8 << 30, max_active=4) as srv:
+        ids = [srv.submit(el.src, el.dst, q, 0.01, 50) for el in graphs]
+        res = [srv.wait(j) for j in ids]
+        comms = [[c.tolist() for c in srv.community_list(j)] for j in ids]
+    for el, r, c in zip(graphs, res, comms):
+        assert r["status"] == lf.LF_OK
+        assert c == alone(lf, el, q, 0.01, 50)
+    # jobs overlapped on the device: some job was admitted before another finished
+    spans = sorted((r["t_admit_ms"], r["t_done_ms"]) for r in res)
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+    assert all(r["t_submit_ms"] <= r["t_admit_ms"] <= r["t_done_ms"] for r in res)
+
+
+def test_budget_admits_one_job_at_a_time(lf):
+    graphs = jobs()[:5]
+    with lf.Server(hbm_budget_bytes=1, max_active=4) as srv:
+        ids = [srv.submit(el.src, el.dst, 256, 0.01, 50) for el in graphs]
+        res = [srv.wait(j) for j in ids]
+    spans = sorted((r["t_admit_ms"], r["t_done_ms"]) for r in res)
+    assert all(spans[i + 1][0] >= spans[i][1] for i in range(len(spans) - 1))
+
+
+def test_oracle_parity_through_the_server(lf, oracle_lib):
+    graphs = jobs()[:3]
+    with lf.Server(max_active=3) as srv:
+        ids = [srv.submit(el.src, el.dst, 16, -math.inf, 4) for el in graphs]
+        for el, j in zip(graphs, ids):
+            r = srv.wait(j)
+            og = oracle_lib.OracleGraph(el.src, el.dst)
+            ref = og.run(16, -math.inf, 4)
+            assert r["iterations"] == ref["iterations"]
+            assert r["wcc_final"] == ref["T"][-1]
+            assert [c.tolist() for c in srv.community_list(j)] == [c.tolist() for c in og.communities()]
+
+
+def test_a_failing_job_does_not_stop_the_server(lf):
+    good = jobs()[0]
+    with lf.Server(max_active=2) as srv:
+        bad = srv.submit(np.array([0, 1], np.int32), np.array([1, -5], np.int32), 16, 0.01, 5)
+        ok = srv.submit(good.src, good.dst, 16, 0.01, 5)
+        with pytest.raises(lf.LazyFoxError) as e:
+            srv.wait(bad)
+        assert e.value.status == lf.LF_ERR_INVALID
+        assert srv.wait(ok)["status"] == lf.LF_OK
