@@ -57,6 +57,9 @@ WORKLOADS = {
     # one batch per step against one graph per call
     "batched": dict(name="batched_planted_graphs_200-20k_nodes_deg_8-40", gen=None, q=256, q2=0,
                     threshold=0.01, max_iters=50),
+    # Poisson stream of planted graphs, nodes log-uniform 1k-2M, degree 10-80
+    "serving": dict(name="serving_poisson_planted_graphs_1k-2M_nodes_deg_10-80", gen=None, q=1024, q2=0,
+                    threshold=0.01, max_iters=50),
 }
 
 
@@ -72,6 +75,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs per batch (batched workload)")
+    ap.add_argument("--jobs", type=int, default=48, help="jobs of the serving stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="mean arrivals per second (serving)")
+    ap.add_argument("--max-nodes", type=int, default=200_000,
+                    help="largest job (serving; the full 1k-2M range generates ~1e9 edges on the host)")
+    ap.add_argument("--max-active", type=int, default=4, help="jobs resident at once (serving)")
     ap.add_argument("--plain-sample", type=int, default=256,
                     help="graphs run one per call for the plain comparison (batched workload)")
     return ap.parse_args()
@@ -214,9 +222,10 @@ def run_reference(args, spec, q):
     rank, world, _ = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
     if rank != 0:
         return 0
-    if spec["gen"] is None:   # batched: the oracle on a sample of the graphs, one after another
+    if spec["gen"] is None:   # batched / serving: the oracle on a sample of the graphs, one after another
         from paper_2210_03211_gb300 import workloads as W
-        graphs = W.batched_planted(min(args.batch_graphs, 32), seed=5)
+        graphs = (W.batched_planted(min(args.batch_graphs, 32), seed=5) if args.workload == "batched"
+                  else W.serving_jobs(8, seed=7, n_hi=20000)[0])
         secs = 0.0
         for el in graphs:
             _, dt, _ = time_oracle(el, q, spec["threshold"], spec["max_iters"])
@@ -362,6 +371,103 @@ def run_batched(args, spec, q):
     return 0
 
 
+def run_serving(args, spec, q):
+    """Jobs arriving as a Poisson stream through the serving loop (lf_server:
+    continuous batching, admission by memory budget, jobs side by side) against
+    the same jobs one graph per call in arrival order (first come, first
+    served on the same GPU): graphs/s over the stream and latency (arrival to
+    result) percentiles."""
+    import numpy as np
+    import torch
+
+    from paper_2210_03211_gb300 import build as lf_build
+    from paper_2210_03211_gb300 import lazyfox
+    from paper_2210_03211_gb300 import workloads as W
+
+    rank, world, local = dist_setup(torch.cuda.is_available())
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU: the library has no CPU path")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        lf_build.build()
+    barrier(world)
+    lazyfox.load_library()
+    graphs, arrivals = W.serving_jobs(args.jobs, seed=7 + rank, n_hi=args.max_nodes, rate=args.rate)
+    J = len(graphs)
+    thr, it = spec["threshold"], spec["max_iters"]
+    # warm-up: two small jobs through both paths
+    small = sorted(range(J), key=lambda i: graphs[i].src.shape[0])[:2]
+    with lazyfox.Server(max_active=args.max_active) as srv:
+        for i in small:
+            srv.wait(srv.submit(graphs[i].src, graphs[i].dst, q, thr, it))
+    for i in small:
+        with lazyfox.Graph(graphs[i].src, graphs[i].dst) as g:
+            g.run(q, thr, it)
+            g.communities()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks_s = ClockSampler("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    clocks_s.start()
+    # serving: submit at the arrival times
+    with lazyfox.Server(max_active=args.max_active) as srv:
+        t0 = time.perf_counter()
+        ids = []
+        for i in range(J):
+            wait = arrivals[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            ids.append(srv.submit(graphs[i].src, graphs[i].dst, q, thr, it))
+        res = [srv.wait(j) for j in ids]
+        served = {i: [c.tolist() for c in srv.community_list(ids[i])] for i in range(min(J, 16))}
+    clocks = clocks_s.stop()
+    lat_s = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in res])
+    span_s = (max(r["t_done_ms"] for r in res) - min(r["t_submit_ms"] for r in res)) / 1e3
+    # plain: one graph per call in arrival order; first come, first served
+    service = np.zeros(J)
+    same = True
+    for i in range(J):
+        torch.cuda.synchronize(dev)
+        a = time.perf_counter()
+        with lazyfox.Graph(graphs[i].src, graphs[i].dst) as g:
+            g.run(q, thr, it)
+            off, mem = g.communities()
+            torch.cuda.synchronize(dev)
+            service[i] = time.perf_counter() - a
+            if i in served:
+                same &= [mem[off[k]:off[k + 1]].tolist() for k in range(off.shape[0] - 1)] == served[i]
+    fin = np.zeros(J)
+    for i in range(J):
+        start = max(arrivals[i], fin[i - 1] if i else 0.0)
+        fin[i] = start + service[i]
+    lat_p = (fin - arrivals) * 1e3
+    span_p = fin[-1] - arrivals[0]
+    value = J / span_s
+    total_ms = reduce_max(span_s * 1e3, world, dev)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": reduce_sum(J, world, dev) / (total_ms / 1e3), "unit": "graphs/s",
+            "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": total_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
+            "config": {"workload": spec["name"], "jobs": J, "rate_per_s": args.rate, "max_nodes": args.max_nodes,
+                       "edges": int(sum(g.src.shape[0] for g in graphs)), "queue_size": q, "threshold": thr,
+                       "max_iters": it, "max_active": args.max_active, "parallelism": f"replicas x{world}",
+                       "timed": "first arrival to last result; each job from host edge list to host communities"},
+            "serving": {"graphs_per_s": value, "p50_ms": float(np.percentile(lat_s, 50)),
+                        "p99_ms": float(np.percentile(lat_s, 99))},
+            "plain": {"graphs_per_s": J / span_p, "p50_ms": float(np.percentile(lat_p, 50)),
+                      "p99_ms": float(np.percentile(lat_p, 99)),
+                      "timed": "one graph per call in arrival order, first come first served"},
+            "speedup_vs_plain": value / (J / span_p),
+            "results_equal_alone_and_served": bool(same),
+            "clocks": clocks,
+            "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": int(8 * sum(g.src.shape[0] for g in graphs)),
+                    "d2h_bytes_per_step": None, "note": "jobs are host edge lists in and host communities out"},
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     spec = WORKLOADS[args.workload]
@@ -370,6 +476,8 @@ def main():
         return run_reference(args, spec, q)
     if args.workload == "batched":
         return run_batched(args, spec, q)
+    if args.workload == "serving":
+        return run_serving(args, spec, q)
 
     import numpy as np
     import torch

@@ -402,3 +402,20 @@ def batched_planted(count: int = 4096, seed: int = 5, n_lo: int = 200, n_hi: int
         out.append(planted_er(n=n, num_comms=max(2, int(round(2 * n / 85))), p_in=min(1.0, float(degs[i]) / 170.0),
                               seed=seed * 100003 + i))
     return out
+
+
+def serving_jobs(count: int = 64, seed: int = 7, n_lo: int = 1000, n_hi: int = 2_000_000, deg_lo: float = 10.0,
+                 deg_hi: float = 80.0, rate: float = 200.0) -> tuple:
+    """The serving workload: `count` planted graphs with node counts
+    log-uniform in [n_lo, n_hi] and average degree uniform in [deg_lo,
+    deg_hi] (as `batched_planted`), arriving as a Poisson stream of `rate`
+    jobs per second.  Returns (graphs, arrival times in seconds from 0)."""
+    s = Stream(seed, 37)
+    ln = s.uniform(count) * (np.log(n_hi) - np.log(n_lo)) + np.log(n_lo)
+    ns = np.maximum(n_lo, np.round(np.exp(ln))).astype(np.int64)
+    degs = deg_lo + s.uniform(count) * (deg_hi - deg_lo)
+    gaps = -np.log(1.0 - s.uniform(count)) / rate
+    arrivals = np.cumsum(gaps) - gaps[0]
+    graphs = [planted_er(n=int(ns[i]), num_comms=max(2, int(round(2 * ns[i] / 85))),
+                         p_in=min(1.0, float(degs[i]) / 170.0), seed=seed * 100019 + i) for i in range(count)]
+    return graphs, arrivals
