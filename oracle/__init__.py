@@ -60,6 +60,8 @@ def lib():
             "og_get_run": (None, [_P, _I32P, _I32P, _F64P, _F64P, _I64P, _I64P, C.c_int32]),
             "og_set_check_invariants": (None, [_P, C.c_int]),
             "og_set_partition": (C.c_int, [_P, _I64P, _I32P, C.c_int64]),
+            "og_f1_pair": (C.c_double, [C.c_int64, C.c_int64, C.c_int64]),
+            "og_cover_f1": (C.c_int, [_I64P, _I32P, C.c_int64, _I64P, _I32P, C.c_int64, _F64P, _I32P]),
             "og_invariant_failures": (C.c_int, [_P]),
             "og_evaluate": (None, [_P, C.c_int32, _I32P, _I32P, _I64P, _I64P, _F64P, _F64P]),
             "og_total": (C.c_double, [_P]),
@@ -94,6 +96,32 @@ def wcchat_node(k, d, n, m, cc) -> float:
 
 def community_score(n, m, vol, cc) -> float:
     return lib().og_community_score(int(n), int(m), int(vol), float(cc))
+
+
+def _cover_csr(cover):
+    sizes = np.array([len(c) for c in cover], dtype=np.int64)
+    off = np.zeros(len(cover) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    mem = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int32) for c in cover])
+                               if len(cover) and off[-1] > 0 else np.zeros(1, dtype=np.int32))
+    return off, mem
+
+
+def cover_f1(detected, reference):
+    """F1-score of a detected cover against a reference cover (lists of id
+    arrays) and, per detected community, the index of its best reference
+    community (-1 if it shares no node with any)."""
+    oa, ma = _cover_csr(detected)
+    ob, mb = _cover_csr(reference)
+    f1 = C.c_double()
+    best = np.zeros(max(1, len(detected)), dtype=np.int32)
+    lib().og_cover_f1(_ptr(oa, C.c_int64), _ptr(ma, C.c_int32), len(detected), _ptr(ob, C.c_int64),
+                      _ptr(mb, C.c_int32), len(reference), C.byref(f1), _ptr(best, C.c_int32))
+    return f1.value, best[:len(detected)]
+
+
+def f1_pair(k: int, a: int, b: int) -> float:
+    return lib().og_f1_pair(int(k), int(a), int(b))
 
 
 class OracleGraph:

@@ -761,6 +761,69 @@ int og_run(og_graph *g, int32_t queue_size, double threshold, int32_t max_iters,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Quality: F1-score of a detected cover against a reference cover (Methods,  */
+/* Evaluation Criteria, F1-Score for Overlapping Communities): the mean over  */
+/* detected communities C' of the best F1(C', C) over reference communities;  */
+/* F1 = 2 (p r) / (p + r), p = |C ^ C'| / |C'|, r = |C ^ C'| / |C|; 0 when    */
+/* they share no node.  Communities are sets of node ids.                      */
+/* ------------------------------------------------------------------------ */
+double og_f1_pair(int64_t k, int64_t a, int64_t b)
+{
+    if (k == 0) return 0.0;
+    double p = (double)k / (double)a, r = (double)k / (double)b;
+    return 2.0 * ((p * r) / (p + r));
+}
+
+int og_cover_f1(const int64_t *off_a, const int32_t *mem_a, int64_t ka, const int64_t *off_b,
+                const int32_t *mem_b, int64_t kb, double *f1, int32_t *best)
+{
+    *f1 = 0.0;
+    if (ka <= 0) return OG_OK;
+    int64_t eb = kb > 0 ? off_b[kb] : 0;
+    /* reference memberships sorted by node: (node << 32 | community) */
+    uint64_t *pairs = (uint64_t *)malloc((size_t)(eb > 0 ? eb : 1) * sizeof(uint64_t));
+    for (int64_t c = 0; c < kb; ++c)
+        for (int64_t i = off_b[c]; i < off_b[c + 1]; ++i)
+            pairs[i] = ((uint64_t)(uint32_t)mem_b[i] << 32) | (uint64_t)c;
+    qsort(pairs, (size_t)eb, sizeof(uint64_t), cmp_u64);
+    int64_t *cnt = (int64_t *)calloc((size_t)(kb > 0 ? kb : 1), sizeof(int64_t));
+    int64_t *touched = (int64_t *)malloc((size_t)(eb > 0 ? eb : 1) * sizeof(int64_t));
+    double *terms = (double *)malloc((size_t)ka * sizeof(double));
+    for (int64_t c = 0; c < ka; ++c) {
+        int64_t nt = 0;
+        for (int64_t i = off_a[c]; i < off_a[c + 1]; ++i) {
+            uint64_t key = (uint64_t)(uint32_t)mem_a[i] << 32;
+            int64_t lo = 0, hi = eb;   /* first pair of the node */
+            while (lo < hi) {
+                int64_t mid = (lo + hi) / 2;
+                if (pairs[mid] < key) lo = mid + 1; else hi = mid;
+            }
+            for (int64_t j = lo; j < eb && (pairs[j] >> 32) == (uint64_t)(uint32_t)mem_a[i]; ++j) {
+                int64_t cb = (int64_t)(pairs[j] & 0xffffffffu);
+                if (cnt[cb]++ == 0) touched[nt++] = cb;
+            }
+        }
+        double m = 0.0;
+        int32_t arg = -1;
+        int64_t a = off_a[c + 1] - off_a[c];
+        for (int64_t t = 0; t < nt; ++t) {
+            int64_t cb = touched[t];
+            double f = og_f1_pair(cnt[cb], a, off_b[cb + 1] - off_b[cb]);
+            if (arg < 0 || f > m || (f == m && cb < arg)) {   /* ties: lowest reference index */
+                m = f;
+                arg = (int32_t)cb;
+            }
+            cnt[cb] = 0;
+        }
+        terms[c] = m;
+        if (best) best[c] = arg;
+    }
+    *f1 = og_fsum(terms, ka) / (double)ka;
+    free(pairs); free(cnt); free(touched); free(terms);
+    return OG_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Accessors for the tests.                                                  */
 /* ------------------------------------------------------------------------ */
 int og_prepare(og_graph *g)
