@@ -386,6 +386,27 @@ lf_status lf_server_release(lf_server *s, int64_t job_id);
 void lf_server_destroy(lf_server *s);
 
 /*
+ * lf_cover_f1 -- F1-score of a detected cover against a reference cover
+ * (Methods, Evaluation Criteria, F1-Score for Overlapping Communities): the
+ * mean over detected communities C' of the largest F1(C', C) over reference
+ * communities C, F1 = 2 (p r) / (p + r) with p = |C & C'| / |C'| and
+ * r = |C & C'| / |C| (0 when they share no node), rounded operation by
+ * operation in double precision; the mean is the correctly rounded sum
+ * divided by the number of detected communities (0 for none).  Not
+ * symmetric: the paper scores LazyFox's communities against Fox's or a
+ * ground truth.  Computed on the GPU.
+ * det_*, ref_*: host CSR covers (offsets num+1 entries from 0, members
+ *               node ids >= 0, no community empty, no id twice in one).
+ * best        : host, num_det entries or NULL: index of each detected
+ *               community's best reference community (lowest on ties; -1
+ *               when it shares no node with any).
+ * stream      : cudaStream_t or NULL (a stream of the call's own).
+ */
+lf_status lf_cover_f1(const int64_t *det_offsets, const int32_t *det_members, int64_t num_det,
+                      const int64_t *ref_offsets, const int32_t *ref_members, int64_t num_ref,
+                      double *f1, int32_t *best, void *stream);
+
+/*
  * lf_run_partial -- lf_run that stops after max_batches queues in total
  * (iteration ends run only for completed iterations), for per-queue parity
  * checks.  max_batches < 0 behaves like lf_run.

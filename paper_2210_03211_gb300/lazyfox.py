@@ -27,7 +27,7 @@ ABI_FUNCTIONS = ("lf_graph_create", "lf_run", "lf_run_partial", "lf_get_communit
                  "lf_last_error", "lf_triangles_noalloc", "lf_set_partition", "lf_set_iteration_callback",
                  "lf_batch_create", "lf_batch_get_info", "lf_batch_get_history", "lf_batch_get_communities",
                  "lf_autotune", "lf_server_create", "lf_server_submit", "lf_server_wait",
-                 "lf_server_get_communities", "lf_server_release", "lf_server_destroy")
+                 "lf_server_get_communities", "lf_server_release", "lf_server_destroy", "lf_cover_f1")
 
 
 class LazyFoxError(RuntimeError):
@@ -127,6 +127,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "lf_server_get_communities": (C.c_int, [P, C.c_int64, i64p, C.c_int64, i32p, C.c_int64, i64p, i64p]),
         "lf_server_release": (C.c_int, [P, C.c_int64]),
         "lf_server_destroy": (None, [P]),
+        "lf_cover_f1": (C.c_int, [i64p, i32p, C.c_int64, i64p, i32p, C.c_int64, f64p, i32p, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -542,3 +543,54 @@ class Server:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+
+def _cover_csr(cover):
+    if isinstance(cover, tuple) and len(cover) == 2 and not isinstance(cover[0], list):
+        return np.ascontiguousarray(cover[0], dtype=np.int64), np.ascontiguousarray(cover[1], dtype=np.int32)
+    sizes = np.array([len(c) for c in cover], dtype=np.int64)
+    off = np.zeros(len(cover) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    mem = (np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int32) for c in cover]))
+           if len(cover) and off[-1] > 0 else np.zeros(0, np.int32))
+    return off, mem
+
+
+def cover_f1(detected, reference, stream=None):
+    """F1-score of a detected cover against a reference cover (``lf_cover_f1``,
+    on the GPU): covers as lists of id arrays or (offsets, members).  Returns
+    (f1, best reference index per detected community)."""
+    L = load_library()
+    oa, ma = _cover_csr(detected)
+    ob, mb = _cover_csr(reference)
+    ka, kb = oa.shape[0] - 1, ob.shape[0] - 1
+    ma1 = ma if ma.shape[0] else np.zeros(1, np.int32)
+    mb1 = mb if mb.shape[0] else np.zeros(1, np.int32)
+    f = C.c_double()
+    best = np.zeros(max(1, ka), np.int32)
+    st = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(L, L.lf_cover_f1(_ptr(oa, C.c_int64), _ptr(ma1, C.c_int32), ka, _ptr(ob, C.c_int64), _ptr(mb1, C.c_int32),
+                            kb, C.byref(f), _ptr(best, C.c_int32), st))
+    return f.value, best[:ka]
+
+
+def quality_report(el, queue_sizes=(2, 4, 8, 16, 32, 64, 128, 256), threshold: float = 0.01, max_iters: int = 50):
+    """F1 of LazyFox at each queue size against Fox (queue size 1) and, when
+    the graph has one, against its planted cover; Fox against the planted
+    cover too (the comparison of the paper's quality table)."""
+    def detect(q):
+        with Graph(el.src, el.dst) as g:
+            g.run(q, threshold, max_iters)
+            return g.communities()
+    fox = detect(1)
+    planted = None
+    if getattr(el, "planted", None) is not None:
+        planted = [np.unique(np.asarray(c, dtype=np.int32)) for c in el.planted]
+        planted = [c for c in planted if c.shape[0]]
+    rows = [dict(queue_size=1, f1_vs_fox=1.0 if fox[0].shape[0] > 1 else 0.0,
+                 f1_vs_planted=cover_f1(fox, planted)[0] if planted else None)]
+    for q in queue_sizes:
+        lazy = detect(q)
+        rows.append(dict(queue_size=q, f1_vs_fox=cover_f1(lazy, fox)[0],
+                         f1_vs_planted=cover_f1(lazy, planted)[0] if planted else None))
+    return rows
