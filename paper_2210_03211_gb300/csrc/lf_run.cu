@@ -1564,12 +1564,27 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval_blocks(RunArgs a, int64_t b
     }
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the previous kernel of the stream finishes;
+// it reads only static data (node order, degrees, adjacency) before
+// pdl_wait, which returns once the previous kernel has completed and its
+// writes are visible.  pdl_trigger lets the next kernel be scheduled early.
+// Both are no-ops for a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <int T>
 __global__ void __launch_bounds__(EV_THREADS) k_eval(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx) {
     extern __shared__ int32_t ev_dyn[];   // HB keys, HB counts, HB upper and HB lower screen bounds
     __shared__ EvalShared es;
+    // the team's node and its first adjacency chunk: static, read before the wait
+    const int w = threadIdx.x >> 5;
+    NodePrefetch pf;
+    prefetch_node(a, bstart, blen, (int)(blockIdx.x * (EV_WARPS / T)) + w / T, w % T, pf);
+    pdl_trigger();
+    pdl_wait();
     eval_group<T>(a, bstart, blen, blockIdx.x * (EV_WARPS / T), queue_serial(a, bidx), ev_dyn,
-                  reinterpret_cast<uint32_t *>(ev_dyn + HB), reinterpret_cast<float *>(ev_dyn + 2 * HB), es);
+                  reinterpret_cast<uint32_t *>(ev_dyn + HB), reinterpret_cast<float *>(ev_dyn + 2 * HB), es, &pf);
 }
 
 // ---------------------------------------------------------------------------
@@ -1703,6 +1718,8 @@ __device__ __forceinline__ void flush_counts(const RunArgs &a, unsigned long lon
 }
 
 __global__ void __launch_bounds__(AP_THREADS) k_apply(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx) {
+    pdl_trigger();
+    pdl_wait();   // the queue's actions come from the kernel before
     const unsigned long long serial = queue_serial(a, bidx);
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     unsigned long long nj = 0, nl = 0;
@@ -2476,10 +2493,27 @@ int choose_team(lf_graph *g, int64_t q) {
     return T;
 }
 
+// Launch with programmatic stream serialisation (see pdl_wait).
+template <typename... P, typename... A>
+void launch_pdl(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    LF_CUDA(cudaLaunchKernelEx(&cfg, k, args...));
+}
+
 template <int T>
 void launch_eval(lf_graph *g, const RunArgs &a, int64_t bstart, int32_t blen, int64_t b) {
     constexpr int teams = EV_WARPS / T;
-    k_eval<T><<<(unsigned)((blen + teams - 1) / teams), EV_THREADS, EV_DYN_SMEM, g->stream>>>(a, bstart, blen, b);
+    launch_pdl(k_eval<T>, (unsigned)((blen + teams - 1) / teams), EV_THREADS, EV_DYN_SMEM, g->stream, a, bstart,
+               blen, b);
 }
 
 void set_eval_attrs() {
@@ -2608,7 +2642,9 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
             ++g->launches;
         }
         if (prof) record_event(g, g->prof_ev[2 * b + 1], capturing);
-        k_apply<<<grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30), AP_THREADS, 0, g->stream>>>(a, bstart, blen, b); ++g->launches;
+        launch_pdl(k_apply, grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30), AP_THREADS, 0, g->stream, a, bstart,
+                   blen, b);
+        ++g->launches;
     }
     LF_LAUNCHED();
 }
