@@ -500,6 +500,10 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize(dev)
+    # launch shape chosen once by the library's autotuner (two-iteration trials, untimed)
+    with lazyfox.Graph(src_d, dst_d, stream=stream) as g0:
+        tune = g0.autotune(q, 2)
+    shape = dict(warps_per_node=tune["warps_per_node"], warp_max_degree=tune["warp_max_degree"])
 
     def one_step(queue, profile, use_graphs=True):
         with torch.cuda.stream(stream):
@@ -507,7 +511,8 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        g = lazyfox.Graph(src_d, dst_d, stream=stream, profile=profile, use_graphs=use_graphs)
+        g = lazyfox.Graph(src_d, dst_d, stream=stream, profile=profile, use_graphs=use_graphs,
+                          **(shape if queue == q else {}))
         st = g.run(queue, spec["threshold"], spec["max_iters"])
         e1.record(stream)
         cs = g.create_stats()
@@ -591,7 +596,7 @@ def main():
         for i in range(nsteps + 1):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            g = lazyfox.Graph(src_np, dst_np)
+            g = lazyfox.Graph(src_np, dst_np, **shape)
             st = g.run(q, spec["threshold"], spec["max_iters"])
             off, mem = g.communities()
             t1 = time.perf_counter()
@@ -632,6 +637,7 @@ def main():
                 "iterations": statistics.median(r[1].ms_iterations for r in res),
                 "queue_kernels_profiled": statistics.median(r[1].prof_move_ms for r in prof)},
             "roofline": roofline,
+            "autotune": tune,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,

@@ -2458,6 +2458,14 @@ int num_sms() {
     return std::max(1, sms);
 }
 
+// Resident blocks per SM of a kernel at a launch shape (at least 1).
+template <typename K>
+int blocks_per_sm(K kernel, int threads, size_t smem) {
+    int v = 0;
+    LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem));
+    return std::max(1, v);
+}
+
 // Queue b: positions [start, start + len) of the order the kernels read (the
 // batch schedule when there is one).
 void queue_bounds(const lf_graph *g, int64_t q, int64_t b, int64_t &start, int32_t &len) {
@@ -2578,17 +2586,14 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
     }
     int dyn_grid = 0, blk_grid = 0;
     if (any_dyn) {
-        static int per_sm = 0, per_sm_blk = 0;
-        if (per_sm == 0) {
-            LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval_dyn, EV_THREADS, EV_DYN_SMEM));
-            LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_blk, k_eval_blocks, EV_THREADS,
-                                                                  EV_DYN_SMEM));
-        }
+        // computed once (function-local statics: thread-safe, as the serving workers need)
+        static const int per_sm = blocks_per_sm(k_eval_dyn, EV_THREADS, EV_DYN_SMEM);
+        static const int per_sm_blk = blocks_per_sm(k_eval_blocks, EV_THREADS, EV_DYN_SMEM);
         dyn_grid = num_sms() * std::max(1, per_sm);
         blk_grid = num_sms() * std::max(1, per_sm_blk);
         LF_CUDA(cudaMemsetAsync(g->dyn_ctr + 4 * first, 0, (size_t)(4 * count) * sizeof(uint32_t), g->stream));
-        ensure_side(g);
     }
+    if (any_dyn || nhubs > 0) ensure_side(g);
 
     const bool prof = g->profile && (int64_t)g->prof_ev.size() >= 2 * (first + count);
     for (int64_t b = first; b < first + count; ++b) {
@@ -2600,7 +2605,7 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
         if (prof) record_event(g, g->prof_ev[2 * b], capturing);
         const int64_t nch =
             g->hub_cqoff_host.empty() ? 0 : g->hub_cqoff_host[(size_t)b + 1] - g->hub_cqoff_host[(size_t)b];
-        const bool fork = dyn && nch > 0;   // hub chunks on the second stream, beside the warps
+        const bool fork = nch > 0;   // hub chunks on the second stream, beside the other evaluations
         if (fork) {
             LF_CUDA(cudaEventRecord(g->ev_fork, g->stream));
             LF_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
@@ -2640,6 +2645,7 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
             default: launch_eval<8>(g, a, bstart, blen, b); break;
             }
             ++g->launches;
+            if (fork) LF_CUDA(cudaStreamWaitEvent(g->stream, g->ev_join, 0));
         }
         if (prof) record_event(g, g->prof_ev[2 * b + 1], capturing);
         launch_pdl(k_apply, grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30), AP_THREADS, 0, g->stream, a, bstart,
@@ -2712,8 +2718,7 @@ void build_schedule(lf_graph *g, int64_t q, const std::vector<char> &active) {
 
 // The WCC-hat total on a resident grid (work is handed out by counters).
 void launch_total(lf_graph *g, const RunArgs &a) {
-    static int per_sm = 0;
-    if (per_sm == 0) LF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_total, TOT_WARPS * 32, 0));
+    static const int per_sm = blocks_per_sm(k_total, TOT_WARPS * 32, 0);
     LF_CUDA(cudaMemsetAsync(g->tot_next, 0, 2 * sizeof(uint32_t), g->stream));
     k_total<<<num_sms() * std::max(1, per_sm), TOT_WARPS * 32, 0, g->stream>>>(a, g->n);
     ++g->launches;
