@@ -272,8 +272,8 @@ lf_status lf_set_iteration_callback(lf_graph *g, lf_iteration_fn cb, void *ctx);
 
 /*
  * lf_batch_create -- many independent graphs in one handle, run together:
- * every kernel launch of lf_run covers all of them (SURVEY's batched
- * configuration; the paper runs one graph at a time).  Graph i is the edge
+ * every kernel launch of lf_run covers all of them (the paper runs one
+ * graph at a time).  Graph i is the edge
  * list src/dst[edge_offsets[i] .. edge_offsets[i+1]) with its own ids (>= 0);
  * each graph is treated exactly as lf_graph_create + lf_run would treat it
  * alone: its own node order, global clustering coefficient cc, initial
@@ -338,8 +338,7 @@ typedef struct lf_tune_result {
 lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_tune_result *result);
 
 /*
- * Serving -- a request loop with continuous batching (SURVEY's serving
- * configuration; not in the paper).  Jobs (one graph each, with its queue
+ * Serving -- a request loop with continuous batching (not in the paper).  Jobs (one graph each, with its queue
  * size, threshold and iteration limit) are submitted at any time; up to
  * max_active worker threads admit them in arrival order while the device
  * memory estimated for the admitted jobs (from their edge counts) stays

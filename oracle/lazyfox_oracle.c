@@ -14,8 +14,7 @@
  * that no multiply-add is fused (the CUDA path evaluates the same expressions
  * with explicitly rounded operations, so the two agree bit for bit).
  *
- * Readings of passages the paper leaves open (each one is listed in
- * the design doc with its reason):
+ * Readings of passages the paper leaves open:
  *   - self-loops are dropped; nodes are the endpoints of the remaining edges
  *     (Preprocessing, "Remove Multi-Edges" / "Dense Node Labels");
  *   - node order: clustering coefficient descending compared as exact

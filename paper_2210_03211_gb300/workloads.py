@@ -14,7 +14,7 @@ splitmix64 stream (Steele, Lea and Flood, "Fast splittable pseudorandom number
 generators", OOPSLA 2014), written out below with numpy uint64 arithmetic, so
 the same seed gives the same graph on any machine and numpy version.
 
-Workloads (the recipes are restated in the design doc):
+Workloads:
 
 * ``planted_er``   -- 1,000 nodes, 20 planted overlapping communities of sizes
   20-150, each node in 1-3 of them, intra-community edge probability 0.15,
