@@ -293,7 +293,8 @@ def run_batched(args, spec, q):
     # the launch shape, chosen once by the library's autotuner on this batch
     with lazyfox.Batch(graphs, stream=stream) as b:
         tune = b.autotune(q, 1)
-    shape = dict(warps_per_node=tune["warps_per_node"], warp_max_degree=tune["warp_max_degree"])
+    shape = dict(warps_per_node=tune["warps_per_node"], warp_max_degree=tune["warp_max_degree"],
+                 hub_degree=tune["hub_degree"])
 
     def batch_step():
         e0 = torch.cuda.Event(enable_timing=True)
@@ -503,7 +504,8 @@ def main():
     # launch shape chosen once by the library's autotuner (two-iteration trials, untimed)
     with lazyfox.Graph(src_d, dst_d, stream=stream) as g0:
         tune = g0.autotune(q, 2)
-    shape = dict(warps_per_node=tune["warps_per_node"], warp_max_degree=tune["warp_max_degree"])
+    shape = dict(warps_per_node=tune["warps_per_node"], warp_max_degree=tune["warp_max_degree"],
+                 hub_degree=tune["hub_degree"])
 
     def one_step(queue, profile, use_graphs=True):
         with torch.cuda.stream(stream):

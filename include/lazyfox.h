@@ -83,6 +83,9 @@ typedef struct lf_options {
                                 publishes one release flag */
     int32_t warps_per_node;  /* warps that evaluate one node together: 1, 2, 4 or 8; 0 (default)
                                 picks by queue size (more warps per node for small queues) */
+    int32_t hub_degree;      /* nodes of higher degree are evaluated with a table in global
+                                memory, in blocks of their own (per-queue launches: on a second
+                                stream); 0 (default) = 384 */
 } lf_options;
 
 /* Per-run statistics.  The history pointers are optional caller buffers with
@@ -320,7 +323,8 @@ lf_status lf_batch_get_communities(lf_graph *g, int64_t *graph_offsets, int64_t 
  * lf_autotune -- choose the launch shape of g's later runs by timing short
  * runs: warps per evaluated node (1, 2, 4 or the automatic choice) and the
  * degree above which a node is evaluated by a whole block instead of warps
- * (no limit, 96 or 192).  Every candidate computes the same result (the shape
+ * (no limit, 96 or 192) and the degree above which it takes the hub path
+ * (384 or 128).  Every candidate computes the same result (the shape
  * changes only which threads do the work), so the choice affects speed only.
  * queue_size: the queue size the later runs will use; trial_iters (>= 1)
  * iterations per trial.  result (may be NULL): the chosen shape, its time and
@@ -331,7 +335,7 @@ typedef struct lf_tune_result {
     int32_t warps_per_node;    /* 0 = automatic */
     int32_t warp_max_degree;   /* 0 = no limit */
     int32_t trials;
-    int32_t pad;
+    int32_t hub_degree;        /* degree above which a node takes the hub path */
     double best_ms;            /* device time of the chosen shape's trial */
     double default_ms;         /* device time of the default shape's trial */
 } lf_tune_result;

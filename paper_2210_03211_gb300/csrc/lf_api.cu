@@ -186,6 +186,7 @@ lf_status create_handle(const int32_t *src, const int32_t *dst, int64_t num_edge
             g->inject_stall = opt->inject_barrier_stall == 1 ? 1 : 0;
             g->barrier_mode = opt->barrier_mode == 1 ? 1 : 0;
             g->warps_per_node = opt->warps_per_node;
+            if (opt->hub_degree > 0) g->hub_degree = opt->hub_degree;
             if ((g->alloc_cb == nullptr) != (g->free_cb == nullptr))
                 fail(LF_ERR_INVALID, "alloc and free callbacks must be set together");
         }
@@ -441,30 +442,34 @@ lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_t
     return call_guarded([&] {
         const int32_t teams[4] = {0, 1, 2, 4};
         const int32_t limits[3] = {0, 96, 192};
-        const int32_t keep_t = g->warps_per_node, keep_l = g->warp_max_degree;
+        const int32_t hubs[2] = {384, 128};
+        const int32_t keep_t = g->warps_per_node, keep_l = g->warp_max_degree, keep_h = g->hub_degree;
         lf_iteration_fn keep_cb = g->it_cb;
         g->it_cb = nullptr;   // trials run without the caller's callback
         double best = 0.0, dflt = 0.0;
-        int32_t bt = keep_t, bl = keep_l, trials = 0;
+        int32_t bt = keep_t, bl = keep_l, bh = keep_h, trials = 0;
         cudaEvent_t e0, e1;
         LF_CUDA(cudaEventCreate(&e0));
         LF_CUDA(cudaEventCreate(&e1));
         try {
+            for (int32_t H : hubs)
             for (int32_t T : teams)
                 for (int32_t L : limits) {
                     g->warps_per_node = T;
                     g->warp_max_degree = L;
+                    g->hub_degree = H;
                     LF_CUDA(cudaEventRecord(e0, g->stream));
                     run_impl(g, queue_size, -INFINITY, trial_iters, -1, nullptr);
                     LF_CUDA(cudaEventRecord(e1, g->stream));
                     LF_CUDA(cudaEventSynchronize(e1));
                     float ms = 0.f;
                     LF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                    if (T == 0 && L == 0) dflt = ms;
+                    if (T == 0 && L == 0 && H == 384) dflt = ms;
                     if (trials == 0 || ms < best) {
                         best = ms;
                         bt = T;
                         bl = L;
+                        bh = H;
                     }
                     ++trials;
                 }
@@ -473,6 +478,7 @@ lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_t
             cudaEventDestroy(e1);
             g->warps_per_node = keep_t;
             g->warp_max_degree = keep_l;
+            g->hub_degree = keep_h;
             g->it_cb = keep_cb;
             throw;
         }
@@ -480,12 +486,13 @@ lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_t
         cudaEventDestroy(e1);
         g->warps_per_node = bt;
         g->warp_max_degree = bl;
+        g->hub_degree = bh;
         g->it_cb = keep_cb;
         if (result) {
             result->warps_per_node = bt;
             result->warp_max_degree = bl;
             result->trials = trials;
-            result->pad = 0;
+            result->hub_degree = bh;
             result->best_ms = best;
             result->default_ms = dflt;
         }

@@ -105,6 +105,7 @@ struct lf_graph {
     int32_t inject_stall = 0;
     int32_t barrier_mode = 0;                      // grid barrier: 0 flat flags, 1 central release flag
     int32_t warps_per_node = 0;                    // team size of the move evaluation (0: by queue size)
+    int32_t hub_degree = 384;                      // above it a node takes the hub path
     unsigned long long launches = 0;               // kernels launched (host count)
     std::vector<std::pair<void *, size_t>> live;   // outstanding allocations
 
@@ -158,7 +159,7 @@ struct lf_graph {
     int32_t *qpos = nullptr;                // position of every node in qorder (-1: not queued)
     std::vector<int64_t> sched;
     int64_t sched_version = 0, graph_sched = -1, hub_plan_sched = -1;
-    int32_t graph_wpn = -1, graph_wmd = -1;   // launch shape the captured iteration was made with
+    int32_t graph_wpn = -1, graph_wmd = -1, graph_hdeg = -1;   // launch shape of the captured iteration
     lf::CommRec *comm = nullptr;  // n records (ncomm used)
     unsigned long long *stamp = nullptr;  // n words
     int32_t K = 0;                // row capacity
@@ -204,6 +205,7 @@ struct lf_graph {
     std::vector<int64_t> hub_cqoff_host;
     int64_t hub_plan_q = 0;
     int32_t hub_plan_K = 0;
+    int32_t hub_plan_deg = 0;
     // nodes of degree > TOT_CHUNK in the WCC-hat total, counted in chunks of
     // neighbours (plan for row capacity tot_plan_K)
     int32_t *tot_hubs = nullptr;        // node ids, degree descending

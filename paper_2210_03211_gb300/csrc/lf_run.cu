@@ -21,7 +21,6 @@ constexpr int EV_THREADS = EV_WARPS * 32;
 constexpr int HW = 512;              // hash slots of one warp
 constexpr int HB = EV_WARPS * HW;    // hash slots of a block (hub nodes)
 constexpr int AP_THREADS = 256;
-constexpr int32_t HUGE_DEG = 384;   // nodes above this degree get a global-memory table
 constexpr size_t EV_DYN_SMEM = (size_t)HB * 16;   // keys, counts, upper and lower screen bounds
 
 struct RunArgs {
@@ -2389,7 +2388,7 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.warp_max_deg = g->warp_max_degree > 0 ? g->warp_max_degree : 0x7fffffff;
     a.profile = g->profile;
     a.qtimes = g->qtimes;
-    a.huge_deg = g->hub_qoff ? HUGE_DEG : 0x7fffffff;
+    a.huge_deg = g->hub_qoff ? g->hub_degree : 0x7fffffff;
     a.hub_pos = g->hub_pos;
     a.hub_qoff = g->hub_qoff;
     a.hub_toff = g->hub_toff;
@@ -2860,18 +2859,21 @@ void free_hub_plan(lf_graph *g) {
     g->hub_plan_K = 0;
 }
 
-// Static per-run plan of the hubs (degree > HUGE_DEG): their positions per
+// Static per-run plan of the hubs (degree > hub_degree): their positions per
 // queue and a table of pow2 >= 2 (d+1) K slots each (K bounds every row, so
 // (d+1) K bounds the entries).  Queues run one after the other, so the
 // tables of every queue share one scratch area.
 void build_hub_plan(lf_graph *g, int64_t q) {
-    if (g->hub_plan_q == q && g->hub_plan_K == g->K && g->hub_plan_sched == g->sched_version) return;
+    if (g->hub_plan_q == q && g->hub_plan_K == g->K && g->hub_plan_sched == g->sched_version &&
+        g->hub_plan_deg == g->hub_degree)
+        return;
     free_hub_plan(g);
     g->hub_plan_q = q;
     g->hub_plan_K = g->K;
+    g->hub_plan_deg = g->hub_degree;
     g->hub_plan_sched = g->sched_version;
     const int64_t n = g->n;
-    if (n == 0 || g->max_deg <= HUGE_DEG) return;
+    if (n == 0 || g->max_deg <= g->hub_degree) return;
     const int64_t len = g->sched.empty() ? n : g->sched.back();   // positions in the order the kernels read
     std::vector<int32_t> order((size_t)std::max<int64_t>(len, 1)), deg((size_t)n);
     if (len > 0)
@@ -2894,7 +2896,7 @@ void build_hub_plan(lf_graph *g, int64_t q) {
         queue_bounds(g, q, b, qs, ql);
         for (int64_t p = qs; p < qs + ql; ++p) {
             const int32_t d = deg[(size_t)order[(size_t)p]];
-            if (d <= HUGE_DEG) continue;
+            if (d <= g->hub_degree) continue;
             uint64_t cap = 32;
             while (cap < 2ull * (uint64_t)(d + 1) * (uint64_t)g->K) cap <<= 1;
             const int32_t c = (d + HUGE_CHUNK - 1) / HUGE_CHUNK;
@@ -3277,7 +3279,8 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             launch_iteration_end(g, a);
         } else if (g->use_graphs > 0 && max_batches < 0) {
             if (!g->iter_exec || g->graph_q != q || g->graph_K != g->K || g->graph_sched != g->sched_version ||
-                g->graph_wpn != g->warps_per_node || g->graph_wmd != g->warp_max_degree) {
+                g->graph_wpn != g->warps_per_node || g->graph_wmd != g->warp_max_degree ||
+                g->graph_hdeg != g->hub_degree) {
                 drop_graph(g);
                 cudaGraph_t graph;
                 const unsigned long long before = g->launches;
@@ -3302,6 +3305,7 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
                 g->graph_sched = g->sched_version;
                 g->graph_wpn = g->warps_per_node;
                 g->graph_wmd = g->warp_max_degree;
+                g->graph_hdeg = g->hub_degree;
             }
             LF_CUDA(cudaGraphLaunch(g->iter_exec, st));
             g->launches += g->graph_kernels;

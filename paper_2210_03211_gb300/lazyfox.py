@@ -48,7 +48,7 @@ class Options(C.Structure):
                 ("use_graphs", C.c_int32), ("profile", C.c_int32), ("exhaustive_fp64", C.c_int32),
                 ("per_queue_launches", C.c_int32), ("barrier_timeout_ms", C.c_int32),
                 ("inject_barrier_stall", C.c_int32), ("barrier_mode", C.c_int32),
-                ("warps_per_node", C.c_int32)]
+                ("warps_per_node", C.c_int32), ("hub_degree", C.c_int32)]
 
 
 class RunStatsC(C.Structure):
@@ -64,7 +64,7 @@ class RunStatsC(C.Structure):
 
 class TuneResultC(C.Structure):
     _fields_ = [("warps_per_node", C.c_int32), ("warp_max_degree", C.c_int32), ("trials", C.c_int32),
-                ("pad", C.c_int32), ("best_ms", C.c_double), ("default_ms", C.c_double)]
+                ("hub_degree", C.c_int32), ("best_ms", C.c_double), ("default_ms", C.c_double)]
 
 
 class ServerOptionsC(C.Structure):
@@ -201,7 +201,7 @@ class Graph:
                  warp_max_degree: int = 0, use_graphs: bool = True, profile: bool = False,
                  exhaustive_fp64: bool = False, per_queue_launches: bool | None = None,
                  barrier_timeout_ms: int = 0, inject_barrier_stall: bool = False, barrier_mode: int = 0,
-                 warps_per_node: int = 0, device=None, edge_offsets=None):
+                 warps_per_node: int = 0, hub_degree: int = 0, device=None, edge_offsets=None):
         import torch
         self._L = load_library()
         self._h = C.c_void_p()
@@ -234,6 +234,7 @@ class Graph:
         opt.inject_barrier_stall = 1 if inject_barrier_stall else 0
         opt.barrier_mode = int(barrier_mode)
         opt.warps_per_node = int(warps_per_node)
+        opt.hub_degree = int(hub_degree)
         if isinstance(src, torch.Tensor):
             if src.dtype != torch.int32 or dst.dtype != torch.int32 or not src.is_cuda:
                 raise TypeError("device edge lists must be int32 CUDA tensors")
@@ -290,7 +291,8 @@ class Graph:
         (lf_autotune); returns the choice and the trial times."""
         r = TuneResultC()
         _check(self._L, self._L.lf_autotune(self._h, int(queue_size), int(trial_iters), C.byref(r)))
-        return dict(warps_per_node=r.warps_per_node, warp_max_degree=r.warp_max_degree, trials=r.trials,
+        return dict(warps_per_node=r.warps_per_node, warp_max_degree=r.warp_max_degree,
+                    hub_degree=r.hub_degree, trials=r.trials,
                     best_ms=r.best_ms, default_ms=r.default_ms)
 
     def set_partition(self, communities):

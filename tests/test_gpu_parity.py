@@ -386,3 +386,15 @@ def test_large_full_size_sampled(lf, oracle_lib):
         s = g.state()
         n_c, m_c, vol_c = _recount(off, adj, s)
         assert np.array_equal(n_c, s["n"]) and np.array_equal(m_c, s["m"]) and np.array_equal(vol_c, s["vol"])
+
+
+@pytest.mark.parametrize("hub_degree,q", [(64, 1024), (64, 4096), (128, 65536)])
+def test_hub_degree_threshold_gives_the_same_run(lf, oracle_lib, hub_degree, q):
+    """Many more nodes on the hub path (global tables, second stream): the
+    run is the oracle's, bit for bit."""
+    el = W.large_like(scale=0.02)
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(q, -math.inf, 5)
+    with lf.Graph(el.src, el.dst, hub_degree=hub_degree) as g:
+        compare_run(g.run(q, -math.inf, 5), ref)
+        compare_state(g, og)
