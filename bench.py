@@ -372,6 +372,18 @@ def run_batched(args, spec, q):
     return 0
 
 
+def fifo_finish(arrivals, service):
+    """Finish times of jobs served one at a time in arrival order (first
+    come, first served): each starts at its arrival or when the previous one
+    finishes, whichever is later."""
+    import numpy as np
+    fin = np.zeros(len(arrivals))
+    for i in range(len(arrivals)):
+        start = max(arrivals[i], fin[i - 1] if i else 0.0)
+        fin[i] = start + service[i]
+    return fin
+
+
 def run_serving(args, spec, q):
     """Jobs arriving as a Poisson stream through the serving loop (lf_server:
     continuous batching, admission by memory budget, jobs side by side) against
@@ -437,10 +449,7 @@ def run_serving(args, spec, q):
             service[i] = time.perf_counter() - a
             if i in served:
                 same &= [mem[off[k]:off[k + 1]].tolist() for k in range(off.shape[0] - 1)] == served[i]
-    fin = np.zeros(J)
-    for i in range(J):
-        start = max(arrivals[i], fin[i - 1] if i else 0.0)
-        fin[i] = start + service[i]
+    fin = fifo_finish(arrivals, service)
     lat_p = (fin - arrivals) * 1e3
     span_p = fin[-1] - arrivals[0]
     value = J / span_s

@@ -51,3 +51,11 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = type("A", (), dict(steps=1, warmup=0, gpus=2))()
     assert bench.run_reference(args, bench.WORKLOADS["eu"], 1) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_fifo_finish_times():
+    """One server, arrival order: a job waits for the previous one."""
+    import numpy as np
+    import bench
+    fin = bench.fifo_finish(np.array([0.0, 0.5, 0.6, 5.0]), np.array([1.0, 1.0, 0.5, 0.25]))
+    assert np.allclose(fin, [1.0, 2.0, 2.5, 5.25])
