@@ -675,6 +675,48 @@ __device__ void decide_node(const RunArgs &a, int i, int32_t d, int32_t cx, uint
     team_sync<T>(tm);
 }
 
+// Histogram of one warp step: the (neighbour, membership) pairs of the
+// warp's 32 neighbours laid end to end and taken 32 per round, so rounds
+// follow the pairs' count rather than the longest row.  A lane finds its
+// pair's neighbour by a binary search over the warp's prefix sums
+// (shuffles), takes the community from that neighbour's row head in
+// registers (or from memory past eight), and equal ids of a round are merged
+// with __match_any_sync before one insert.
+__device__ __forceinline__ void fill_flat(const RunArgs &a, int32_t *keys, uint32_t *vals, uint32_t hm, int32_t y,
+                                          int32_t cy, const int4 &r0, const int4 &r1) {
+    const int lane = threadIdx.x & 31;
+    int incl = cy;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int tot = __shfl_sync(FULL, incl, 31);
+    const int excl = incl - cy;
+    for (int e0 = 0; e0 < tot; e0 += 32) {
+        const int e = e0 + lane;
+        int j = 0;   // last lane whose pairs start at or before e
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int ex = __shfl_sync(FULL, excl, j + step);
+            if (ex <= e) j += step;
+        }
+        const int k = e - __shfl_sync(FULL, excl, j);
+        const int32_t v0 = __shfl_sync(FULL, r0.x, j), v1 = __shfl_sync(FULL, r0.y, j);
+        const int32_t v2 = __shfl_sync(FULL, r0.z, j), v3 = __shfl_sync(FULL, r0.w, j);
+        const int32_t v4 = __shfl_sync(FULL, r1.x, j), v5 = __shfl_sync(FULL, r1.y, j);
+        const int32_t v6 = __shfl_sync(FULL, r1.z, j), v7 = __shfl_sync(FULL, r1.w, j);
+        const int32_t yj = __shfl_sync(FULL, y, j);
+        int32_t C = -2 - lane;
+        if (e < tot) {
+            C = k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : k == 3 ? v3 : k == 4 ? v4 : k == 5 ? v5 : k == 6 ? v6 : v7;
+            if (k >= 8) C = __ldcg(&a.mem[(int64_t)yj * a.K + k]);
+        }
+        const unsigned mask = __match_any_sync(FULL, C);
+        if (C >= 0 && lane == __ffs(mask) - 1) ht_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false);
+    }
+}
+
 template <int T>
 __device__ void eval_team(const RunArgs &a, int i, int32_t x, int32_t d, int64_t beg, int64_t end, int64_t bound,
                           int32_t y0, int32_t c0, int32_t *keys, uint32_t *vals, float *ubs, int32_t *bkey,
@@ -708,15 +750,10 @@ __device__ void eval_team(const RunArgs &a, int i, int32_t x, int32_t d, int64_t
             cy = __ldcg(&a.nmem[y]);
         }
         if (p < end) pb += 8ull + 4ull * (unsigned long long)cy;
-        const int32_t cmax = __reduce_max_sync(FULL, cy);
         const int32_t *rowy = a.mem + (int64_t)y * a.K;
         int4 r0, r1;
         row_head(rowy, cy, r0, r1);
-        for (int s = 0; s < cmax; ++s) {
-            int32_t C = s < cy ? row_entry(r0, r1, rowy, s) : -2 - lane;
-            unsigned mask = __match_any_sync(FULL, C);
-            if (C >= 0 && lane == __ffs(mask) - 1) ht_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false);
-        }
+        fill_flat(a, keys, vals, hm, y, cy, r0, r1);
     }
     team_sync<T>(tm);
     Best bj, bl;
