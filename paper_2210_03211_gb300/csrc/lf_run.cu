@@ -682,8 +682,11 @@ __device__ void decide_node(const RunArgs &a, int i, int32_t d, int32_t cx, uint
 // (shuffles), takes the community from that neighbour's row head in
 // registers (or from memory past eight), and equal ids of a round are merged
 // with __match_any_sync before one insert.
-__device__ __forceinline__ void fill_flat(const RunArgs &a, int32_t *keys, uint32_t *vals, uint32_t hm, int32_t y,
-                                          int32_t cy, const int4 &r0, const int4 &r1) {
+// keep(C): whether this pass counts C; insert(C, count): count C (one lane per
+// distinct C of a round).
+template <typename Keep, typename Insert>
+__device__ __forceinline__ void fill_flat_with(const RunArgs &a, int32_t y, int32_t cy, const int4 &r0, const int4 &r1,
+                                               Keep keep, Insert insert) {
     const int lane = threadIdx.x & 31;
     int incl = cy;
 #pragma unroll
@@ -711,10 +714,17 @@ __device__ __forceinline__ void fill_flat(const RunArgs &a, int32_t *keys, uint3
         if (e < tot) {
             C = k == 0 ? v0 : k == 1 ? v1 : k == 2 ? v2 : k == 3 ? v3 : k == 4 ? v4 : k == 5 ? v5 : k == 6 ? v6 : v7;
             if (k >= 8) C = __ldcg(&a.mem[(int64_t)yj * a.K + k]);
+            if (!keep(C)) C = -2 - lane;
         }
         const unsigned mask = __match_any_sync(FULL, C);
-        if (C >= 0 && lane == __ffs(mask) - 1) ht_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false);
+        if (C >= 0 && lane == __ffs(mask) - 1) insert(C, (uint32_t)__popc(mask));
     }
+}
+
+__device__ __forceinline__ void fill_flat(const RunArgs &a, int32_t *keys, uint32_t *vals, uint32_t hm, int32_t y,
+                                          int32_t cy, const int4 &r0, const int4 &r1) {
+    fill_flat_with(a, y, cy, r0, r1, [](int32_t) { return true; },
+                   [&](int32_t C, uint32_t c) { ht_insert(keys, vals, hm, C, c, false); });
 }
 
 template <int T>
@@ -820,18 +830,14 @@ __device__ void eval_block(const RunArgs &a, int i, int32_t x, int64_t bound, in
                     cy = __ldcg(&a.nmem[y]);
                     if (part == 0) pb += 8ull + 4ull * (unsigned long long)cy;
                 }
-                const int32_t cmax = __reduce_max_sync(FULL, cy);
                 const int32_t *rowy = a.mem + (int64_t)y * a.K;
                 int4 r0, r1;
                 row_head(rowy, cy, r0, r1);
-                for (int s = 0; s < cmax; ++s) {
-                    int32_t C = s < cy ? row_entry(r0, r1, rowy, s) : -1;
-                    if (C >= 0 && P > 1 && part_of(C, P) != (uint32_t)part) C = -1;
-                    if (C < 0) C = -2 - lane;
-                    unsigned mask = __match_any_sync(FULL, C);
-                    if (C >= 0 && lane == __ffs(mask) - 1)
-                        if (!ht_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false)) bs.overflow = 1;
-                }
+                fill_flat_with(
+                    a, y, cy, r0, r1, [&](int32_t C) { return P == 1 || part_of(C, P) == (uint32_t)part; },
+                    [&](int32_t C, uint32_t c) {
+                        if (!ht_insert(keys, vals, hm, C, c, false)) bs.overflow = 1;
+                    });
             }
             __syncthreads();
             if (bs.overflow) {
@@ -1299,18 +1305,13 @@ __global__ void __launch_bounds__(EV_THREADS) k_huge_chunks(RunArgs a, int64_t b
     for (int r = 0; r < HUGE_ROUNDS; ++r) {
         const int32_t y = ys[r], cy = cys[r];
         if (beg + r * EV_THREADS + w * 32 + lane < end) pb += 8ull + 4ull * (unsigned long long)cy;
-        const int32_t cmax = __reduce_max_sync(FULL, cy);
         const int32_t *rowy = a.mem + (int64_t)y * a.K;
         int4 r0, r1;
         row_head(rowy, cy, r0, r1);
-        for (int s = 0; s < cmax; ++s) {
-            const int32_t C = s < cy ? row_entry(r0, r1, rowy, s) : -2 - lane;
-            const unsigned mask = __match_any_sync(FULL, C);
-            if (C >= 0 && lane == __ffs(mask) - 1)
-                if (!st_insert_bounded(skeys, svals, SH - 1, C, (uint32_t)__popc(mask), 32))
-                    if (!hub_insert(keys, vals, hm, C, (uint32_t)__popc(mask), false, list, &a.hub_ncand[h]))
-                        bad = true;
-        }
+        fill_flat_with(a, y, cy, r0, r1, [](int32_t) { return true; }, [&](int32_t C, uint32_t c) {
+            if (!st_insert_bounded(skeys, svals, SH - 1, C, c, 32))
+                if (!hub_insert(keys, vals, hm, C, c, false, list, &a.hub_ncand[h])) bad = true;
+        });
     }
     __syncthreads();
     for (uint32_t s0 = threadIdx.x; s0 < SH; s0 += 4 * EV_THREADS) {
@@ -1538,7 +1539,7 @@ __global__ void __launch_bounds__(EV_THREADS) k_eval_dyn(RunArgs a, int64_t bsta
 // counter; a node whose entries exceed the team's table goes on to the next
 // list.  in_ctr: [count, next]; out_ctr: [count].
 template <int T>
-__global__ void __launch_bounds__(EV_THREADS) k_eval_tdyn(RunArgs a, int64_t bstart, int64_t bidx, uint32_t *in_ctr,
+__global__ void __launch_bounds__(EV_THREADS, 3) k_eval_tdyn(RunArgs a, int64_t bstart, int64_t bidx, uint32_t *in_ctr,
                                                           const int32_t *in_list, const long long *in_bound,
                                                           uint32_t *out_ctr, int32_t *out_list,
                                                           long long *out_bound) {
@@ -1610,7 +1611,7 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <int T>
-__global__ void __launch_bounds__(EV_THREADS) k_eval(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx) {
+__global__ void __launch_bounds__(EV_THREADS, 3) k_eval(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx) {
     extern __shared__ int32_t ev_dyn[];   // HB keys, HB counts, HB upper and HB lower screen bounds
     __shared__ EvalShared es;
     // the team's node and its first adjacency chunk: static, read before the wait
