@@ -358,8 +358,11 @@ lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_t
  *                      own status, with its result in *res (may be NULL).
  *   lf_server_get_communities: as lf_get_communities, for a finished job.
  *   lf_server_release: forgets a finished job's result.
- *   lf_server_destroy: drops the jobs not yet admitted, waits for the running
- *                      ones, frees everything.
+ *   lf_server_destroy: drops the jobs not yet admitted (they finish with
+ *                      LF_ERR_STATE), waits for the running ones and for the
+ *                      threads inside lf_server_wait to return, frees
+ *                      everything.  No call on the same server may start once
+ *                      it has begun.
  * Times in lf_job_result are milliseconds since the server was created.
  */
 typedef struct lf_server lf_server;

@@ -1475,14 +1475,6 @@ __device__ void eval_group(const RunArgs &a, int64_t bstart, int32_t blen, int b
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(EV_THREADS) k_eval_huge(RunArgs a, int64_t bstart, int64_t bidx) {
-    __shared__ BlockScratch bs;
-    __shared__ int32_t bkey[EV_WARPS][32];
-    __shared__ uint32_t bval[EV_WARPS][32];
-    const int w = threadIdx.x >> 5;
-    eval_huge(a, bstart, bidx, queue_serial(a, bidx), bkey[w], bval[w], bs);
-}
-
 // Large queues: a resident grid whose warps take the queue's nodes one at a
 // time from a counter, so that no warp waits at a block-wide barrier for the
 // others' nodes.  Nodes whose histogram does not fit a warp's table are

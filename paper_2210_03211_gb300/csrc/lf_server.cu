@@ -50,6 +50,7 @@ struct lf_server {
     int64_t next_id = 1;
     int64_t reserved = 0;   // estimated bytes of the jobs admitted and not finished
     int active = 0;
+    int waiters = 0;        // threads inside lf_server_wait
     bool stop = false;
     std::vector<std::thread> workers;
 };
@@ -215,9 +216,14 @@ lf_status lf_server_wait(lf_server *s, int64_t job_id, double timeout_s, lf_job_
     }
     std::shared_ptr<Job> job = it->second;
     const auto pred = [&] { return job->done; };
-    if (timeout_s < 0) {
+    ++s->waiters;
+    bool finished = true;
+    if (timeout_s < 0)
         s->cv_done.wait(lk, pred);
-    } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) {
+    else
+        finished = s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred);
+    if (--s->waiters == 0 && s->stop) s->cv_done.notify_all();   // lf_server_destroy waits for this
+    if (!finished) {
         lf::set_error(LF_ERR_TIMEOUT, "job %lld not finished", (long long)job_id);
         return LF_ERR_TIMEOUT;
     }
@@ -274,12 +280,26 @@ lf_status lf_server_release(lf_server *s, int64_t job_id) {
 void lf_server_destroy(lf_server *s) {
     if (!s) return;
     {
+        // jobs not yet admitted are dropped: each finishes with LF_ERR_STATE,
+        // so that a thread waiting on one wakes up instead of waiting forever
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
-        s->pending.clear();   // jobs not yet admitted are dropped
+        for (auto &job : s->pending) {
+            job->res.status = LF_ERR_STATE;
+            job->res.t_done_ms = ms_since(s);
+            job->error = "cancelled: the server was destroyed before the job was admitted";
+            job->done = true;
+        }
+        s->pending.clear();
     }
     s->cv_work.notify_all();
+    s->cv_done.notify_all();
     for (auto &t : s->workers) t.join();
+    {
+        // every job is finished now; let the threads inside lf_server_wait leave
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->cv_done.wait(lk, [&] { return s->waiters == 0; });
+    }
     delete s;
 }
 

@@ -83,3 +83,27 @@ def test_a_failing_job_does_not_stop_the_server(lf):
             srv.wait(bad)
         assert e.value.status == lf.LF_ERR_INVALID
         assert srv.wait(ok)["status"] == lf.LF_OK
+
+
+def test_destroy_cancels_jobs_not_yet_admitted(lf):
+    import threading
+    import time
+    el = W.dblp_like(seed=3, scale=0.3)
+    srv = lf.Server(max_active=1)
+    ids = [srv.submit(el.src, el.dst, 16, -math.inf, 20) for _ in range(6)]
+    out = {}
+
+    def waiter():
+        try:
+            out["res"] = srv.wait(ids[-1])
+        except lf.LazyFoxError as e:
+            out["err"] = e
+
+    t = threading.Thread(target=waiter)
+    t.start()
+    time.sleep(0.3)   # the waiter is inside lf_server_wait; the first job (20 full iterations) still runs
+    srv.close()       # returns once the running job finished and the waiter left
+    t.join(60)
+    assert not t.is_alive()
+    assert "err" in out, out
+    assert out["err"].status == lf.LF_ERR_STATE and "cancelled" in str(out["err"])
