@@ -72,6 +72,10 @@ def lib():
             "og_community_score": (C.c_double, [C.c_int64, C.c_int64, C.c_int64, C.c_double]),
             "og_exact_wcc": (C.c_double, [_P, C.c_int32, _I32P, C.c_int64]),
             "og_adjacent": (C.c_int, [_P, C.c_int32, C.c_int32]),
+            "og_literal_gain": (C.c_double, [_P, C.c_int32, C.c_int32]),
+            "og_evaluate_literal": (None, [_P, C.c_int32, _I32P, _I32P, _F64P, _F64P]),
+            "og_set_literal_diagnostic": (None, [_P, C.c_int]),
+            "og_get_literal_diagnostic": (None, [_P, _I64P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -256,6 +260,29 @@ class OracleGraph:
 
     def total(self) -> float:
         return lib().og_total(self._h)
+
+    def literal_gain(self, x: int, c: int) -> float:
+        """Change of the literal \\wcchat(P) if x alone joins c (not a member)
+        or leaves it (a member); a diagnostic of the gain reading."""
+        return lib().og_literal_gain(self._h, int(x), int(c))
+
+    def evaluate_literal(self, x: int):
+        """x's decision with literal gains instead of mean-field ones."""
+        j, lv = C.c_int32(), C.c_int32()
+        gj, gl = C.c_double(), C.c_double()
+        lib().og_evaluate_literal(self._h, int(x), C.byref(j), C.byref(lv), C.byref(gj), C.byref(gl))
+        return dict(join=j.value, leave=lv.value, gjoin=gj.value, gleave=gl.value)
+
+    def set_literal_diagnostic(self, on: bool):
+        """Following runs also take every decision with literal gains and count agreement."""
+        lib().og_set_literal_diagnostic(self._h, 1 if on else 0)
+
+    def literal_diagnostic(self) -> dict:
+        out = np.zeros(8, dtype=np.int64)
+        lib().og_get_literal_diagnostic(self._h, _ptr(out, C.c_int64))
+        keys = ("evaluations", "same_join", "same_leave", "same_both", "joins_meanfield", "joins_literal",
+                "leaves_meanfield", "leaves_literal")
+        return {k: int(v) for k, v in zip(keys, out)}
 
     def total_meanfield(self) -> float:
         return lib().og_total_meanfield(self._h)

@@ -79,6 +79,11 @@ typedef struct og_graph {
     int64_t part_k;
     int64_t *part_off;
     int32_t *part_mem;
+    /* diagnostic of the gain reading (off by default): during og_run, every
+     * evaluated node's decision is also taken with the literal gains and the
+     * two are compared; see og_set_literal_diagnostic */
+    int literal_diag;
+    int64_t diag[8];
 } og_graph;
 
 /* ------------------------------------------------------------------------ */
@@ -646,6 +651,73 @@ static og_action evaluate_node(const og_graph *g, int32_t x)
     return a;
 }
 
+/* Diagnostic of the gain reading (not used for any decision).  The literal
+ * gain of a move (Joining / Leaving a Community) is the change of \wcchat(P)
+ * -- the sum of the per-node estimator over all memberships -- when x alone
+ * enters (joining != 0) or leaves community c and every other membership
+ * stays: C's members see n_C, m_C and, for neighbours of x, deg(y,C) change,
+ * and x's own term appears or disappears; no other term changes.  The terms
+ * after the move and the negated terms before it are added with the
+ * correctly rounded sum.  Costs O(n + |C| deg) per candidate: small graphs. */
+static double literal_gain(const og_graph *g, int32_t x, int32_t c, int joining)
+{
+    int64_t d = deg(g, x);
+    int64_t kx = neighbours_in(g, x, c);
+    int64_t n0 = g->cn[c], m0 = g->cm[c];
+    int64_t n1 = joining ? n0 + 1 : n0 - 1;
+    int64_t m1 = joining ? m0 + kx : m0 - kx;
+    double *terms = (double *)malloc((size_t)(2 * n0 + 2) * sizeof(double));
+    int64_t t = 0;
+    for (int64_t y = 0; y < g->n; ++y) {
+        if (y == x || !mem_has(g, y, c)) continue;
+        int64_t ky = neighbours_in(g, y, c);
+        int64_t ky1 = ky;
+        if (find_in_row(g, y, x) >= 0) ky1 += joining ? 1 : -1;
+        terms[t++] = og_wcchat_node(ky1, deg(g, y), n1, m1, g->cc);
+        terms[t++] = -og_wcchat_node(ky, deg(g, y), n0, m0, g->cc);
+    }
+    if (joining) terms[t++] = og_wcchat_node(kx, d, n1, m1, g->cc);
+    else terms[t++] = -og_wcchat_node(kx, d, n0, m0, g->cc);
+    double gain = og_fsum(terms, t);
+    free(terms);
+    return gain;
+}
+
+/* The decision of evaluate_node with the literal gains in place of the
+ * mean-field ones: the same candidates (communities met among the
+ * neighbours to join, own communities to leave), the best strictly
+ * positive gain of each kind, ties to the lowest id. */
+static og_action evaluate_node_literal(const og_graph *g, int32_t x)
+{
+    og_action a = { -1, -1, 0, 0, 0.0, 0.0 };
+    int64_t ne = 0;
+    for (int64_t p = g->off[x]; p < g->off[x + 1]; ++p) ne += g->nmem[g->adj[p]];
+    int64_t total = ne + g->nmem[x];
+    int32_t *ent = (int32_t *)malloc((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
+    int64_t e = 0;
+    for (int64_t p = g->off[x]; p < g->off[x + 1]; ++p) {
+        int32_t y = g->adj[p];
+        for (int32_t j = 0; j < g->nmem[y]; ++j) ent[e++] = g->mem[y][j];
+    }
+    for (int32_t j = 0; j < g->nmem[x]; ++j) ent[e++] = g->mem[x][j];
+    qsort(ent, (size_t)total, sizeof(int32_t), cmp_i32);
+    for (int64_t i = 0; i < total; ) {
+        int32_t c = ent[i];
+        int64_t run = 0;
+        while (i < total && ent[i] == c) { ++run; ++i; }
+        int own = mem_has(g, x, c);
+        int64_t k = own ? run - 1 : run;
+        double gain = literal_gain(g, x, c, !own);
+        if (!own) {
+            if (gain > 0.0 && (a.join < 0 || gain > a.gjoin)) { a.join = c; a.kjoin = k; a.gjoin = gain; }
+        } else {
+            if (gain > 0.0 && (a.leave < 0 || gain > a.gleave)) { a.leave = c; a.kleave = k; a.gleave = gain; }
+        }
+    }
+    free(ent);
+    return a;
+}
+
 /* Apply one node's actions to the current partition, leave first.  Each
  * single move changes the community's internal edge count by the number of
  * edges between the node and the community's members at that moment. */
@@ -725,6 +797,7 @@ int og_run(og_graph *g, int32_t queue_size, double threshold, int32_t max_iters,
     g->iterations = 0;
     g->converged = 0;
     g->invariant_failures = 0;
+    memset(g->diag, 0, sizeof(g->diag));
     g->T0 = og_total(g);
     double prev = g->T0;
     int64_t batches = 0;
@@ -734,7 +807,22 @@ int og_run(og_graph *g, int32_t queue_size, double threshold, int32_t max_iters,
         for (int64_t start = 0; start < g->n; start += queue_size) {
             if (max_batches >= 0 && batches >= max_batches) { free(acts); return OG_OK; }
             int64_t end = start + queue_size < g->n ? start + queue_size : g->n;
-            for (int64_t i = start; i < end; ++i) acts[i - start] = evaluate_node(g, g->order[i]);
+            for (int64_t i = start; i < end; ++i) {
+                acts[i - start] = evaluate_node(g, g->order[i]);
+                if (g->literal_diag) {
+                    /* same snapshot: nothing of this queue is applied yet */
+                    og_action lit = evaluate_node_literal(g, g->order[i]);
+                    int same_j = lit.join == acts[i - start].join, same_l = lit.leave == acts[i - start].leave;
+                    g->diag[0]++;
+                    g->diag[1] += same_j;
+                    g->diag[2] += same_l;
+                    g->diag[3] += same_j && same_l;
+                    g->diag[4] += acts[i - start].join >= 0;
+                    g->diag[5] += lit.join >= 0;
+                    g->diag[6] += acts[i - start].leave >= 0;
+                    g->diag[7] += lit.leave >= 0;
+                }
+            }
             for (int64_t i = start; i < end; ++i) {
                 apply_actions(g, g->order[i], acts[i - start]);
                 joins += acts[i - start].join >= 0;
@@ -909,6 +997,29 @@ void og_evaluate(const og_graph *g, int32_t x, int32_t *join, int32_t *leave,
     og_action a = evaluate_node(g, x);
     *join = a.join; *leave = a.leave; *kjoin = a.kjoin; *kleave = a.kleave;
     *gjoin = a.gjoin; *gleave = a.gleave;
+}
+
+/* Literal gain of x joining c (x not a member) or leaving it (a member). */
+double og_literal_gain(const og_graph *g, int32_t x, int32_t c)
+{
+    return literal_gain(g, x, c, !mem_has(g, x, c));
+}
+
+void og_evaluate_literal(const og_graph *g, int32_t x, int32_t *join, int32_t *leave, double *gjoin,
+                         double *gleave)
+{
+    og_action a = evaluate_node_literal(g, x);
+    *join = a.join; *leave = a.leave; *gjoin = a.gjoin; *gleave = a.gleave;
+}
+
+/* on != 0: the following runs compare every decision with the literal one.
+ * Counts of the last run: evaluations, equal join decisions, equal leave
+ * decisions, both equal, mean-field joins, literal joins, mean-field leaves,
+ * literal leaves. */
+void og_set_literal_diagnostic(og_graph *g, int on) { g->literal_diag = on; }
+void og_get_literal_diagnostic(const og_graph *g, int64_t *out)
+{
+    for (int i = 0; i < 8; ++i) out[i] = g->diag[i];
 }
 
 double og_get_cc(const og_graph *g) { return g->cc; }
