@@ -59,3 +59,16 @@ def test_fifo_finish_times():
     import bench
     fin = bench.fifo_finish(np.array([0.0, 0.5, 0.6, 5.0]), np.array([1.0, 1.0, 0.5, 0.25]))
     assert np.allclose(fin, [1.0, 2.0, 2.5, 5.25])
+
+
+def test_oracle_sample_runs_one_process_per_core():
+    """The CPU baseline of the batched workload: independent graphs through the
+    oracle in a 'spawn' pool; every graph is run once and the CPU seconds add up."""
+    import bench
+    from paper_2210_03211_gb300 import workloads as W
+    graphs = [W.planted_er(n=120, num_comms=4, size_lo=10, size_hi=30, seed=s) for s in range(5)]
+    gps, cpu_s = bench.oracle_graphs_per_s(graphs, 4, 0.01, 50, 2)
+    assert gps > 0 and cpu_s > 0
+    # the wall time of the sample cannot be below its CPU time spread over two processes
+    assert len(graphs) / gps >= cpu_s / 2 * 0.9
+    assert bench.host_cores() >= 1
