@@ -322,6 +322,8 @@ class Graph:
         """on_iteration(iteration, wcc) is called after every iteration; it may
         call communities() (the intermediate result) and returns True to stop."""
         cb = None
+        if on_iteration is None:
+            on_iteration = getattr(self, "_on_iteration", None)   # set by lf_set_iteration_callback
         if on_iteration is not None:
             def _tramp(_g, it, wcc, _ctx):
                 try:
@@ -596,3 +598,147 @@ def quality_report(el, queue_sizes=(2, 4, 8, 16, 32, 64, 128, 256), threshold: f
         rows.append(dict(queue_size=q, f1_vs_fox=cover_f1(lazy, fox)[0],
                          f1_vs_planted=cover_f1(lazy, planted)[0] if planted else None))
     return rows
+
+
+# -- the entry points of include/lazyfox.h under their own names ---------------
+# One thin function per entry point: a handle is a Graph, Batch or Server
+# object; host buffers are numpy arrays, device buffers int32/int64 CUDA
+# tensors.  Each marshals its arguments and reaches the entry point of the
+# same name (through the methods above, which do the marshalling).
+
+def lf_graph_create(src, dst, **options) -> Graph:
+    """Build a graph and run the preprocessing; options as for :class:`Graph`."""
+    return Graph(src, dst, **options)
+
+
+def lf_run(g: Graph, queue_size: int, wcc_threshold: float = 0.01, max_iters: int = 50) -> RunStats:
+    return g.run(queue_size, wcc_threshold, max_iters)
+
+
+def lf_run_partial(g: Graph, queue_size: int, wcc_threshold: float, max_iters: int, max_batches: int) -> RunStats:
+    return g.run(queue_size, wcc_threshold, max_iters, max_batches=max_batches)
+
+
+def lf_get_communities(g: Graph):
+    """(offsets int64[k+1], members int32[...]) in original node ids."""
+    return g.communities()
+
+
+def lf_get_node_stats(g: Graph):
+    """(t int64[n], vt int32[n], cc)."""
+    return g.node_stats()
+
+
+def lf_get_sizes(g: Graph):
+    """(nodes n, undirected simple edges m)."""
+    n, m = C.c_int64(), C.c_int64()
+    _check(g._L, g._L.lf_get_sizes(g._h, C.byref(n), C.byref(m)))
+    return n.value, m.value
+
+
+def lf_get_create_stats(g: Graph) -> dict:
+    return g.create_stats()
+
+
+def lf_get_csr(g: Graph):
+    """(offsets int64[n+1], neighbours int32[2m], labels int32[n])."""
+    return g.csr()
+
+
+def lf_get_oriented(g: Graph):
+    return g.oriented()
+
+
+def lf_get_order(g: Graph):
+    return g.order()
+
+
+def lf_get_state(g: Graph) -> dict:
+    return g.state()
+
+
+def lf_graph_destroy(g: Graph) -> None:
+    g.close()
+
+
+def lf_last_error() -> str:
+    """The calling thread's message of its last failed call."""
+    return load_library().lf_last_error().decode(errors="replace")
+
+
+def lf_triangles_noalloc(ooff, oadj, t, vt, stream=None) -> None:
+    """t(x,V) and vt(x,V) of an oriented CSR (device tensors: ooff int64[n+1],
+    oadj int32[m]) into device tensors t int64[n] and vt int32[n], without any
+    device allocation (``stream``: a torch.cuda.Stream or None)."""
+    import torch
+    for a, dt in ((ooff, torch.int64), (oadj, torch.int32), (t, torch.int64), (vt, torch.int32)):
+        if not isinstance(a, torch.Tensor) or a.dtype != dt or not a.is_cuda or not a.is_contiguous():
+            raise TypeError("lf_triangles_noalloc takes contiguous CUDA tensors: ooff int64, oadj int32, "
+                            "t int64, vt int32")
+    n = ooff.numel() - 1
+    if n < 0 or t.numel() < n or vt.numel() < n:
+        raise ValueError("ooff needs n+1 entries and t, vt n each")
+    L = load_library()
+    st = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(L, L.lf_triangles_noalloc(C.c_void_p(ooff.data_ptr()), C.c_void_p(oadj.data_ptr()), n, oadj.numel(),
+                                     C.c_void_p(t.data_ptr()), C.c_void_p(vt.data_ptr()), st))
+
+
+def lf_set_partition(g: Graph, communities) -> None:
+    g.set_partition(communities)
+
+
+def lf_set_iteration_callback(g: Graph, fn) -> None:
+    """fn(iteration, wcc) after every iteration of g's later runs (True stops
+    the run); None removes it."""
+    g._on_iteration = fn
+
+
+def lf_batch_create(graphs, **options) -> Batch:
+    return Batch(graphs, **options)
+
+
+def lf_batch_get_info(b: Batch) -> dict:
+    return b.info()
+
+
+def lf_batch_get_history(b: Batch, graph: int):
+    return b.history(graph)
+
+
+def lf_batch_get_communities(b: Batch):
+    """For every graph, its communities as arrays of its own node ids."""
+    return b.graph_communities()
+
+
+def lf_autotune(g: Graph, queue_size: int, trial_iters: int = 1) -> dict:
+    return g.autotune(queue_size, trial_iters)
+
+
+def lf_server_create(hbm_budget_bytes: int = 0, max_active: int = 4) -> Server:
+    return Server(hbm_budget_bytes, max_active)
+
+
+def lf_server_submit(s: Server, src, dst, queue_size: int, wcc_threshold: float = 0.01, max_iters: int = 50) -> int:
+    return s.submit(src, dst, queue_size, wcc_threshold, max_iters)
+
+
+def lf_server_wait(s: Server, job: int, timeout_s: float = -1.0) -> dict:
+    return s.wait(job, timeout_s)
+
+
+def lf_server_get_communities(s: Server, job: int):
+    return s.community_list(job)
+
+
+def lf_server_release(s: Server, job: int) -> None:
+    s.release(job)
+
+
+def lf_server_destroy(s: Server) -> None:
+    s.close()
+
+
+def lf_cover_f1(detected, reference, stream=None):
+    """(F1, best reference index per detected community)."""
+    return cover_f1(detected, reference, stream)
