@@ -76,6 +76,7 @@ def lib():
             "og_evaluate_literal": (None, [_P, C.c_int32, _I32P, _I32P, _F64P, _F64P]),
             "og_set_literal_diagnostic": (None, [_P, C.c_int]),
             "og_get_literal_diagnostic": (None, [_P, _I64P]),
+            "og_get_meanfield_history": (None, [_P, _F64P, C.c_int32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -230,8 +231,10 @@ class OracleGraph:
         lib().og_get_run(self._h, C.byref(it), C.byref(conv), C.byref(T0), _ptr(T, C.c_double),
                          _ptr(j, C.c_int64), _ptr(lv, C.c_int64), cap)
         k = it.value
+        S = np.zeros(cap, dtype=np.float64)
+        lib().og_get_meanfield_history(self._h, _ptr(S, C.c_double), cap)
         return dict(iterations=k, converged=bool(conv.value), T0=T0.value,
-                    T=T[:k].copy(), joins=j[:k].copy(), leaves=lv[:k].copy())
+                    T=T[:k].copy(), joins=j[:k].copy(), leaves=lv[:k].copy(), S=S[:k].copy())
 
     def state(self):
         """Memberships (CSR over dense ids) and aggregates for every community id.

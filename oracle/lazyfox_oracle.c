@@ -69,6 +69,7 @@ typedef struct og_graph {
     int32_t converged;
     double T0;
     double *T_hist;
+    double *S_hist;        /* diagnostic: sum of the mean-field community scores per iteration */
     int64_t *joins_hist, *leaves_hist;
     int32_t hist_cap;
     int check_invariants;  /* recount aggregates after every batch */
@@ -789,9 +790,10 @@ int og_run(og_graph *g, int32_t queue_size, double threshold, int32_t max_iters,
     if (queue_size < 1 || max_iters < 0) return OG_ERR_INVALID;
     int st = g->part_k >= 0 ? init_from_partition(g) : og_init_clustering(g);
     if (st) return st;
-    free(g->T_hist); free(g->joins_hist); free(g->leaves_hist);
+    free(g->T_hist); free(g->S_hist); free(g->joins_hist); free(g->leaves_hist);
     g->hist_cap = max_iters > 0 ? max_iters : 1;
     g->T_hist = (double *)calloc((size_t)g->hist_cap, sizeof(double));
+    g->S_hist = (double *)calloc((size_t)g->hist_cap, sizeof(double));
     g->joins_hist = (int64_t *)calloc((size_t)g->hist_cap, sizeof(int64_t));
     g->leaves_hist = (int64_t *)calloc((size_t)g->hist_cap, sizeof(int64_t));
     g->iterations = 0;
@@ -834,6 +836,7 @@ int og_run(og_graph *g, int32_t queue_size, double threshold, int32_t max_iters,
         prune(g);
         double T = og_total(g);
         g->T_hist[it - 1] = T;
+        g->S_hist[it - 1] = og_total_meanfield(g);
         g->joins_hist[it - 1] = joins;
         g->leaves_hist[it - 1] = leaves;
         g->iterations = it;
@@ -987,6 +990,13 @@ void og_get_run(const og_graph *g, int32_t *iterations, int32_t *converged, doub
     }
 }
 
+/* Diagnostic history: the sum of the mean-field community scores after each
+ * iteration of the last run (beside the literal totals that drive the stop). */
+void og_get_meanfield_history(const og_graph *g, double *S_hist, int32_t cap)
+{
+    for (int32_t i = 0; i < g->iterations && i < cap; ++i) S_hist[i] = g->S_hist[i];
+}
+
 void og_set_check_invariants(og_graph *g, int on) { g->check_invariants = on; }
 int og_invariant_failures(const og_graph *g) { return g->invariant_failures; }
 
@@ -1030,6 +1040,6 @@ void og_destroy(og_graph *g)
     free_state(g);
     free(g->part_off); free(g->part_mem);
     free(g->labels); free(g->off); free(g->adj); free(g->t); free(g->vt); free(g->order);
-    free(g->T_hist); free(g->joins_hist); free(g->leaves_hist);
+    free(g->T_hist); free(g->S_hist); free(g->joins_hist); free(g->leaves_hist);
     free(g);
 }

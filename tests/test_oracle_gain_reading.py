@@ -150,3 +150,28 @@ def test_disjoint_cliques_agree_completely(oracle_lib):
     d = og.literal_diagnostic()
     assert d["evaluations"] == og.n and d["same_both"] == og.n
     assert d["joins_literal"] == d["leaves_literal"] == 0
+
+
+def test_meanfield_history_is_the_sum_of_community_scores(oracle_lib):
+    """The diagnostic history beside the literal totals: after every
+    iteration, the correctly rounded sum of S(n_C, m_C, vol_C) over the live
+    communities -- checked on the last iteration against the scores of the
+    final aggregates, and on isolated cliques against the closed form
+    S = n / cc (every member's estimator is 1/cc there)."""
+    el = W.planted_er(n=120, num_comms=6, size_lo=10, size_hi=30, p_in=0.3, seed=3)
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    r = og.run(4, 0.01, 50)
+    assert r["S"].shape == r["T"].shape
+    st = og.state()
+    terms = [oracle_lib.community_score(int(n), int(m), int(v), og.cc)
+             for n, m, v in zip(st["n"], st["m"], st["vol"]) if n > 0]
+    assert r["S"][-1] == oracle_lib.fsum(terms)
+    src, dst = [], []
+    for base, k in ((0, 4), (10, 5), (20, 6)):
+        for i in range(k):
+            for j in range(i + 1, k):
+                src.append(base + i)
+                dst.append(base + j)
+    og = oracle_lib.OracleGraph(np.array(src, np.int32), np.array(dst, np.int32))
+    r = og.run(1, 0.01, 5)
+    assert og.cc == 1.0 and abs(r["S"][-1] - 15.0) <= 8 * EPS * 15 and abs(r["T"][-1] - 15.0) <= 8 * EPS * 15
