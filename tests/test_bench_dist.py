@@ -1,5 +1,7 @@
-"""Host-side multi-rank logic of bench.py (replicas; max of times and sum of
-units over ranks) on two gloo ranks on the CPU."""
+"""Host-side logic of bench.py: the multi-rank replicas (max of times and sum of
+units over ranks) on two gloo ranks on the CPU, the reference arm's rank
+rule, first-come-first-served finish times, the process pool of the CPU
+baseline, the traffic gate, the peak lookup and the clock samples."""
 import os
 import socket
 
@@ -72,3 +74,46 @@ def test_oracle_sample_runs_one_process_per_core():
     # the wall time of the sample cannot be below its CPU time spread over two processes
     assert len(graphs) / gps >= cpu_s / 2 * 0.9
     assert bench.host_cores() >= 1
+
+
+def test_traffic_is_reported_only_for_the_captured_source(tmp_path, monkeypatch):
+    """The committed ncu traffic counts for a kernel whose source changed
+    since the capture are not reported (None)."""
+    import hashlib
+    import bench
+    src_dir = tmp_path / "paper_2210_03211_gb300" / "csrc"
+    src_dir.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    src = src_dir / "lf_run.cu"
+    src.write_text("// kernel source\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles" / "k_eval_traffic.txt").write_text(
+        "# comment: with a colon\nsource: lf_run.cu\n"
+        f"source_sha256_16: {sha}\ndram_bytes_per_launch_scaled: 2977331\ncaptured_on: test\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic("k_eval") == {"bytes_per_launch": 2977331.0, "workload": "test"}
+    src.write_text("// kernel source, changed\n")
+    assert bench.ncu_traffic("k_eval") is None
+    assert bench.ncu_traffic("k_other") is None
+
+
+def test_measured_peak_and_its_fallback(tmp_path, monkeypatch):
+    import json
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_hbm() == (bench.FALLBACK_HBM_GBS, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6813.8, "bf16_tflops": 1900}))
+    assert bench.measured_hbm() == (6813.8, "measured")
+
+
+def test_clock_samples_give_median_max_and_reasons(tmp_path):
+    import bench
+    s = bench.ClockSampler("GPU-0")
+    s.path = str(tmp_path / "clocks.csv")
+    with open(s.path, "w") as f:
+        f.write("2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n")
+        f.write("2055, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("[N/A]\n")
+    out = s.stop()
+    assert out == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
