@@ -211,19 +211,24 @@ def test_edge_cases(lf, oracle_lib):
 @pytest.mark.parametrize("q", [64, 1024])
 def test_full_size_335k_parity(lf, oracle_lib, q):
     """The 335k-node / ~0.93M-edge workload at full size, in the configuration
-    the benchmark times: every output compared with the oracle."""
+    the benchmark times: every output compared with the oracle, with the
+    default launch shape and with the shape the autotuner picks for the
+    benchmark (two-iteration trials)."""
     el = W.dblp_like()
     og = oracle_lib.OracleGraph(el.src, el.dst)
     ref = og.run(q, 0.01, 50)
+    want = og.communities()
     with lf.Graph(el.src, el.dst) as g:
         compare_preprocessing(g, og)
-        st = g.run(q, 0.01, 50)
-        compare_run(st, ref)
-        compare_state(g, og)
-        off, mem = g.communities()
-        want = og.communities()
-        assert off.shape[0] - 1 == len(want)
-        assert np.array_equal(mem, np.concatenate(want))
+        for tuned in (False, True):
+            if tuned:
+                g.autotune(q, 2)
+            st = g.run(q, 0.01, 50)
+            compare_run(st, ref)
+            compare_state(g, og)
+            off, mem = g.communities()
+            assert off.shape[0] - 1 == len(want)
+            assert np.array_equal(mem, np.concatenate(want))
 
 
 @pytest.mark.parametrize("el", [CASES[-1], CASES[-2], CASES[-4]], ids=[IDS[-1], IDS[-2], IDS[-4]])
