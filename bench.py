@@ -28,6 +28,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -241,6 +242,21 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def host_info() -> dict:
+    """The host a CPU baseline ran on: the logical CPUs this process may use,
+    the architecture and the CPU model as lscpu names it (None if unknown)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:  # noqa: BLE001 - no lscpu: the model stays unknown
+        pass
+    return {"nproc": host_cores(), "machine": platform.machine(), "cpu_model": model}
+
+
 def oracle_graphs_per_s(graphs, q, threshold, max_iters, cores):
     """The oracle on independent graphs, one process per host core: a 'spawn'
     pool (safe after GPU calls), every worker started and the oracle loaded
@@ -276,7 +292,7 @@ def run_reference(args, spec, q):
                 "config": {"workload": spec["name"], "graphs": len(graphs), "queue_size": q},
                 "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": cores, "kind": "oracle",
                                  "sample": f"the first {len(graphs)} graphs of the {what}, one oracle process "
-                                           f"per host core ({cpu_s:.1f} CPU seconds)"},
+                                           f"per host core ({cpu_s:.1f} CPU seconds)", "host": host_info()},
                 "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -298,7 +314,8 @@ def run_reference(args, spec, q):
         "config": {"workload": spec["name"], "queue_size": q, "threshold": spec["threshold"],
                    "max_iters": spec["max_iters"], "iterations": iters},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full runs (preprocessing + all iterations) of the workload"},
+                         "sample": f"{args.steps} full runs (preprocessing + all iterations) of the workload",
+                         "host": host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -393,7 +410,7 @@ def run_batched(args, spec, q):
         cpu_gps, cpu_s = oracle_graphs_per_s(cpu_sample, q, spec["threshold"], spec["max_iters"], cores)
         cpu = {"value": cpu_gps, "unit": "graphs/s", "cores": cores, "kind": "oracle",
                "sample": f"the first {len(cpu_sample)} graphs of the batch, one oracle process per host core "
-                         f"({cpu_s:.1f} CPU seconds)"}
+                         f"({cpu_s:.1f} CPU seconds)", "host": host_info()}
     if rank == 0:
         batch_ms = np.array([r[0] for r in res])
         line = {
@@ -680,7 +697,7 @@ def main():
         u, dt, it = time_oracle(el, q, spec["threshold"], spec["max_iters"])
         cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one full run (preprocessing + {it} iterations) of the same workload at queue size {q}",
-               "seconds": dt}
+               "seconds": dt, "host": host_info()}
 
     if rank == 0:
         r0 = res[0]

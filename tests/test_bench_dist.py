@@ -117,3 +117,10 @@ def test_clock_samples_give_median_max_and_reasons(tmp_path):
         f.write("[N/A]\n")
     out = s.stop()
     assert out == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_host_info_names_the_cpu():
+    import bench
+    h = bench.host_info()
+    assert h["nproc"] == bench.host_cores() >= 1 and h["machine"]
+    assert h["cpu_model"] is None or isinstance(h["cpu_model"], str)
