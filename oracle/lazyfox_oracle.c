@@ -34,10 +34,11 @@
  *   - stop when (T_it - T_prev) / T_prev < threshold; if T_prev == 0, stop
  *     iff T_it == 0 (Stopping Criteria).
  *
- * Parity pins: see tests/test_oracle_*.py.  The whole-run outputs on generic
- * graphs (memberships after many iterations) have no external reference: the
- * paper prints no intermediate values, so that part is "parity unpinned"
- * beyond the invariants, closed forms and brute-force checks in the tests.
+ * Parity pins: see tests/test_oracle_*.py; whole runs on tiny graphs are
+ * compared with an exact-rational brute force.  Whole runs on graphs beyond
+ * brute-force size have no external reference (the paper prints no
+ * intermediate values), so that part is "parity unpinned" beyond the
+ * invariants, closed forms and brute-force checks in the tests.
  */
 #include <math.h>
 #include <stdint.h>

@@ -1,0 +1,178 @@
+"""Whole runs of the oracle against an exact-rational brute force.
+
+The brute force below is written from the paper's definitions alone, in exact
+rational arithmetic, with none of the oracle's data structures: simple sets
+for the graph and the communities, triangles by enumeration, every aggregate
+recounted from the member sets (Methods: Preprocessing, Node Order, Heuristic
+Counting of Triangles, Initial Clustering, Node Changes with Algorithm 1,
+Parallelism on Node Change Computations with Algorithm 2, Stopping Criteria,
+Post-processing; the gain of a move is the change of the community's
+mean-field score, as in the oracle).  On tiny graphs it gives the runs exactly,
+so the oracle's FP64 runs must agree with it wherever no decision is within
+rounding distance of a tie: a candidate's gain next to 0, two best gains next
+to each other, or the relative change next to the threshold.  Such graphs are
+counted and skipped; the test asserts that most graphs decide.
+"""
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+from paper_2210_03211_gb300 import workloads as W
+
+MARGIN = Fr(1, 10 ** 9)   # relative distance below which FP64 may legitimately decide otherwise
+
+
+def B(z):
+    return z * (z - 1) / 2 if z >= 1 else Fr(0)
+
+
+def member_score(k, d, n, m, cc):
+    """The per-node estimator for a member with k neighbours inside, degree d,
+    in a community of n members and m internal edges."""
+    if n < 2:
+        return Fr(0)
+    p = Fr(2 * m, n * (n - 1))
+    ev = B(Fr(d)) * cc
+    if ev <= 0:
+        return Fr(0)
+    return (B(Fr(k)) * p / ev) * Fr(d) / ((n - 1) + (d - k))
+
+
+def community_score(n, m, vol, cc):
+    """The mean-field score: n members with internal degree 2m/n and degree vol/n."""
+    if n < 2:
+        return Fr(0)
+    din, D, p = Fr(2 * m, n), Fr(vol, n), Fr(2 * m, n * (n - 1))
+    ev = B(D) * cc
+    if ev <= 0:
+        return Fr(0)
+    return n * (B(din) * p / ev) * (D / ((n - 1) + (D - din)))
+
+
+class Tight(Exception):
+    """A decision within rounding distance of a tie."""
+
+
+def exact_run(edges, q, threshold, max_iters):
+    pairs = {(min(u, v), max(u, v)) for u, v in edges if u != v}
+    ids = sorted({x for p in pairs for x in p})
+    N = {v: set() for v in ids}
+    for u, v in pairs:
+        N[u].add(v)
+        N[v].add(u)
+    deg = {v: len(N[v]) for v in ids}
+    t = {v: sum(1 for a in N[v] for b in N[v] if a < b and b in N[a]) for v in ids}
+    CC = {v: Fr(t[v], deg[v] * (deg[v] - 1) // 2) if deg[v] > 1 else Fr(0) for v in ids}
+    cc = sum(CC.values(), Fr(0)) / len(ids)
+    order = sorted(ids, key=lambda v: (-CC[v], -deg[v], v))
+    # initial clustering: a node not yet in a community opens one with its unassigned neighbours
+    comms, assigned = [], set()
+    for v in order:
+        if v in assigned:
+            continue
+        c = {v} | {u for u in N[v] if u not in assigned}
+        assigned |= c
+        comms.append(c)
+
+    def agg(c):
+        m = sum(1 for a in c for b in N[a] if b in c) // 2
+        return len(c), m, sum(deg[a] for a in c)
+
+    def total():
+        return sum((member_score(len(N[x] & c), deg[x], *agg(c)[:2], cc) for c in comms for x in c), Fr(0))
+
+    def best(gains):
+        """gains: (after, before, inputs, community).  FP64 evaluates equal
+        inputs to equal values and two zero scores to a zero gain, so only
+        nonzero scores whose difference is near 0, or near-equal best gains
+        from different inputs, are within rounding distance of a tie."""
+        for after, before, _, _ in gains:
+            if (after or before) and abs(after - before) <= MARGIN * max(abs(after), abs(before)):
+                raise Tight()
+        pos = sorted(((a - b, key, c) for a, b, key, c in gains if a - b > 0), key=lambda t: (-t[0], t[2]))
+        if len(pos) > 1 and pos[1][1] != pos[0][1] and pos[0][0] - pos[1][0] <= MARGIN * pos[0][0]:
+            raise Tight()
+        return pos[0][2] if pos else -1
+
+    T_prev = total()
+    T0, hist, joins, leaves = T_prev, [], [], []
+    for _ in range(max_iters):
+        nj = nl = 0
+        for s in range(0, len(order), q):
+            acts = []
+            for x in order[s:s + q]:   # every queued node sees the partition as the queue found it
+                jg, lg = [], []
+                for ci, c in enumerate(comms):
+                    n, m, vol = agg(c)
+                    k = len(N[x] & c)
+                    before = community_score(n, m, vol, cc)
+                    key = (n, m, vol, k)
+                    if x in c:
+                        lg.append((community_score(n - 1, m - k, vol - deg[x], cc), before, key, ci))
+                    elif k > 0:
+                        jg.append((community_score(n + 1, m + k, vol + deg[x], cc), before, key, ci))
+                acts.append((x, best(jg), best(lg)))
+            for x, j, lv in acts:   # then all of the queue's actions, a leave before a join
+                if lv >= 0:
+                    comms[lv].discard(x)
+                    nl += 1
+                if j >= 0:
+                    comms[j].add(x)
+                    nj += 1
+        comms = [c if len(c) >= 2 else set() for c in comms]   # ids stay; degenerate ones empty
+        T = total()
+        hist.append(T)
+        joins.append(nj)
+        leaves.append(nl)
+        if T_prev == 0:
+            stop = T == 0
+        else:
+            rel = (T - T_prev) / T_prev
+            if abs(rel - Fr(threshold)) <= MARGIN * max(abs(rel), 1):
+                raise Tight()
+            stop = rel < Fr(threshold)
+        T_prev = T
+        if stop:
+            break
+    final = [sorted(c) for c in comms if c]
+    return dict(T0=T0, T=hist, joins=joins, leaves=leaves, communities=final)
+
+
+def graphs():
+    rng = np.random.default_rng(2024)
+    out = []
+    for i in range(60):
+        n = int(rng.integers(5, 13))
+        p = float(rng.uniform(0.25, 0.6))
+        e = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < p]
+        if e:
+            out.append((f"gnp_{i}", e))
+    for s in range(6):
+        el = W.planted_er(n=24, num_comms=3, size_lo=6, size_hi=12, p_in=0.5, bg_frac=0.05, seed=s,
+                          sparse_ids=False)
+        out.append((f"planted_{s}", list(zip(el.src.tolist(), el.dst.tolist()))))
+    return out
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 7])
+def test_oracle_runs_equal_exact_rational_runs(oracle_lib, q):
+    decided = tight = 0
+    for name, edges in graphs():
+        try:
+            ref = exact_run(edges, q, 0.01, 12)
+        except Tight:
+            tight += 1
+            continue
+        src = np.array([a for a, _ in edges], np.int32)
+        dst = np.array([b for _, b in edges], np.int32)
+        g = oracle_lib.OracleGraph(src, dst)
+        r = g.run(q, 0.01, 12)
+        assert r["iterations"] == len(ref["T"]), name
+        assert r["joins"].tolist() == ref["joins"] and r["leaves"].tolist() == ref["leaves"], name
+        assert r["T0"] == pytest.approx(float(ref["T0"]), rel=1e-12, abs=1e-300), name
+        for got, want in zip(r["T"], ref["T"]):
+            assert got == pytest.approx(float(want), rel=1e-12, abs=1e-300), name
+        assert [c.tolist() for c in g.communities()] == ref["communities"], name
+        decided += 1
+    assert decided >= 3 * (decided + tight) // 4, (decided, tight)
