@@ -54,7 +54,7 @@ class Tight(Exception):
     """A decision within rounding distance of a tie."""
 
 
-def exact_run(edges, q, threshold, max_iters):
+def exact_run(edges, q, threshold, max_iters, cover=None):
     pairs = {(min(u, v), max(u, v)) for u, v in edges if u != v}
     ids = sorted({x for p in pairs for x in p})
     N = {v: set() for v in ids}
@@ -66,14 +66,17 @@ def exact_run(edges, q, threshold, max_iters):
     CC = {v: Fr(t[v], deg[v] * (deg[v] - 1) // 2) if deg[v] > 1 else Fr(0) for v in ids}
     cc = sum(CC.values(), Fr(0)) / len(ids)
     order = sorted(ids, key=lambda v: (-CC[v], -deg[v], v))
-    # initial clustering: a node not yet in a community opens one with its unassigned neighbours
+    # initial clustering: a node not yet in a community opens one with its
+    # unassigned neighbours; or an inserted division, community i = cover[i]
     comms, assigned = [], set()
-    for v in order:
+    for v in ([] if cover is not None else order):
         if v in assigned:
             continue
         c = {v} | {u for u in N[v] if u not in assigned}
         assigned |= c
         comms.append(c)
+    if cover is not None:
+        comms = [set(c) for c in cover]
 
     def agg(c):
         m = sum(1 for a in c for b in N[a] if b in c) // 2
@@ -173,6 +176,36 @@ def test_oracle_runs_equal_exact_rational_runs(oracle_lib, q):
         assert r["T0"] == pytest.approx(float(ref["T0"]), rel=1e-12, abs=1e-300), name
         for got, want in zip(r["T"], ref["T"]):
             assert got == pytest.approx(float(want), rel=1e-12, abs=1e-300), name
+        assert [c.tolist() for c in g.communities()] == ref["communities"], name
+        decided += 1
+    assert decided >= 3 * (decided + tight) // 4, (decided, tight)
+
+
+@pytest.mark.parametrize("q", [1, 3])
+def test_inserted_divisions_equal_exact_rational_runs(oracle_lib, q):
+    """Runs from an inserted division (overlapping, in a given order) agree
+    with the brute force started from the same division."""
+    rng = np.random.default_rng(7)
+    decided = tight = 0
+    for name, edges in graphs()[:40]:
+        nodes = sorted({x for e in edges for x in e if e[0] != e[1]})
+        cover = []
+        for _ in range(int(rng.integers(1, 5))):
+            size = int(rng.integers(1, max(2, len(nodes) // 2) + 1))
+            cover.append(sorted(int(v) for v in rng.choice(nodes, size=size, replace=False)))
+        try:
+            ref = exact_run(edges, q, 0.01, 8, cover=cover)
+        except Tight:
+            tight += 1
+            continue
+        src = np.array([a for a, _ in edges], np.int32)
+        dst = np.array([b for _, b in edges], np.int32)
+        g = oracle_lib.OracleGraph(src, dst)
+        g.set_partition([np.array(c, np.int32) for c in cover])
+        r = g.run(q, 0.01, 8)
+        assert r["iterations"] == len(ref["T"]), name
+        assert r["joins"].tolist() == ref["joins"] and r["leaves"].tolist() == ref["leaves"], name
+        assert r["T0"] == pytest.approx(float(ref["T0"]), rel=1e-12, abs=1e-300), name
         assert [c.tolist() for c in g.communities()] == ref["communities"], name
         decided += 1
     assert decided >= 3 * (decided + tight) // 4, (decided, tight)
