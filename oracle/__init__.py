@@ -77,6 +77,8 @@ def lib():
             "og_set_literal_diagnostic": (None, [_P, C.c_int]),
             "og_get_literal_diagnostic": (None, [_P, _I64P]),
             "og_get_meanfield_history": (None, [_P, _F64P, C.c_int32]),
+            "og_set_gain_rule": (C.c_int, [_P, C.c_int]),
+            "og_get_gain_rule": (C.c_int, [_P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -211,13 +213,29 @@ class OracleGraph:
         if st:
             raise ValueError(f"og_set_partition failed {st}")
 
+    GAIN_RULES = {"literal": 0, "meanfield": 1}
+
+    def set_gain_rule(self, rule: str):
+        """Decision rule of the following runs: "literal" (the paper's gain, the
+        change of \\wcchat(P)) or "meanfield" (the change of the mean-field
+        community score, a departure kept as an option)."""
+        if rule not in self.GAIN_RULES or lib().og_set_gain_rule(self._h, self.GAIN_RULES[rule]):
+            raise ValueError(f"unknown gain rule {rule!r}")
+
+    @property
+    def gain_rule(self) -> str:
+        v = lib().og_get_gain_rule(self._h)
+        return next(k for k, c in self.GAIN_RULES.items() if c == v)
+
     def set_check_invariants(self, on: bool):
         lib().og_set_check_invariants(self._h, 1 if on else 0)
 
     def invariant_failures(self) -> int:
         return lib().og_invariant_failures(self._h)
 
-    def run(self, queue_size: int, threshold: float, max_iters: int, max_batches: int = -1):
+    def run(self, queue_size: int, threshold: float, max_iters: int, max_batches: int = -1, rule=None):
+        if rule is not None:
+            self.set_gain_rule(rule)
         st = lib().og_run(self._h, int(queue_size), float(threshold), int(max_iters), int(max_batches))
         if st:
             raise ValueError(f"og_run failed {st}")

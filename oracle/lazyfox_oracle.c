@@ -21,10 +21,16 @@
  *     rationals, then degree descending, then dense id ascending (Node Order);
  *   - cc = correctly rounded sum of the rounded local CCs over all n nodes,
  *     divided by n (Heuristic Counting of Triangles, global cc);
- *   - the gain of a join or leave is the change of the community's
- *     mean-field score S(n, m, vol): every member is given the community's
- *     mean internal degree 2m/n and mean total degree vol/n in the per-node
- *     estimator (Heuristic Counting of Triangles + Joining/Leaving);
+ *   - the gain of a join or leave is, as the paper defines it (Node Changes:
+ *     Joining / Leaving a Community), the improvement of \wcchat(P') over
+ *     \wcchat(P), the sums of the per-node estimator over all memberships
+ *     (\wcchat, sum equations): the moved community's members' terms after
+ *     the move (new size, new internal edge count, and for x's neighbours
+ *     their deg(y,C) changed by one) and x's own term, less the same
+ *     community's terms before it, added with the correctly rounded sum
+ *     (OG_GAIN_LITERAL).  A departure kept as an option (OG_GAIN_MEANFIELD):
+ *     the change of the community's mean-field score S(n, m, vol), every
+ *     member given the mean internal degree 2m/n and mean total degree vol/n;
  *   - B(z) = C(z,2) for z >= 1, else 0;
  *   - "positive improvement" is strictly > 0; ties go to the lowest id;
  *   - a node may both leave and join in one step (leave applied first) and
@@ -50,6 +56,10 @@
 #define OG_ERR_OOM 2
 #define OG_ERR_STATE 6
 
+/* decision rule of a move (see the readings above) */
+#define OG_GAIN_LITERAL 0
+#define OG_GAIN_MEANFIELD 1
+
 typedef struct og_graph {
     int64_t n, m;          /* nodes, undirected simple edges */
     int32_t *labels;       /* dense id -> original id (ascending) */
@@ -65,6 +75,10 @@ typedef struct og_graph {
     int64_t *cn, *cm, *cvol; /* members, internal edges, sum of member degrees */
     int32_t **mem;         /* per node: ascending community ids */
     int32_t *nmem, *capmem;
+    int32_t **kin;         /* per node, beside mem: deg(x,C) = |N(x) & C| of each membership */
+    int32_t **cmem;        /* per community: ascending member ids (the same memberships) */
+    int32_t *ncmem, *capcmem;
+    int gain_rule;         /* OG_GAIN_LITERAL or OG_GAIN_MEANFIELD */
     /* last run */
     int32_t iterations;
     int32_t converged;
@@ -178,6 +192,7 @@ og_graph *og_create(const int32_t *src, const int32_t *dst, int64_t num_edges, i
     og_graph *g = (og_graph *)calloc(1, sizeof(og_graph));
     if (!g) { *status = OG_ERR_OOM; return NULL; }
     g->part_k = -1;
+    g->gain_rule = OG_GAIN_MEANFIELD;
     for (int64_t e = 0; e < num_edges; ++e) {
         if (src[e] < 0 || dst[e] < 0) { *status = OG_ERR_INVALID; free(g); return NULL; }
     }
@@ -438,24 +453,75 @@ static int mem_has(const og_graph *g, int64_t y, int32_t c)
     return bsearch(&c, g->mem[y], (size_t)g->nmem[y], sizeof(int32_t), cmp_i32) != NULL;
 }
 
+/* insert v into the ascending list (*list, *cnt) of capacity *cap */
+static void list_insert(int32_t **list, int32_t *cnt, int32_t *cap, int32_t v)
+{
+    if (*cnt == *cap) {
+        *cap = *cap ? 2 * *cap : 4;
+        *list = (int32_t *)realloc(*list, (size_t)*cap * sizeof(int32_t));
+    }
+    int32_t i = *cnt;
+    while (i > 0 && (*list)[i - 1] > v) { (*list)[i] = (*list)[i - 1]; --i; }
+    (*list)[i] = v;
+    (*cnt)++;
+}
+
+static void list_remove(int32_t *list, int32_t *cnt, int32_t v)
+{
+    int32_t j = 0;
+    for (int32_t i = 0; i < *cnt; ++i)
+        if (list[i] != v) list[j++] = list[i];
+    *cnt = j;
+}
+
+/* position of c in x's row, -1 if x is not a member */
+static int32_t mem_slot(const og_graph *g, int64_t x, int32_t c)
+{
+    const int32_t *hit = (const int32_t *)bsearch(&c, g->mem[x], (size_t)g->nmem[x], sizeof(int32_t), cmp_i32);
+    return hit ? (int32_t)(hit - g->mem[x]) : -1;
+}
+
+/* x becomes a member of c: c enters x's row (with deg(x,c) counted), x
+ * enters c's member list, and every neighbour of x in c has one more
+ * neighbour in c. */
 static void mem_insert(og_graph *g, int64_t x, int32_t c)
 {
+    int32_t k = 0;
+    for (int64_t p = g->off[x]; p < g->off[x + 1]; ++p) {
+        int32_t y = g->adj[p];
+        int32_t s = mem_slot(g, y, c);
+        if (s >= 0) { g->kin[y][s]++; ++k; }
+    }
     if (g->nmem[x] == g->capmem[x]) {
         g->capmem[x] = g->capmem[x] ? 2 * g->capmem[x] : 4;
         g->mem[x] = (int32_t *)realloc(g->mem[x], (size_t)g->capmem[x] * sizeof(int32_t));
+        g->kin[x] = (int32_t *)realloc(g->kin[x], (size_t)g->capmem[x] * sizeof(int32_t));
     }
     int32_t i = g->nmem[x];
-    while (i > 0 && g->mem[x][i - 1] > c) { g->mem[x][i] = g->mem[x][i - 1]; --i; }
+    while (i > 0 && g->mem[x][i - 1] > c) {
+        g->mem[x][i] = g->mem[x][i - 1];
+        g->kin[x][i] = g->kin[x][i - 1];
+        --i;
+    }
     g->mem[x][i] = c;
+    g->kin[x][i] = k;
     g->nmem[x]++;
+    list_insert(&g->cmem[c], &g->ncmem[c], &g->capcmem[c], (int32_t)x);
 }
 
+/* x stops being a member of c: the reverse of mem_insert */
 static void mem_remove(og_graph *g, int64_t x, int32_t c)
 {
     int32_t j = 0;
     for (int32_t i = 0; i < g->nmem[x]; ++i)
-        if (g->mem[x][i] != c) g->mem[x][j++] = g->mem[x][i];
+        if (g->mem[x][i] != c) { g->mem[x][j] = g->mem[x][i]; g->kin[x][j] = g->kin[x][i]; ++j; }
     g->nmem[x] = j;
+    list_remove(g->cmem[c], &g->ncmem[c], (int32_t)x);
+    for (int64_t p = g->off[x]; p < g->off[x + 1]; ++p) {
+        int32_t y = g->adj[p];
+        int32_t s = mem_slot(g, y, c);
+        if (s >= 0) g->kin[y][s]--;
+    }
 }
 
 /* |N(x) \cap C| in the current state */
@@ -469,11 +535,32 @@ static int64_t neighbours_in(const og_graph *g, int64_t x, int32_t c)
 
 static void free_state(og_graph *g)
 {
-    if (g->mem) for (int64_t x = 0; x < g->n; ++x) free(g->mem[x]);
-    free(g->mem); free(g->nmem); free(g->capmem);
+    if (g->mem) for (int64_t x = 0; x < g->n; ++x) { free(g->mem[x]); free(g->kin[x]); }
+    if (g->cmem) for (int64_t c = 0; c < g->ncomm; ++c) free(g->cmem[c]);
+    free(g->mem); free(g->kin); free(g->nmem); free(g->capmem);
+    g->kin = NULL;
+    free(g->cmem); free(g->ncmem); free(g->capcmem);
     free(g->cn); free(g->cm); free(g->cvol);
     g->mem = NULL; g->nmem = g->capmem = NULL; g->cn = g->cm = g->cvol = NULL;
+    g->cmem = NULL; g->ncmem = g->capcmem = NULL;
     g->ncomm = 0;
+}
+
+/* empty rows for n nodes and empty member lists for k communities */
+static void alloc_state(og_graph *g, int64_t k)
+{
+    int64_t n = g->n;
+    g->mem = (int32_t **)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t *));
+    g->kin = (int32_t **)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t *));
+    g->nmem = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    g->capmem = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    g->ncomm = k;
+    g->cmem = (int32_t **)calloc((size_t)(k > 0 ? k : 1), sizeof(int32_t *));
+    g->ncmem = (int32_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int32_t));
+    g->capcmem = (int32_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int32_t));
+    g->cn = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
+    g->cm = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
+    g->cvol = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
 }
 
 /* Initial clustering: walk the node order; a node not yet in a community
@@ -484,9 +571,6 @@ int og_init_clustering(og_graph *g)
     if (!g->order) return OG_ERR_STATE;
     free_state(g);
     int64_t n = g->n;
-    g->mem = (int32_t **)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t *));
-    g->nmem = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
-    g->capmem = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
     int32_t *comm = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
     for (int64_t x = 0; x < n; ++x) comm[x] = -1;
     int32_t k = 0;
@@ -498,10 +582,7 @@ int og_init_clustering(og_graph *g)
             if (comm[g->adj[p]] < 0) comm[g->adj[p]] = k;
         ++k;
     }
-    g->ncomm = k;
-    g->cn = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
-    g->cm = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
-    g->cvol = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
+    alloc_state(g, k);
     for (int64_t x = 0; x < n; ++x) {
         mem_insert(g, x, comm[x]);
         g->cn[comm[x]]++;
@@ -521,13 +602,7 @@ static int init_from_partition(og_graph *g)
 {
     free_state(g);
     int64_t n = g->n, k = g->part_k;
-    g->mem = (int32_t **)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t *));
-    g->nmem = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
-    g->capmem = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
-    g->ncomm = k;
-    g->cn = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
-    g->cm = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
-    g->cvol = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
+    alloc_state(g, k);
     for (int64_t c = 0; c < k; ++c)
         for (int64_t i = g->part_off[c]; i < g->part_off[c + 1]; ++i) {
             int32_t x = g->part_mem[i];
@@ -653,14 +728,14 @@ static og_action evaluate_node(const og_graph *g, int32_t x)
     return a;
 }
 
-/* Diagnostic of the gain reading (not used for any decision).  The literal
- * gain of a move (Joining / Leaving a Community) is the change of \wcchat(P)
- * -- the sum of the per-node estimator over all memberships -- when x alone
- * enters (joining != 0) or leaves community c and every other membership
- * stays: C's members see n_C, m_C and, for neighbours of x, deg(y,C) change,
- * and x's own term appears or disappears; no other term changes.  The terms
- * after the move and the negated terms before it are added with the
- * correctly rounded sum.  Costs O(n + |C| deg) per candidate: small graphs. */
+/* The paper's gain of a move (Joining / Leaving a Community): the change of
+ * \wcchat(P) -- the sum of the per-node estimator over all memberships --
+ * when x alone enters (joining != 0) or leaves community c and every other
+ * membership stays: C's members see n_C, m_C and, for neighbours of x,
+ * deg(y,C) change, and x's own term appears or disappears; no other term
+ * changes.  The terms after the move and the negated terms before it are
+ * added with the correctly rounded sum.  Costs O(sum of the members'
+ * degrees) per candidate. */
 static double literal_gain(const og_graph *g, int32_t x, int32_t c, int joining)
 {
     int64_t d = deg(g, x);
@@ -670,9 +745,10 @@ static double literal_gain(const og_graph *g, int32_t x, int32_t c, int joining)
     int64_t m1 = joining ? m0 + kx : m0 - kx;
     double *terms = (double *)malloc((size_t)(2 * n0 + 2) * sizeof(double));
     int64_t t = 0;
-    for (int64_t y = 0; y < g->n; ++y) {
-        if (y == x || !mem_has(g, y, c)) continue;
-        int64_t ky = neighbours_in(g, y, c);
+    for (int32_t i = 0; i < g->ncmem[c]; ++i) {
+        int64_t y = g->cmem[c][i];
+        if (y == x) continue;
+        int64_t ky = g->kin[y][mem_slot(g, y, c)];
         int64_t ky1 = ky;
         if (find_in_row(g, y, x) >= 0) ky1 += joining ? 1 : -1;
         terms[t++] = og_wcchat_node(ky1, deg(g, y), n1, m1, g->cc);
@@ -685,10 +761,10 @@ static double literal_gain(const og_graph *g, int32_t x, int32_t c, int joining)
     return gain;
 }
 
-/* The decision of evaluate_node with the literal gains in place of the
- * mean-field ones: the same candidates (communities met among the
- * neighbours to join, own communities to leave), the best strictly
- * positive gain of each kind, ties to the lowest id. */
+/* A node's decision with the paper's gains: the candidates are the
+ * communities met among the neighbours that x is not in (joins) and x's own
+ * communities (leaves); per kind the best strictly positive gain, ties to
+ * the lowest id (Algorithm 1 body). */
 static og_action evaluate_node_literal(const og_graph *g, int32_t x)
 {
     og_action a = { -1, -1, 0, 0, 0.0, 0.0 };
@@ -741,7 +817,8 @@ static void apply_actions(og_graph *g, int32_t x, og_action a)
     }
 }
 
-/* Full recount of every community aggregate from the memberships. */
+/* Full recount of every community aggregate, of the member lists and of
+ * each membership's deg(x,C) from the rows. */
 static int recount_ok(const og_graph *g)
 {
     int64_t k = g->ncomm;
@@ -755,10 +832,16 @@ static int recount_ok(const og_graph *g)
             if (j > 0 && g->mem[x][j - 1] >= c) ok = 0;
             n[c]++;
             vol[c] += deg(g, x);
-            m2[c] += neighbours_in(g, x, c);
+            int64_t kx = neighbours_in(g, x, c);
+            m2[c] += kx;
+            if (g->kin[x][j] != kx) ok = 0;
         }
-    for (int64_t c = 0; c < k; ++c)
+    for (int64_t c = 0; c < k; ++c) {
         if (n[c] != g->cn[c] || vol[c] != g->cvol[c] || m2[c] != 2 * g->cm[c]) ok = 0;
+        if (g->ncmem[c] != n[c]) ok = 0;
+        for (int32_t i = 0; i < g->ncmem[c]; ++i)
+            if ((i > 0 && g->cmem[c][i - 1] >= g->cmem[c][i]) || !mem_has(g, g->cmem[c][i], (int32_t)c)) ok = 0;
+    }
     free(n); free(m2); free(vol);
     return ok;
 }
@@ -769,11 +852,11 @@ static void prune(og_graph *g)
     for (int64_t x = 0; x < g->n; ++x) {
         int32_t j = 0;
         for (int32_t i = 0; i < g->nmem[x]; ++i)
-            if (g->cn[g->mem[x][i]] >= 2) g->mem[x][j++] = g->mem[x][i];
+            if (g->cn[g->mem[x][i]] >= 2) { g->mem[x][j] = g->mem[x][i]; g->kin[x][j] = g->kin[x][i]; ++j; }
         g->nmem[x] = j;
     }
     for (int64_t c = 0; c < g->ncomm; ++c)
-        if (g->cn[c] < 2) { g->cn[c] = 0; g->cm[c] = 0; g->cvol[c] = 0; }
+        if (g->cn[c] < 2) { g->cn[c] = 0; g->cm[c] = 0; g->cvol[c] = 0; g->ncmem[c] = 0; }
 }
 
 /*
@@ -811,18 +894,21 @@ int og_run(og_graph *g, int32_t queue_size, double threshold, int32_t max_iters,
             if (max_batches >= 0 && batches >= max_batches) { free(acts); return OG_OK; }
             int64_t end = start + queue_size < g->n ? start + queue_size : g->n;
             for (int64_t i = start; i < end; ++i) {
-                acts[i - start] = evaluate_node(g, g->order[i]);
+                int32_t x = g->order[i];
+                og_action lit = { -1, -1, 0, 0, 0.0, 0.0 }, mf = lit;
+                if (g->gain_rule == OG_GAIN_LITERAL || g->literal_diag) lit = evaluate_node_literal(g, x);
+                if (g->gain_rule == OG_GAIN_MEANFIELD || g->literal_diag) mf = evaluate_node(g, x);
+                acts[i - start] = g->gain_rule == OG_GAIN_LITERAL ? lit : mf;
                 if (g->literal_diag) {
                     /* same snapshot: nothing of this queue is applied yet */
-                    og_action lit = evaluate_node_literal(g, g->order[i]);
-                    int same_j = lit.join == acts[i - start].join, same_l = lit.leave == acts[i - start].leave;
+                    int same_j = lit.join == mf.join, same_l = lit.leave == mf.leave;
                     g->diag[0]++;
                     g->diag[1] += same_j;
                     g->diag[2] += same_l;
                     g->diag[3] += same_j && same_l;
-                    g->diag[4] += acts[i - start].join >= 0;
+                    g->diag[4] += mf.join >= 0;
                     g->diag[5] += lit.join >= 0;
-                    g->diag[6] += acts[i - start].leave >= 0;
+                    g->diag[6] += mf.leave >= 0;
                     g->diag[7] += lit.leave >= 0;
                 }
             }
@@ -1023,7 +1109,18 @@ void og_evaluate_literal(const og_graph *g, int32_t x, int32_t *join, int32_t *l
     *join = a.join; *leave = a.leave; *gjoin = a.gjoin; *gleave = a.gleave;
 }
 
-/* on != 0: the following runs compare every decision with the literal one.
+/* Decision rule of the following runs: OG_GAIN_LITERAL (the paper's gain,
+ * the default) or OG_GAIN_MEANFIELD (the mean-field departure). */
+int og_set_gain_rule(og_graph *g, int rule)
+{
+    if (rule != OG_GAIN_LITERAL && rule != OG_GAIN_MEANFIELD) return OG_ERR_INVALID;
+    g->gain_rule = rule;
+    return OG_OK;
+}
+int og_get_gain_rule(const og_graph *g) { return g->gain_rule; }
+
+/* on != 0: the following runs take every decision with both rules and count
+ * agreement (the rule set by og_set_gain_rule decides).
  * Counts of the last run: evaluations, equal join decisions, equal leave
  * decisions, both equal, mean-field joins, literal joins, mean-field leaves,
  * literal leaves. */

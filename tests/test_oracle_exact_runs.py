@@ -1,4 +1,4 @@
-"""Whole runs of the oracle against an exact-rational brute force.
+r"""Whole runs of the oracle against an exact-rational brute force.
 
 The brute force below is written from the paper's definitions alone, in exact
 rational arithmetic, with none of the oracle's data structures: simple sets
@@ -6,8 +6,11 @@ for the graph and the communities, triangles by enumeration, every aggregate
 recounted from the member sets (Methods: Preprocessing, Node Order, Heuristic
 Counting of Triangles, Initial Clustering, Node Changes with Algorithm 1,
 Parallelism on Node Change Computations with Algorithm 2, Stopping Criteria,
-Post-processing; the gain of a move is the change of the community's
-mean-field score, as in the oracle).  On tiny graphs it gives the runs exactly,
+Post-processing).  The gain of a move is either the paper's -- the change of
+\wcchat(P), formed by moving the node in a copy of the member sets and
+summing the estimator over the changed community before and after -- or the
+mean-field departure (the change of the community's mean-field score), as
+the oracle's rule is set.  On tiny graphs it gives the runs exactly,
 so the oracle's FP64 runs must agree with it wherever no decision is within
 rounding distance of a tie: a candidate's gain next to 0, two best gains next
 to each other, or the relative change next to the threshold.  Such graphs are
@@ -54,7 +57,7 @@ class Tight(Exception):
     """A decision within rounding distance of a tie."""
 
 
-def exact_run(edges, q, threshold, max_iters, cover=None):
+def exact_run(edges, q, threshold, max_iters, cover=None, rule="literal"):
     pairs = {(min(u, v), max(u, v)) for u, v in edges if u != v}
     ids = sorted({x for p in pairs for x in p})
     N = {v: set() for v in ids}
@@ -85,6 +88,13 @@ def exact_run(edges, q, threshold, max_iters, cover=None):
     def total():
         return sum((member_score(len(N[x] & c), deg[x], *agg(c)[:2], cc) for c in comms for x in c), Fr(0))
 
+    def wcchat_of(c):
+        r"""\wcchat(C) = sum of the members' estimators, and the inputs that fix
+        its FP64 terms (equal inputs give equal doubles)."""
+        n, m, _ = agg(c)
+        ks = tuple(sorted((len(N[y] & c), deg[y]) for y in c))
+        return sum((member_score(k, d, n, m, cc) for k, d in ks), Fr(0)), (ks, n, m)
+
     def best(gains):
         """gains: (after, before, inputs, community).  FP64 evaluates equal
         inputs to equal values and two zero scores to a zero gain, so only
@@ -107,14 +117,22 @@ def exact_run(edges, q, threshold, max_iters, cover=None):
             for x in order[s:s + q]:   # every queued node sees the partition as the queue found it
                 jg, lg = [], []
                 for ci, c in enumerate(comms):
-                    n, m, vol = agg(c)
                     k = len(N[x] & c)
-                    before = community_score(n, m, vol, cc)
-                    key = (n, m, vol, k)
-                    if x in c:
-                        lg.append((community_score(n - 1, m - k, vol - deg[x], cc), before, key, ci))
-                    elif k > 0:
-                        jg.append((community_score(n + 1, m + k, vol + deg[x], cc), before, key, ci))
+                    if x not in c and k == 0:
+                        continue
+                    if rule == "literal":
+                        # P' differs from P in community c only: \wcchat(P') - \wcchat(P)
+                        # = \wcchat(c after the move) - \wcchat(c)
+                        before, kb = wcchat_of(c)
+                        after, ka = wcchat_of(c - {x} if x in c else c | {x})
+                        key = (ka, kb)
+                    else:
+                        n, m, vol = agg(c)
+                        before = community_score(n, m, vol, cc)
+                        key = (n, m, vol, k)
+                        after = (community_score(n - 1, m - k, vol - deg[x], cc) if x in c
+                                 else community_score(n + 1, m + k, vol + deg[x], cc))
+                    (lg if x in c else jg).append((after, before, key, ci))
                 acts.append((x, best(jg), best(lg)))
             for x, j, lv in acts:   # then all of the queue's actions, a leave before a join
                 if lv >= 0:
@@ -158,19 +176,20 @@ def graphs():
     return out
 
 
+@pytest.mark.parametrize("rule", ["literal", "meanfield"])
 @pytest.mark.parametrize("q", [1, 2, 3, 7])
-def test_oracle_runs_equal_exact_rational_runs(oracle_lib, q):
+def test_oracle_runs_equal_exact_rational_runs(oracle_lib, q, rule):
     decided = tight = 0
     for name, edges in graphs():
         try:
-            ref = exact_run(edges, q, 0.01, 12)
+            ref = exact_run(edges, q, 0.01, 12, rule=rule)
         except Tight:
             tight += 1
             continue
         src = np.array([a for a, _ in edges], np.int32)
         dst = np.array([b for _, b in edges], np.int32)
         g = oracle_lib.OracleGraph(src, dst)
-        r = g.run(q, 0.01, 12)
+        r = g.run(q, 0.01, 12, rule=rule)
         assert r["iterations"] == len(ref["T"]), name
         assert r["joins"].tolist() == ref["joins"] and r["leaves"].tolist() == ref["leaves"], name
         assert r["T0"] == pytest.approx(float(ref["T0"]), rel=1e-12, abs=1e-300), name
@@ -181,8 +200,9 @@ def test_oracle_runs_equal_exact_rational_runs(oracle_lib, q):
     assert decided >= 3 * (decided + tight) // 4, (decided, tight)
 
 
+@pytest.mark.parametrize("rule", ["literal", "meanfield"])
 @pytest.mark.parametrize("q", [1, 3])
-def test_inserted_divisions_equal_exact_rational_runs(oracle_lib, q):
+def test_inserted_divisions_equal_exact_rational_runs(oracle_lib, q, rule):
     """Runs from an inserted division (overlapping, in a given order) agree
     with the brute force started from the same division."""
     rng = np.random.default_rng(7)
@@ -194,7 +214,7 @@ def test_inserted_divisions_equal_exact_rational_runs(oracle_lib, q):
             size = int(rng.integers(1, max(2, len(nodes) // 2) + 1))
             cover.append(sorted(int(v) for v in rng.choice(nodes, size=size, replace=False)))
         try:
-            ref = exact_run(edges, q, 0.01, 8, cover=cover)
+            ref = exact_run(edges, q, 0.01, 8, cover=cover, rule=rule)
         except Tight:
             tight += 1
             continue
@@ -202,7 +222,7 @@ def test_inserted_divisions_equal_exact_rational_runs(oracle_lib, q):
         dst = np.array([b for _, b in edges], np.int32)
         g = oracle_lib.OracleGraph(src, dst)
         g.set_partition([np.array(c, np.int32) for c in cover])
-        r = g.run(q, 0.01, 8)
+        r = g.run(q, 0.01, 8, rule=rule)
         assert r["iterations"] == len(ref["T"]), name
         assert r["joins"].tolist() == ref["joins"] and r["leaves"].tolist() == ref["leaves"], name
         assert r["T0"] == pytest.approx(float(ref["T0"]), rel=1e-12, abs=1e-300), name

@@ -203,7 +203,7 @@ def test_disjoint_cliques_initial_clustering(oracle_lib):
     assert got == sorted([list(range(0, 5)), list(range(10, 14)), list(range(20, 27))])
 
 
-@pytest.mark.parametrize("name", ["bowtie", "k4_pendant", "path5"])
+@pytest.mark.parametrize("name", ["bowtie", "k4_pendant", "path5", "triangle_tail"])
 def test_golden_preprocessing(oracle_lib, name):
     fx = json.load(open(os.path.join(GOLDEN, name + ".json")))
     el = W.from_pairs(fx["edges"])

@@ -101,25 +101,30 @@ def test_invalid_divisions_are_rejected(oracle_lib):
     assert np.array_equal(a["T"], b["T"])
 
 
-def test_golden_leave_from_an_inserted_division(oracle_lib):
+@pytest.mark.parametrize("rule", ["literal", "meanfield"])
+def test_golden_leave_from_an_inserted_division(oracle_lib, rule):
     """A hand-derived run with a leave (tests/golden/pendant_leave.json): the
     pendant node of an inserted division leaves it, and the mean-field and
-    literal gains of that leave have the hand values."""
+    literal gains of the start's moves have the hand values; the run is the
+    same under both rules."""
     import json
     import os
     from fractions import Fraction
     fx = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "pendant_leave.json")))
+    assert rule in fx["gain_rules"]
     el = W.from_pairs(fx["edges"])
     g = oracle_lib.OracleGraph(el.src, el.dst)
     assert g.cc == pytest.approx(float(Fraction(fx["cc"])), rel=2 ** -52)
     g.set_partition([np.array(c, np.int32) for c in fx["partition"]])
-    g.run(fx["queue_size"], fx["threshold"], 0)
+    g.run(fx["queue_size"], fx["threshold"], 0, rule="meanfield")
     eps = 2.0 ** -52
     ev = g.evaluate(3)
     assert ev["leave"] == 0 and ev["join"] == -1 and ev["kleave"] == 1
     assert abs(ev["gleave"] - float(Fraction(fx["leave_gain_node3"]))) <= 8 * eps * 64 / 21
     assert abs(g.literal_gain(3, 0) - float(Fraction(fx["literal_leave_gain_node3"]))) <= 8 * eps * 4
-    r = g.run(fx["queue_size"], fx["threshold"], fx["max_iters"])
+    for x, c, want in fx["literal_gains_at_start"]:
+        assert abs(g.literal_gain(x, c) - float(Fraction(want))) <= 16 * eps * 4, (x, c)
+    r = g.run(fx["queue_size"], fx["threshold"], fx["max_iters"], rule=rule)
     assert r["T0"] == pytest.approx(float(Fraction(fx["T0"])), rel=1e-14)
     assert r["iterations"] == fx["iterations"] and r["converged"]
     for got, want in zip(r["T"], fx["T"]):

@@ -1,7 +1,8 @@
 """Pins of the oracle's Fox / LazyFox iteration: hand-derived runs, recount
 invariants after every queue, brute-force candidate enumeration, the
 equivalence of LazyFox and Fox when a queue's nodes cannot interact, and the
-stopping criterion.
+stopping criterion -- under the paper's gain (the change of WCC-hat(P)) and
+under the mean-field departure.
 
 Paper passages: Node Changes (Joining / Leaving a Community, Algorithm 1),
 Parallelism on Node Change Computations (Algorithm 2), Stopping Criteria,
@@ -20,12 +21,25 @@ from paper_2210_03211_gb300 import workloads as W
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-@pytest.mark.parametrize("name", ["bowtie", "k4_pendant", "path5"])
-def test_golden_runs(oracle_lib, name):
+GOLDEN_RUNS = [(name, rule) for name in ["bowtie", "k4_pendant", "path5", "triangle_tail"]
+               for rule in json.load(open(os.path.join(GOLDEN, name + ".json")))["gain_rules"]]
+RULES = ["literal", "meanfield"]
+
+
+@pytest.mark.parametrize("name,rule", GOLDEN_RUNS)
+def test_golden_runs(oracle_lib, name, rule):
+    """Hand-derived runs under the gain rule(s) each fixture was derived for;
+    for the paper's rule also the literal gains of moves from the initial
+    clustering."""
     fx = json.load(open(os.path.join(GOLDEN, name + ".json")))
     el = W.from_pairs(fx["edges"])
     g = oracle_lib.OracleGraph(el.src, el.dst)
-    r = g.run(fx["queue_size"], fx["threshold"], fx["max_iters"])
+    if rule == "literal":
+        g.run(1, 0.01, 0)
+        for x, c, want in fx["literal_gains_at_start"]:
+            want = float(Fraction(want))
+            assert abs(g.literal_gain(x, c) - want) <= 2.0 ** -48 * max(1.0, float(Fraction(fx["T0"]))), (x, c)
+    r = g.run(fx["queue_size"], fx["threshold"], fx["max_iters"], rule=rule)
     assert r["T0"] == pytest.approx(float(Fraction(fx["T0"])), rel=1e-14, abs=1e-300)
     assert r["iterations"] == fx["iterations"]
     assert r["converged"]
@@ -49,10 +63,11 @@ def test_disjoint_cliques_converge_without_moves(oracle_lib):
         off += s + 2
     el = W.from_pairs(pairs)
     g = oracle_lib.OracleGraph(el.src, el.dst)
-    r = g.run(1, 0.01, 50)
-    assert r["T0"] == sum(sizes)
-    assert r["iterations"] == 1 and r["joins"][0] == 0 and r["leaves"][0] == 0
-    assert r["T"][0] == sum(sizes)
+    for rule in RULES:
+        r = g.run(1, 0.01, 50, rule=rule)
+        assert r["T0"] == sum(sizes)
+        assert r["iterations"] == 1 and r["joins"][0] == 0 and r["leaves"][0] == 0
+        assert r["T"][0] == sum(sizes)
 
 
 def recount(g, st):
@@ -72,12 +87,15 @@ def recount(g, st):
     return n, m2 // 2, vol
 
 
+@pytest.mark.parametrize("rule", RULES)
 @pytest.mark.parametrize("q", [1, 3, 64, 1000])
-def test_aggregates_equal_recounts_after_every_queue(oracle_lib, q):
-    el = W.eu_core_like()
+def test_aggregates_equal_recounts_after_every_queue(oracle_lib, q, rule):
+    """After every queue: n_C, m_C, vol_C, the member lists and each
+    membership's deg(x,C) equal a recount from the rows."""
+    el = W.eu_core_like() if rule == "meanfield" or q > 1 else W.planted_er(n=300, num_comms=10, seed=3)
     g = oracle_lib.OracleGraph(el.src, el.dst)
     g.set_check_invariants(True)
-    g.run(q, 0.01, 2)
+    g.run(q, 0.01, 2, rule=rule)
     assert g.invariant_failures() == 0
     # and the python recount of the final state agrees
     st = g.state()
@@ -94,7 +112,7 @@ def test_candidates_and_choice_by_brute_force(oracle_lib):
     a strictly larger gain (or an equal gain and a lower id)."""
     el = W.eu_core_like()
     g = oracle_lib.OracleGraph(el.src, el.dst)
-    g.run(16, 0.01, 1, max_batches=30)
+    g.run(16, 0.01, 1, max_batches=30, rule="meanfield")
     st = g.state()
     off, adj, _ = g.csr()
     cc = g.cc
@@ -135,34 +153,37 @@ def interleaved_components(copies: int, pairs):
     return W.from_pairs(out)
 
 
-def test_lazyfox_equals_fox_when_queue_nodes_cannot_interact(oracle_lib):
+@pytest.mark.parametrize("rule", RULES)
+def test_lazyfox_equals_fox_when_queue_nodes_cannot_interact(oracle_lib, rule):
     """If no two nodes of a queue share a neighbouring or own community, the
     bulk apply of Algorithm 2 changes nothing against Algorithm 1: with the
     queue size equal to the number of identical, disjoint, interleaved copies,
     each queue holds one node per copy, so LazyFox(q) must equal Fox."""
-    base = W.eu_core_like(seed=5)
+    base = W.eu_core_like(seed=5) if rule == "meanfield" else W.planted_er(n=200, num_comms=8, seed=5)
     bg = oracle_lib.OracleGraph(base.src, base.dst, prepare=False)
     off, adj, _ = bg.csr()
     pairs = [(x, int(y)) for x in range(bg.n) for y in adj[off[x]:off[x + 1]] if y > x]
     copies = 4
     el = interleaved_components(copies, pairs)
     g = oracle_lib.OracleGraph(el.src, el.dst)
-    lazy = g.run(copies, 0.01, 6)
+    lazy = g.run(copies, 0.01, 6, rule=rule)
     lazy_comms = [c.tolist() for c in g.communities()]
-    fox = g.run(1, 0.01, 6)
+    fox = g.run(1, 0.01, 6, rule=rule)
     fox_comms = [c.tolist() for c in g.communities()]
     assert lazy["iterations"] == fox["iterations"]
     assert np.array_equal(lazy["T"], fox["T"])
     assert lazy_comms == fox_comms
     # and the copies are identical to each other: each result is the base result
     single = oracle_lib.OracleGraph(base.src, base.dst)
-    sr = single.run(1, 0.01, 6)
+    sr = single.run(1, 0.01, 6, rule=rule)
     assert np.allclose(fox["T"], copies * sr["T"], rtol=1e-12)
 
 
-def test_stopping_criterion(oracle_lib):
-    el = W.eu_core_like()
+@pytest.mark.parametrize("rule", RULES)
+def test_stopping_criterion(oracle_lib, rule):
+    el = W.eu_core_like() if rule == "meanfield" else W.planted_er(n=300, num_comms=10, seed=3)
     g = oracle_lib.OracleGraph(el.src, el.dst)
+    g.set_gain_rule(rule)
     r = g.run(8, -math.inf, 5)
     assert r["iterations"] == 5 and not r["converged"]
     r = g.run(8, math.inf, 5)
@@ -181,10 +202,11 @@ def test_stopping_criterion(oracle_lib):
         prev = T
 
 
-def test_membership_counts_grow_at_most_one_per_iteration(oracle_lib):
-    el = W.eu_core_like()
+@pytest.mark.parametrize("rule", RULES)
+def test_membership_counts_grow_at_most_one_per_iteration(oracle_lib, rule):
+    el = W.eu_core_like() if rule == "meanfield" else W.planted_er(n=300, num_comms=10, seed=3)
     g = oracle_lib.OracleGraph(el.src, el.dst)
     for it in range(1, 6):
-        g.run(32, -math.inf, it)
+        g.run(32, -math.inf, it, rule=rule)
         st = g.state()
         assert np.max(np.diff(st["mem_off"])) <= 1 + it
