@@ -86,7 +86,19 @@ typedef struct lf_options {
     int32_t hub_degree;      /* nodes of higher degree are evaluated with a table in global
                                 memory, in blocks of their own (per-queue launches: on a second
                                 stream); 0 (default) = 384 */
+    int32_t gain_rule;       /* decision rule of a move (LF_GAIN_*); 0: the library default */
 } lf_options;
+
+/* lf_options.gain_rule.  LF_GAIN_LITERAL is the paper's gain (Methods, Node
+ * Changes: Joining / Leaving a Community): the improvement of WCC-hat(P') over
+ * WCC-hat(P), the sums of the per-node estimator over all memberships, i.e.
+ * the changed community's members' terms (new size and internal edge count,
+ * and for the node's neighbours deg(y,C) changed by one) and the node's own
+ * term, summed exactly and rounded once.  LF_GAIN_MEANFIELD is a departure
+ * kept as an option: the change of the community's mean-field score, every
+ * member given the mean internal degree 2m/n and mean degree vol/n. */
+#define LF_GAIN_LITERAL 1
+#define LF_GAIN_MEANFIELD 2
 
 /* Per-run statistics.  The history pointers are optional caller buffers with
  * `history_cap` entries each (NULL to skip). */

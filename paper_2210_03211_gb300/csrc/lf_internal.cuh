@@ -106,6 +106,7 @@ struct lf_graph {
     int32_t barrier_mode = 0;                      // grid barrier: 0 flat flags, 1 central release flag
     int32_t warps_per_node = 0;                    // team size of the move evaluation (0: by queue size)
     int32_t hub_degree = 384;                      // above it a node takes the hub path
+    int32_t gain_rule = LF_GAIN_MEANFIELD;         // decision rule of the move evaluation
     unsigned long long launches = 0;               // kernels launched (host count)
     std::vector<std::pair<void *, size_t>> live;   // outstanding allocations
 
@@ -223,6 +224,25 @@ struct lf_graph {
     int32_t *dyn_list = nullptr;
     long long *dyn_bound = nullptr;
     int64_t dyn_list_cap = 0;
+    // the paper's gain (gain_rule == LF_GAIN_LITERAL): deg(x,C) beside each
+    // membership, the member index of the current iteration (members at its
+    // start, by community; its joiners as per-community lists), per-community
+    // sums F(n-1), F(n), F(n+1), per-queue counters (overflow count, overflow
+    // next, touched count), the overflow list, the touched list and stamps
+    int32_t *kmem = nullptr;              // n*K
+    unsigned long long *cm_off = nullptr; // n+1
+    unsigned long long *cm_cur = nullptr; // n+1
+    int32_t *cm_node = nullptr;           // n*K
+    int64_t cm_cap = 0;
+    int32_t *jl_head = nullptr, *jl_next = nullptr, *jl_node = nullptr;   // n each
+    uint32_t *lit_misc = nullptr;         // [0]: joiners listed in this iteration
+    double *litF = nullptr;               // 3n
+    uint32_t *tstamp = nullptr;           // n
+    uint32_t *lit_ctr = nullptr;          // 3 per queue
+    int64_t lit_ctr_cap = 0;
+    int32_t *lit_over = nullptr;          // qcap
+    int32_t *touched = nullptr;           // 2 qcap
+    int64_t lit_qcap = 0;
     // second stream: hub chunks run beside the other evaluation kernels of a queue
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -84,6 +84,19 @@ struct RunArgs {
     uint32_t *tot_done;
     uint32_t *tot_next;
     int64_t tot_nchunks;
+    // the paper's gain: deg(x,C) beside every membership, the member index of
+    // the iteration (members at its start by community, and its joiners), the
+    // per-community sums F(n-1), F(n), F(n+1), and the communities a queue's
+    // moves touched (null under the mean-field rule)
+    int32_t *kmem;
+    const unsigned long long *cm_off;
+    const int32_t *cm_node;
+    int32_t *jl_head, *jl_next, *jl_node;
+    uint32_t *jl_count;
+    double *litF;
+    int32_t *touched;
+    uint32_t *ntouched;
+    uint32_t *tstamp;
 };
 
 // ---------------------------------------------------------------------------
@@ -1757,6 +1770,918 @@ __global__ void __launch_bounds__(AP_THREADS) k_apply(RunArgs a, int64_t bstart,
 }
 
 // ---------------------------------------------------------------------------
+// a7/a8 with the paper's gain.  The gain of x joining (leaving) C is the
+// change of WCC-hat(P) (Node Changes: Joining / Leaving a Community, with
+// the WCC-hat sum equations): C's members' terms after the move -- new size
+// and internal edge count, and for x's neighbours deg(y,C) one higher (lower)
+// -- and x's own term, less C's terms before it, summed exactly and rounded
+// once.  With deg(y,C) kept per membership (kmem, beside the rows) and the
+// members of C reachable through a per-iteration index (the members at the
+// iteration's start, cm_off/cm_node, plus a list of the iteration's joiners),
+// the exact value costs a pass over C.  It is only needed near ties: every
+// candidate first gets a bracket from per-community sums.  Writing
+//     g_y(nu) = C(k_y,2) d_y / (C(d_y,2) (nu - 1 + d_y - k_y)),
+// a member's estimator at size nu and internal edges m is (2m/(nu(nu-1))/cc)
+// g_y(nu), so in real arithmetic
+//   join:  gain = p'/cc [F(n+1) + sum_{y in N(x)&C} h+_y + g_x(n+1)] - p/cc F(n)
+//   leave: gain = p'/cc [F(n-1) - g_x(n-1) + sum_{y in N(x)&C} h-_y] - p/cc F(n)
+// with F(nu) = sum_{y in C} g_y(nu) (litF: three sums per community, kept
+// current after every queue for the communities it touched), p, p' the
+// densities before and after, and h+_y = g_y(n+1; k_y+1) - g_y(n+1; k_y),
+// h-_y = g_y(n-1; k_y-1) - g_y(n-1; k_y) in closed forms free of
+// cancellation.  Every term is non-negative except the h-, so the FP64 value
+// of this expression and the exact value of the rounded terms both lie within
+// (n + k + 64) 2.07u M of the real one (M: the same expression with every
+// term's magnitude; at most 2n + k + 40 roundings of non-negative sums and a
+// handful of products).  Per kind, candidates whose upper end cannot reach
+// the best lower end (or 0) are dropped; one surviving candidate with a
+// positive lower end is the answer; otherwise the survivors' gains are
+// computed exactly (a signed integer superaccumulator over C's members) and
+// compared.  The margin also covers one rounding of the compared values, so
+// a dropped candidate can neither win nor tie.
+// ---------------------------------------------------------------------------
+constexpr int LW = 512;                            // table slots of one warp
+constexpr int LB_SLOTS = EV_WARPS * LW;            // table slots of a block
+constexpr uint32_t SURV_FLAG = 0x40000000u;        // candidate survives the bracket test
+constexpr uint32_t CNT_MASK = 0x3fffffffu;
+constexpr size_t LIT_SMEM = (size_t)LB_SLOTS * (8 + 4 + 4 + 4) + (size_t)EV_WARPS * SACC_CHUNKS * 8;
+constexpr int LIT_PART_ENTRIES = 1024;             // entries per pass of a multi-pass node
+
+// Signed exact accumulation: like sacc_add, with negative values added as
+// negated digits (64-bit words wrap, so each word holds a signed sum).
+__device__ __forceinline__ void ssacc_add(unsigned long long *acc, double v) {
+    if (v == 0.0) return;
+    const bool neg = v < 0.0;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    unsigned long long mant = b & 0xfffffffffffffull;
+    int p;
+    if (e == 0) {
+        p = 0;
+    } else {
+        mant |= 1ull << 52;
+        p = (int)e - 1;
+    }
+    const int c = p >> 5, sh = p & 31;
+    const unsigned long long lo = mant << sh;
+    const unsigned long long hi = sh ? (mant >> (64 - sh)) : 0ull;
+    const unsigned long long d[3] = {lo & 0xffffffffull, lo >> 32, hi};
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+        if (d[t]) atomicAdd(&acc[c + t], neg ? (unsigned long long)(-(long long)d[t]) : d[t]);
+}
+
+// The double nearest (ties to even) to the non-negative value held in 32-bit
+// digits dg (bit 0 = 2^-1074).
+__device__ inline double round_digits(const uint32_t *dg) {
+    int top = -1;
+    for (int i = SACC_CHUNKS - 1; i >= 0; --i)
+        if (dg[i]) {
+            top = i;
+            break;
+        }
+    if (top < 0) return 0.0;
+    int P = 32 * top + (31 - __clz((int)dg[top]));
+    auto bit = [&](int q) -> unsigned long long {
+        return q < 0 ? 0ull : (unsigned long long)((dg[q >> 5] >> (q & 31)) & 1u);
+    };
+    if (P <= 52) {
+        unsigned long long v = 0;
+        for (int q = P; q >= 0; --q) v = (v << 1) | bit(q);
+        return __longlong_as_double((long long)v);
+    }
+    unsigned long long mant = 0;
+    for (int q = P; q >= P - 52; --q) mant = (mant << 1) | bit(q);
+    const int r = P - 53;
+    const bool round_bit = bit(r) != 0;
+    bool sticky = false;
+    for (int i = 0; i < (r >> 5) && !sticky; ++i) sticky = dg[i] != 0u;
+    if (!sticky && (r & 31)) sticky = (dg[r >> 5] & ((1u << (r & 31)) - 1u)) != 0u;
+    if (round_bit && (sticky || (mant & 1ull))) ++mant;
+    if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++P;
+    }
+    const long long biased = (long long)P - 51;
+    if (biased >= 2047) return __longlong_as_double(0x7ff0000000000000ll);
+    return __longlong_as_double((long long)(((unsigned long long)biased << 52) | (mant & 0xfffffffffffffull)));
+}
+
+// Round the signed accumulated value to the nearest double and clear the
+// accumulator.  One thread.
+__device__ inline double ssacc_round_and_clear(unsigned long long *acc) {
+    uint32_t dg[SACC_CHUNKS];
+    long long carry = 0;
+    for (int i = 0; i < SACC_CHUNKS; ++i) {
+        const long long v = (long long)acc[i] + carry;
+        acc[i] = 0ull;
+        const uint32_t low = (uint32_t)(unsigned long long)v;
+        dg[i] = low;
+        carry = (v - (long long)low) / 4294967296ll;   // exact: v - low is a multiple of 2^32
+    }
+    const bool neg = carry < 0;   // the value is (digits) - 2^(32 * SACC_CHUNKS)
+    if (neg) {
+        unsigned long long c = 1;
+        for (int i = 0; i < SACC_CHUNKS; ++i) {
+            const unsigned long long t = (unsigned long long)(uint32_t)~dg[i] + c;
+            dg[i] = (uint32_t)t;
+            c = t >> 32;
+        }
+    }
+    const double r = round_digits(dg);
+    return neg ? -r : r;
+}
+
+// Position of C in a row of cnt ascending ids, -1 if absent.
+__device__ __forceinline__ int row_find(const int32_t *row, int32_t cnt, int32_t C) {
+    int lo = 0, hi = cnt - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int32_t v = __ldcg(&row[mid]);
+        if (v == C) return mid;
+        if (v < C) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+// y in the ascending adjacency list adj[beg, end)?
+__device__ __forceinline__ bool adj_has(const int32_t *adj, int64_t beg, int64_t end, int32_t y) {
+    int64_t lo = beg, hi = end - 1;
+    while (lo <= hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int32_t v = adj[mid];
+        if (v == y) return true;
+        if (v < y) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return false;
+}
+
+// g_y(nu) = C(k,2) d / (C(d,2) (nu - 1 + d - k)): a member's estimator
+// without the factor (2m / (nu (nu - 1))) / cc.  Zero where the estimator is
+// (k < 2, or d < 2 so that E[t(x,V)] = 0).
+__device__ __forceinline__ double lit_g(int64_t k, int64_t d, int64_t nu) {
+    if (k < 2 || d < 2) return 0.0;
+    const int64_t den = nu - 1 + d - k;
+    if (den <= 0) return 0.0;
+    const double bk = 0.5 * ((double)k * (double)(k - 1));
+    const double bd = 0.5 * ((double)d * (double)(d - 1));
+    return (bk * (double)d) / (bd * (double)den);
+}
+
+// h+ = g(n+1; k+1) - g(n+1; k) = d (k D + C(k,2)) / (C(d,2) D (D-1)), D = n + d - k
+// (a neighbour y of a joining x; y is not x, so k <= d - 1 and D - 1 >= n >= 1)
+__device__ __forceinline__ double lit_h_join(int64_t k, int64_t d, int64_t n) {
+    if (d < 2 || k < 1) return 0.0;
+    const double D = (double)(n + d - k);
+    const double bk = 0.5 * ((double)k * (double)(k - 1));
+    const double bd = 0.5 * ((double)d * (double)(d - 1));
+    return ((double)d * ((double)k * D + bk)) / (bd * (D * (D - 1.0)));
+}
+
+// h- = g(n-1; k-1) - g(n-1; k) = -d (C(k-1,2) + (k-1)(D+1)) / (C(d,2) D (D+1)),
+// D = n - 2 + d - k (used only when n - 1 >= 2, so D >= 1)
+__device__ __forceinline__ double lit_h_leave(int64_t k, int64_t d, int64_t n) {
+    if (d < 2 || k < 2 || n < 3) return 0.0;
+    const double D = (double)(n - 2 + d - k);
+    const double bk1 = 0.5 * ((double)(k - 1) * (double)(k - 2));
+    const double bd = 0.5 * ((double)d * (double)(d - 1));
+    return -((double)d * (bk1 + (double)(k - 1) * (D + 1.0))) / (bd * (D * (D + 1.0)));
+}
+
+// Bracket of one candidate: FP64 value X of the expression above and a bound
+// E on its distance from the exactly summed, once rounded gain.
+__device__ __forceinline__ void lit_screen(const RunArgs &a, int32_t C, uint32_t v, int32_t d, double Hs, double &X,
+                                           double &E) {
+    const bool own = (v & OWN_FLAG) != 0;
+    const int64_t k = (int64_t)(v & CNT_MASK);
+    const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
+    const int64_t n = r.x;
+    const double m2 = (double)(uint32_t)r.y;
+    const double cc = a.gcc ? a.gcc[r.w] : a.cc;
+    if (!(cc > 0.0) || n < 1) {   // every estimator term is 0
+        X = 0.0;
+        E = 0.0;
+        return;
+    }
+    const double Fm = __ldcg(&a.litF[3 * (int64_t)C]);
+    const double F0 = __ldcg(&a.litF[3 * (int64_t)C + 1]);
+    const double Fp = __ldcg(&a.litF[3 * (int64_t)C + 2]);
+    const double Bc = n >= 2 ? (m2 / ((double)n * (double)(n - 1))) / cc : 0.0;
+    double A = 0.0, S1 = 0.0, Sm = 0.0;
+    if (!own) {
+        A = ((m2 + 2.0 * (double)k) / ((double)(n + 1) * (double)n)) / cc;
+        S1 = (Fp + Hs) + lit_g(k, d, n + 1);
+        Sm = S1;
+    } else if (n - 1 >= 2) {
+        A = ((m2 - 2.0 * (double)k) / ((double)(n - 1) * (double)(n - 2))) / cc;
+        const double gx = lit_g(k, d, n - 1);
+        S1 = (Fm - gx) + Hs;
+        Sm = (Fm + gx) - Hs;
+    }
+    X = A * S1 - Bc * F0;
+    const double M = A * Sm + Bc * F0;
+    E = ((double)(n + k) + 64.0) * 2.3e-16 * M + 1e-300;
+}
+
+// The exact gain of x joining (own = false) or leaving C: every member's term
+// after and before, x's own term, added into a signed superaccumulator (acc:
+// the warp's, zero on entry and on exit).  One warp.
+__device__ double lit_exact_gain(const RunArgs &a, int32_t x, int32_t d, int32_t C, bool own, int64_t k,
+                                 unsigned long long *acc) {
+    const int lane = threadIdx.x & 31;
+    const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
+    const int64_t n0 = r.x;
+    const uint32_t m20 = (uint32_t)r.y;
+    const double cc = a.gcc ? a.gcc[r.w] : a.cc;
+    const int64_t n1 = own ? n0 - 1 : n0 + 1;
+    const uint32_t m21 = own ? m20 - (uint32_t)(2 * k) : m20 + (uint32_t)(2 * k);
+    const int64_t xb = a.off[x], xe = a.off[x + 1];
+    auto member = [&](int32_t y) {
+        if (y == x) return;
+        const int32_t cy = __ldcg(&a.nmem[y]);
+        const int s = row_find(a.mem + (int64_t)y * a.K, cy, C);
+        if (s < 0) return;   // left C earlier in this iteration
+        const int64_t ky = __ldcg(&a.kmem[(int64_t)y * a.K + s]);
+        const int64_t dy = a.deg[y];
+        const int64_t k1 = adj_has(a.adj, xb, xe, y) ? (own ? ky - 1 : ky + 1) : ky;
+        ssacc_add(acc, wcchat_member(k1, dy, n1, m21, cc));
+        ssacc_add(acc, -wcchat_member(ky, dy, n0, m20, cc));
+    };
+    const int64_t b0 = a.cm_off[C], b1 = a.cm_off[C + 1];
+    for (int64_t p = b0 + lane; p < b1; p += 32) member(__ldcg(&a.cm_node[p]));
+    int idx = 0;
+    for (int32_t e = __ldcg(&a.jl_head[C]); e >= 0; e = __ldcg(&a.jl_next[e]), ++idx)
+        if ((idx & 31) == lane) member(__ldcg(&a.jl_node[e]));
+    if (lane == 0) ssacc_add(acc, own ? -wcchat_member(k, d, n0, m20, cc) : wcchat_member(k, d, n1, m21, cc));
+    __syncwarp();
+    double g = 0.0;
+    if (lane == 0) g = ssacc_round_and_clear(acc);
+    __syncwarp();
+    return __shfl_sync(FULL, g, 0);
+}
+
+// Per-warp values a literal team exchanges.
+struct LitScratch {
+    double lbj[EV_WARPS], lbl[EV_WARPS];
+    int cj[EV_WARPS], cl[EV_WARPS];
+    int32_t sCj[EV_WARPS], sCl[EV_WARPS], skj[EV_WARPS], skl[EV_WARPS];
+    double sLj[EV_WARPS], sLl[EV_WARPS];
+    double bgj[EV_WARPS], bgl[EV_WARPS];
+    int32_t bcj[EV_WARPS], bcl[EV_WARPS], bkj[EV_WARPS], bkl[EV_WARPS];
+    int flag[EV_WARPS];
+    long long part[EV_WARPS];
+};
+
+struct LitNode {
+    int32_t x, d, cx;
+    int64_t beg, end;
+};
+
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+__device__ __forceinline__ int lit_find(const int32_t *keys, uint32_t hm, int32_t key) {
+    uint32_t h = hash32((uint32_t)key) & hm;
+    for (uint32_t probe = 0; probe <= hm; ++probe) {
+        const int32_t k = keys[h];
+        if (k == key) return (int)h;
+        if (k == EMPTY_KEY) return -1;
+        h = (h + 1) & hm;
+    }
+    return -1;
+}
+
+// One pass over the node's candidates of part p (of P): fill the table
+// (keys, counts with the own flag), the candidates' sizes (aux), the
+// neighbour corrections (dv), then each candidate's bracket: dv <- X,
+// aux <- E (as a float rounded up).  Per lane: the largest lower ends of the
+// two kinds.  Returns false (team-wide) if the table overflowed.
+template <int T>
+__device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int32_t *keys, uint32_t *vals,
+                         int32_t *aux, double *dv, uint32_t H, LitScratch &ls, int tm, int w_in, double &lbj,
+                         double &lbl, unsigned long long &pb, bool count_bytes) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tl = w_in * 32 + lane;
+    constexpr int NT = T * 32;
+    const uint32_t hm = H - 1;
+    for (uint32_t s = tl; s < H; s += NT) {
+        keys[s] = EMPTY_KEY;
+        vals[s] = 0u;
+        dv[s] = 0.0;
+    }
+    team_sync<T>(tm);
+    bool ok = true;
+    const int32_t *rowx = a.mem + (int64_t)ln.x * a.K;
+    for (int j = tl; j < ln.cx; j += NT) {
+        const int32_t C = __ldcg(&rowx[j]);
+        if (P == 1 || (int)part_of(C, P) == p) ok &= ht_insert(keys, vals, hm, C, 0u, true);
+    }
+    team_sync<T>(tm);
+    for (int64_t q = ln.beg + tl; q < ln.end; q += NT) {
+        const int32_t y = a.adj[q];
+        const int32_t cy = __ldcg(&a.nmem[y]);
+        const int32_t *rowy = a.mem + (int64_t)y * a.K;
+        if (count_bytes) pb += 12ull + 8ull * (unsigned long long)cy;
+        for (int s = 0; s < cy; ++s) {
+            const int32_t C = __ldcg(&rowy[s]);
+            if (P == 1 || (int)part_of(C, P) == p) ok &= ht_insert(keys, vals, hm, C, 1u, false);
+        }
+    }
+    // a full table: the whole team starts over with more parts
+    if constexpr (T > 1) {
+        const bool all = __all_sync(FULL, ok);
+        if (lane == 0) ls.flag[w] = all ? 1 : 0;
+        team_sync<T>(tm);
+        for (int k2 = 0; k2 < T; ++k2) ok &= ls.flag[tm * T + k2] != 0;
+        team_sync<T>(tm);
+    } else {
+        ok = __all_sync(FULL, ok);
+    }
+    if (!ok) return false;
+    for (uint32_t s = tl; s < H; s += NT) {
+        const int32_t C = keys[s];
+        if (C != EMPTY_KEY) aux[s] = __ldcg(&a.comm[C].n);
+    }
+    team_sync<T>(tm);
+    for (int64_t q = ln.beg + tl; q < ln.end; q += NT) {
+        const int32_t y = a.adj[q];
+        const int32_t cy = __ldcg(&a.nmem[y]);
+        const int32_t *rowy = a.mem + (int64_t)y * a.K;
+        const int32_t *krow = a.kmem + (int64_t)y * a.K;
+        const int64_t dy = a.deg[y];
+        for (int s = 0; s < cy; ++s) {
+            const int32_t C = __ldcg(&rowy[s]);
+            if (P > 1 && (int)part_of(C, P) != p) continue;
+            const int slot = lit_find(keys, hm, C);
+            if (slot < 0) continue;
+            const int64_t ky = __ldcg(&krow[s]);
+            const int64_t n = aux[slot];
+            const double h = (vals[slot] & OWN_FLAG) ? lit_h_leave(ky, dy, n) : lit_h_join(ky, dy, n);
+            if (h != 0.0) atomicAdd(&dv[slot], h);
+        }
+    }
+    team_sync<T>(tm);
+    for (uint32_t s = tl; s < H; s += NT) {
+        const int32_t C = keys[s];
+        if (C == EMPTY_KEY) continue;
+        const uint32_t v = vals[s];
+        double X, E;
+        lit_screen(a, C, v, ln.d, dv[s], X, E);
+        const float Ef = __double2float_ru(E * (1.0 + 1e-6));
+        dv[s] = X;
+        aux[s] = __float_as_int(Ef);
+        const double L = X - (double)Ef;
+        if (v & OWN_FLAG) lbl = fmax(lbl, L);
+        else lbj = fmax(lbj, L);
+        if (count_bytes) pb += 40ull;
+    }
+    team_sync<T>(tm);
+    return true;
+}
+
+// The largest value of a team (through ls.lbj/lbl slots of its warps).
+template <int T>
+__device__ __forceinline__ void team_max2(LitScratch &ls, int tm, double &x1, double &x2) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    x1 = warp_max_d(x1);
+    x2 = warp_max_d(x2);
+    if constexpr (T > 1) {
+        if (lane == 0) {
+            ls.lbj[w] = x1;
+            ls.lbl[w] = x2;
+        }
+        team_sync<T>(tm);
+        for (int k2 = 0; k2 < T; ++k2) {
+            x1 = fmax(x1, ls.lbj[tm * T + k2]);
+            x2 = fmax(x2, ls.lbl[tm * T + k2]);
+        }
+        team_sync<T>(tm);
+    }
+}
+
+// Mark the survivors of the bracket test in the table (SURV_FLAG) and count
+// them per kind; for a lone survivor, its id, count and lower end.
+template <int T>
+__device__ void lit_mark(const RunArgs &a, int32_t *keys, uint32_t *vals, const int32_t *aux, const double *dv,
+                         uint32_t H, double lbj, double lbl, LitScratch &ls, int tm, int w_in, int &cj, int &cl,
+                         int32_t &Cj, int32_t &Cl, int32_t &kj, int32_t &kl, double &Lj, double &Ll) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int nj = 0, nl = 0;
+    int32_t fCj = -1, fCl = -1, fkj = 0, fkl = 0;
+    double fLj = 0.0, fLl = 0.0;
+    for (uint32_t b0 = (uint32_t)w_in * 32; b0 < H; b0 += T * 32) {
+        const uint32_t s = b0 + lane;
+        bool sj = false, sl = false;
+        int32_t C = EMPTY_KEY;
+        uint32_t v = 0;
+        double L = 0.0;
+        if (s < H) {
+            C = keys[s];
+            if (C != EMPTY_KEY) {
+                v = vals[s];
+                const double X = dv[s], E = (double)__int_as_float(aux[s]);
+                const double U = X + E;
+                L = X - E;
+                const bool own = (v & OWN_FLAG) != 0;
+                const bool surv = !a.screen || (U > 0.0 && U >= (own ? lbl : lbj));
+                if (surv) {
+                    vals[s] = v | SURV_FLAG;
+                    if (own) sl = true;
+                    else sj = true;
+                } else if (v & SURV_FLAG) {
+                    vals[s] = v & ~SURV_FLAG;
+                }
+            }
+        }
+        const unsigned mj = __ballot_sync(FULL, sj), ml = __ballot_sync(FULL, sl);
+        if (mj) {
+            const int src = __ffs(mj) - 1;
+            const int32_t c1 = __shfl_sync(FULL, C, src);
+            const uint32_t v1 = __shfl_sync(FULL, v, src);
+            const double l1 = __shfl_sync(FULL, L, src);
+            if (nj == 0) {
+                fCj = c1;
+                fkj = (int32_t)(v1 & CNT_MASK);
+                fLj = l1;
+            }
+            nj += __popc(mj);
+        }
+        if (ml) {
+            const int src = __ffs(ml) - 1;
+            const int32_t c1 = __shfl_sync(FULL, C, src);
+            const uint32_t v1 = __shfl_sync(FULL, v, src);
+            const double l1 = __shfl_sync(FULL, L, src);
+            if (nl == 0) {
+                fCl = c1;
+                fkl = (int32_t)(v1 & CNT_MASK);
+                fLl = l1;
+            }
+            nl += __popc(ml);
+        }
+    }
+    if constexpr (T > 1) {
+        if (lane == 0) {
+            ls.cj[w] = nj; ls.cl[w] = nl;
+            ls.sCj[w] = fCj; ls.sCl[w] = fCl; ls.skj[w] = fkj; ls.skl[w] = fkl;
+            ls.sLj[w] = fLj; ls.sLl[w] = fLl;
+        }
+        team_sync<T>(tm);
+        nj = nl = 0;
+        for (int k2 = 0; k2 < T; ++k2) {
+            const int q = tm * T + k2;
+            if (ls.cj[q] > 0 && nj == 0) { fCj = ls.sCj[q]; fkj = ls.skj[q]; fLj = ls.sLj[q]; }
+            if (ls.cl[q] > 0 && nl == 0) { fCl = ls.sCl[q]; fkl = ls.skl[q]; fLl = ls.sLl[q]; }
+            nj += ls.cj[q];
+            nl += ls.cl[q];
+        }
+        team_sync<T>(tm);
+    }
+    cj += nj;
+    cl += nl;
+    if (Cj < 0 && fCj >= 0) { Cj = fCj; kj = fkj; Lj = fLj; }
+    if (Cl < 0 && fCl >= 0) { Cl = fCl; kl = fkl; Ll = fLl; }
+}
+
+// Exact gains of the marked survivors of the kinds still open; each warp of
+// the team takes its slots' survivors one at a time.
+template <int T>
+__device__ void lit_exact_survivors(const RunArgs &a, const LitNode &ln, const int32_t *keys, const uint32_t *vals,
+                                    uint32_t H, bool do_j, bool do_l, unsigned long long *acc, int w_in, Best &bj,
+                                    Best &bl) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t b0 = (uint32_t)w_in * 32; b0 < H; b0 += T * 32) {
+        const uint32_t s = b0 + lane;
+        bool want = false;
+        int32_t C = EMPTY_KEY;
+        uint32_t v = 0;
+        if (s < H) {
+            C = keys[s];
+            if (C != EMPTY_KEY) {
+                v = vals[s];
+                want = (v & SURV_FLAG) && ((v & OWN_FLAG) ? do_l : do_j);
+            }
+        }
+        unsigned m = __ballot_sync(FULL, want);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const int32_t c1 = __shfl_sync(FULL, C, src);
+            const uint32_t v1 = __shfl_sync(FULL, v, src);
+            const bool own = (v1 & OWN_FLAG) != 0;
+            const int64_t k = (int64_t)(v1 & CNT_MASK);
+            const double g = lit_exact_gain(a, ln.x, ln.d, c1, own, k, acc);
+            if (g > 0.0) {
+                Best &b = own ? bl : bj;
+                if (better(g, c1, b.g, b.c)) b = Best{g, c1, (int32_t)k};
+            }
+        }
+    }
+}
+
+// A node's decision with the paper's gain, by a team of T warps over a table
+// of H slots (P parts of the candidates, one pass each).  False if a part
+// overflowed the table (the caller retries with more parts).
+template <int T>
+__device__ bool lit_eval_node(const RunArgs &a, int i, const LitNode &ln, int P, int32_t *keys, uint32_t *vals,
+                              int32_t *aux, double *dv, uint32_t H, LitScratch &ls, unsigned long long *acc,
+                              int tm, int w_in) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long pb = 0;
+    double lbj = -INFINITY, lbl = -INFINITY;
+    for (int p = 0; p < P; ++p)
+        if (!lit_pass<T>(a, ln, P, p, keys, vals, aux, dv, H, ls, tm, w_in, lbj, lbl, pb, a.profile != 0))
+            return false;
+    team_max2<T>(ls, tm, lbj, lbl);
+    int cj = 0, cl = 0;
+    int32_t Cj = -1, Cl = -1, kj = 0, kl = 0;
+    double Lj = 0.0, Ll = 0.0;
+    for (int p = 0; p < P; ++p) {
+        if (P > 1 && !lit_pass<T>(a, ln, P, p, keys, vals, aux, dv, H, ls, tm, w_in, lbj, lbl, pb, false))
+            return false;
+        lit_mark<T>(a, keys, vals, aux, dv, H, lbj, lbl, ls, tm, w_in, cj, cl, Cj, Cl, kj, kl, Lj, Ll);
+    }
+    Best bj{0.0, -1, 0}, bl{0.0, -1, 0};
+    bool do_j = cj > 0, do_l = cl > 0;
+    if (a.screen && cj == 1 && Lj > 0.0) {
+        bj = Best{INFINITY, Cj, kj};
+        do_j = false;
+    }
+    if (a.screen && cl == 1 && Ll > 0.0) {
+        bl = Best{INFINITY, Cl, kl};
+        do_l = false;
+    }
+    if (do_j || do_l) {
+        for (int p = 0; p < P; ++p) {
+            if (P > 1) {
+                double d1 = -INFINITY, d2 = -INFINITY;
+                if (!lit_pass<T>(a, ln, P, p, keys, vals, aux, dv, H, ls, tm, w_in, d1, d2, pb, false)) return false;
+                int c1 = 0, c2 = 0;
+                int32_t e1 = -1, e2 = -1, e3 = 0, e4 = 0;
+                double e5 = 0.0, e6 = 0.0;
+                lit_mark<T>(a, keys, vals, aux, dv, H, lbj, lbl, ls, tm, w_in, c1, c2, e1, e2, e3, e4, e5, e6);
+            }
+            lit_exact_survivors<T>(a, ln, keys, vals, H, do_j, do_l, acc, w_in, bj, bl);
+            team_sync<T>(tm);
+        }
+        if constexpr (T > 1) {
+            if (lane == 0) {
+                ls.bgj[w] = bj.g; ls.bcj[w] = bj.c; ls.bkj[w] = bj.k;
+                ls.bgl[w] = bl.g; ls.bcl[w] = bl.c; ls.bkl[w] = bl.k;
+            }
+            team_sync<T>(tm);
+            if (w_in == 0) {
+                for (int k2 = 1; k2 < T; ++k2) {
+                    const int q = tm * T + k2;
+                    if (better(ls.bgj[q], ls.bcj[q], bj.g, bj.c)) bj = Best{ls.bgj[q], ls.bcj[q], ls.bkj[q]};
+                    if (better(ls.bgl[q], ls.bcl[q], bl.g, bl.c)) bl = Best{ls.bgl[q], ls.bcl[q], ls.bkl[q]};
+                }
+            }
+            team_sync<T>(tm);
+        }
+    }
+    if (a.profile) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pb += __shfl_down_sync(FULL, pb, o);
+        if (lane == 0) atomicAdd(&a.ds->prof_bytes, pb + (w_in == 0 ? 44ull + 8ull * (unsigned long long)ln.cx : 0ull));
+    }
+    if (w_in == 0 && lane == 0) write_action(a, i, bj, bl, 0ull);
+    team_sync<T>(tm);
+    return true;
+}
+
+__device__ __forceinline__ void lit_smem(double *base, double *&dv, int32_t *&keys, uint32_t *&vals, int32_t *&aux,
+                                         unsigned long long *&acc) {
+    dv = base;
+    keys = reinterpret_cast<int32_t *>(base + LB_SLOTS);
+    vals = reinterpret_cast<uint32_t *>(keys + LB_SLOTS);
+    aux = reinterpret_cast<int32_t *>(vals + LB_SLOTS);
+    acc = reinterpret_cast<unsigned long long *>(aux + LB_SLOTS);
+}
+
+// Teams of T warps, one queued node each.  A node whose entries (own rows
+// plus its neighbours' rows) could fill more than half of the team's table
+// is listed for k_lit_big.  Counters: over[0] = listed nodes, over[1] = next.
+template <int T>
+__global__ void __launch_bounds__(EV_THREADS, 2) k_lit_eval(RunArgs a, int64_t bstart, int32_t blen, uint32_t *over,
+                                                           int32_t *over_list) {
+    extern __shared__ double lit_dyn[];
+    __shared__ LitScratch ls;
+    double *dv;
+    int32_t *keys, *aux;
+    uint32_t *vals;
+    unsigned long long *acc;
+    lit_smem(lit_dyn, dv, keys, vals, aux, acc);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int c = lane; c < SACC_CHUNKS; c += 32) acc[w * SACC_CHUNKS + c] = 0ull;
+    pdl_trigger();
+    pdl_wait();
+    const int tm = w / T, w_in = w % T;
+    const int i = (int)blockIdx.x * (EV_WARPS / T) + tm;
+    if (i >= blen) return;   // the whole team leaves together
+    LitNode ln;
+    ln.x = a.order[bstart + i];
+    ln.beg = a.off[ln.x];
+    ln.end = a.off[ln.x + 1];
+    ln.d = (int32_t)(ln.end - ln.beg);
+    ln.cx = __ldcg(&a.nmem[ln.x]);
+    long long bound = w_in == 0 && lane == 0 ? ln.cx : 0;
+    for (int64_t q = ln.beg + w_in * 32 + lane; q < ln.end; q += T * 32) bound += __ldcg(&a.nmem[a.adj[q]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bound += __shfl_xor_sync(FULL, bound, o);
+    if constexpr (T > 1) {
+        if (lane == 0) ls.part[w] = bound;
+        team_sync<T>(tm);
+        bound = 0;
+        for (int k2 = 0; k2 < T; ++k2) bound += ls.part[tm * T + k2];
+        team_sync<T>(tm);
+    }
+    uint32_t H = 32;
+    while ((long long)H < 2 * bound) H <<= 1;
+    if (H > (uint32_t)(T * LW)) {
+        if (w_in == 0 && lane == 0) {
+            const uint32_t slot = atomicAdd(&over[0], 1u);
+            over_list[slot] = i;
+        }
+        return;
+    }
+    const int base = tm * T * LW;
+    if (!lit_eval_node<T>(a, i, ln, 1, keys + base, vals + base, aux + base, dv + base, H, ls, acc + w * SACC_CHUNKS,
+                          tm, w_in)) {
+        if (w_in == 0 && lane == 0) atomicOr(&a.ds->err, DERR_CHECK);   // cannot happen: H >= 2 x entries
+    }
+}
+
+// Listed nodes, one block each, over the block's whole table in as many
+// parts as needed (a part that overflows doubles the parts).
+__global__ void __launch_bounds__(EV_THREADS, 2) k_lit_big(RunArgs a, int64_t bstart, uint32_t *over,
+                                                          const int32_t *over_list) {
+    extern __shared__ double lit_dyn[];
+    __shared__ LitScratch ls;
+    __shared__ int s_i;
+    double *dv;
+    int32_t *keys, *aux;
+    uint32_t *vals;
+    unsigned long long *acc;
+    lit_smem(lit_dyn, dv, keys, vals, aux, acc);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int c = lane; c < SACC_CHUNKS; c += 32) acc[w * SACC_CHUNKS + c] = 0ull;
+    pdl_trigger();
+    pdl_wait();
+    const uint32_t count = __ldcg(&over[0]);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t t = atomicAdd(&over[1], 1u);
+            s_i = t < count ? over_list[t] : -1;
+        }
+        __syncthreads();
+        const int i = s_i;
+        __syncthreads();
+        if (i < 0) break;
+        LitNode ln;
+        ln.x = a.order[bstart + i];
+        ln.beg = a.off[ln.x];
+        ln.end = a.off[ln.x + 1];
+        ln.d = (int32_t)(ln.end - ln.beg);
+        ln.cx = __ldcg(&a.nmem[ln.x]);
+        long long bound = threadIdx.x == 0 ? ln.cx : 0;
+        for (int64_t q = ln.beg + threadIdx.x; q < ln.end; q += EV_THREADS) bound += __ldcg(&a.nmem[a.adj[q]]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bound += __shfl_xor_sync(FULL, bound, o);
+        if (lane == 0) ls.part[w] = bound;
+        __syncthreads();
+        bound = 0;
+        for (int k2 = 0; k2 < EV_WARPS; ++k2) bound += ls.part[k2];
+        __syncthreads();
+        int P = (int)((bound + LIT_PART_ENTRIES - 1) / LIT_PART_ENTRIES);
+        if (P < 1) P = 1;
+        while (!lit_eval_node<EV_WARPS>(a, i, ln, P, keys, vals, aux, dv, (uint32_t)LB_SLOTS, ls,
+                                        acc + w * SACC_CHUNKS, 0, w)) {
+            P *= 2;
+            if (P > (1 << 22)) {   // cannot happen for < 2^31 entries; leave an error, not a loop
+                if (threadIdx.x == 0) atomicOr(&a.ds->err, DERR_CHECK);
+                break;
+            }
+        }
+    }
+}
+
+// Apply of one queue under the paper's gain: as apply_node (rows, n_C,
+// vol_C, 2m_C with the same in-queue corrections), and in addition each
+// membership's deg(x,C) moves with the row, a joiner's starts at its count
+// before the queue (k_lit_kupd adds the queue's other moves), the joiner is
+// appended to C's list of this iteration's joiners, and every community a
+// move touches is listed once for k_lit_fsum.
+__device__ void lit_apply_node(const RunArgs &a, int64_t bstart, int32_t blen, int64_t i, uint32_t serial,
+                               unsigned long long &nj, unsigned long long &nl) {
+    const int lane = threadIdx.x & 31;
+    const int32_t j = __ldcg(&a.act[i]), l = __ldcg(&a.act[a.qcap + i]);
+    if (j < 0 && l < 0) return;
+    const int32_t x = a.order[bstart + i];
+    int jj = 0, jl = 0, ll = 0;
+    for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
+        const int32_t y = a.adj[p];
+        const int64_t py = a.pos[y];
+        if (py >= bstart && py < bstart + blen) {
+            const int64_t iy = py - bstart;
+            const int32_t aj = __ldcg(&a.act[iy]), al = __ldcg(&a.act[a.qcap + iy]);
+            if (j >= 0) {
+                jj += aj == j;
+                jl += al == j;
+            }
+            if (l >= 0) ll += al == l;
+        }
+    }
+    jj = __reduce_add_sync(FULL, jj);
+    jl = __reduce_add_sync(FULL, jl);
+    ll = __reduce_add_sync(FULL, ll);
+    const int32_t d = a.deg[x];
+    const int32_t kjoin = __ldcg(&a.act[2 * a.qcap + i]);
+    int32_t *row = a.mem + (int64_t)x * a.K;
+    int32_t *krow = a.kmem + (int64_t)x * a.K;
+    const int32_t c = __ldcg(&a.nmem[x]);
+    int32_t c_new = c;
+    if (lane == 0) {
+        int32_t cc2 = c;
+        if (l >= 0) {
+            int32_t o = 0;
+            for (int32_t s = 0; s < cc2; ++s) {
+                const int32_t v = __ldcg(&row[s]);
+                if (v != l) {
+                    krow[o] = __ldcg(&krow[s]);
+                    row[o++] = v;
+                }
+            }
+            cc2 = o;
+        }
+        if (j >= 0) {
+            if (cc2 >= a.K) {
+                atomicOr(&a.ds->err, DERR_CAPACITY);
+            } else {
+                int32_t s = cc2;
+                while (s > 0) {
+                    const int32_t v = __ldcg(&row[s - 1]);
+                    if (v <= j) break;
+                    row[s] = v;
+                    krow[s] = __ldcg(&krow[s - 1]);
+                    --s;
+                }
+                row[s] = j;
+                krow[s] = kjoin;
+                ++cc2;
+            }
+        }
+        c_new = cc2;
+        if (l >= 0) {
+            const int32_t kl = __ldcg(&a.act[3 * a.qcap + i]);
+            atomicAdd(&a.comm[l].n, -1);
+            atomicAdd(&a.comm[l].vol, (uint32_t)(-d));
+            atomicAdd(&a.comm[l].m2, (uint32_t)(-2 * kl + ll));
+            ++nl;
+            if (atomicExch(&a.tstamp[l], serial) != serial) a.touched[atomicAdd(a.ntouched, 1u)] = l;
+        }
+        if (j >= 0) {
+            atomicAdd(&a.comm[j].n, 1);
+            atomicAdd(&a.comm[j].vol, (uint32_t)d);
+            atomicAdd(&a.comm[j].m2, (uint32_t)(2 * kjoin + jj - 2 * jl));
+            ++nj;
+            const int32_t e = (int32_t)atomicAdd(a.jl_count, 1u);
+            a.jl_node[e] = x;
+            a.jl_next[e] = atomicExch(&a.jl_head[j], e);
+            if (atomicExch(&a.tstamp[j], serial) != serial) a.touched[atomicAdd(a.ntouched, 1u)] = j;
+        }
+        a.nmem[x] = c_new;
+    }
+}
+
+__global__ void __launch_bounds__(AP_THREADS) k_lit_apply(RunArgs a, int64_t bstart, int32_t blen, int64_t bidx) {
+    pdl_trigger();
+    pdl_wait();
+    const uint32_t serial = (uint32_t)queue_serial(a, bidx);
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    unsigned long long nj = 0, nl = 0;
+    if (i < blen) lit_apply_node(a, bstart, blen, i, serial, nj, nl);
+    flush_counts(a, nj, nl);
+}
+
+// Every neighbour y of a node that joined (left) C and is in C after the
+// queue has one more (fewer) neighbour in C.  Summed over the queue this
+// turns each membership's count before the queue into its count after it,
+// for stayers and joiners alike (leavers' memberships are gone).
+__global__ void __launch_bounds__(AP_THREADS) k_lit_kupd(RunArgs a, int64_t bstart, int32_t blen) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= blen) return;
+    const int32_t j = __ldcg(&a.act[i]), l = __ldcg(&a.act[a.qcap + i]);
+    if (j < 0 && l < 0) return;
+    const int32_t x = a.order[bstart + i];
+    for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
+        const int32_t y = a.adj[p];
+        const int32_t cy = __ldcg(&a.nmem[y]);
+        const int32_t *row = a.mem + (int64_t)y * a.K;
+        if (j >= 0) {
+            const int s = row_find(row, cy, j);
+            if (s >= 0) atomicAdd(&a.kmem[(int64_t)y * a.K + s], 1);
+        }
+        if (l >= 0) {
+            const int s = row_find(row, cy, l);
+            if (s >= 0) atomicAdd(&a.kmem[(int64_t)y * a.K + s], -1);
+        }
+    }
+}
+
+// F(n-1), F(n), F(n+1) of communities: list[0 .. *count) (or every id below
+// ncount when list is null), one block per community.
+__global__ void __launch_bounds__(256) k_lit_fsum(RunArgs a, const int32_t *list, const uint32_t *count,
+                                                  int64_t ncount) {
+    __shared__ double red[3][8];
+    const int64_t total = list ? (int64_t)__ldcg(count) : ncount;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const int32_t C = list ? __ldcg(&list[t]) : (int32_t)t;
+        const int64_t n = __ldcg(&a.comm[C].n);
+        double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+        if (n > 0) {
+            auto member = [&](int32_t y) {
+                const int32_t cy = __ldcg(&a.nmem[y]);
+                const int s = row_find(a.mem + (int64_t)y * a.K, cy, C);
+                if (s < 0) return;
+                const int64_t ky = __ldcg(&a.kmem[(int64_t)y * a.K + s]);
+                const int64_t dy = a.deg[y];
+                f0 += lit_g(ky, dy, n - 1);
+                f1 += lit_g(ky, dy, n);
+                f2 += lit_g(ky, dy, n + 1);
+            };
+            const int64_t b0 = a.cm_off[C], b1 = a.cm_off[C + 1];
+            for (int64_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) member(__ldcg(&a.cm_node[p]));
+            int idx = 0;
+            for (int32_t e = __ldcg(&a.jl_head[C]); e >= 0; e = __ldcg(&a.jl_next[e]), ++idx)
+                if (idx % (int)blockDim.x == (int)threadIdx.x) member(__ldcg(&a.jl_node[e]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            f0 += __shfl_xor_sync(FULL, f0, o);
+            f1 += __shfl_xor_sync(FULL, f1, o);
+            f2 += __shfl_xor_sync(FULL, f2, o);
+        }
+        if (lane == 0) {
+            red[0][w] = f0;
+            red[1][w] = f1;
+            red[2][w] = f2;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double s = 0.0;
+            for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) s += red[threadIdx.x][k2];
+            a.litF[3 * (int64_t)C + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// deg(x,C) of every membership, counted over x's neighbours (a warp per node).
+__global__ void k_lit_kinit(RunArgs a, int64_t n) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+        const int32_t cx = a.nmem[x];
+        const int32_t *row = a.mem + x * a.K;
+        for (int32_t s = 0; s < cx; ++s) {
+            const int32_t C = row[s];
+            int cnt = 0;
+            for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
+                const int32_t y = a.adj[p];
+                cnt += row_find(a.mem + (int64_t)y * a.K, a.nmem[y], C) >= 0;
+            }
+            cnt = __reduce_add_sync(FULL, cnt);
+            if (lane == 0) a.kmem[x * a.K + s] = cnt;
+        }
+    }
+}
+
+// Member index at an iteration's start: members per community, then (after
+// a scan into cm_off) every node listed under each of its communities.
+__global__ void k_lit_count(RunArgs a, int64_t n, unsigned long long *cnt) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t cx = a.nmem[x];
+        const int32_t *row = a.mem + x * a.K;
+        for (int32_t s = 0; s < cx; ++s) atomicAdd(&cnt[row[s]], 1ull);
+    }
+}
+
+__global__ void k_lit_fill(RunArgs a, int64_t n, unsigned long long *cursor, int32_t *cm_node) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t cx = a.nmem[x];
+        const int32_t *row = a.mem + x * a.K;
+        for (int32_t s = 0; s < cx; ++s) cm_node[atomicAdd(&cursor[row[s]], 1ull)] = (int32_t)x;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Persistent queue loop: one cooperative launch runs queues first ..
 // first+count-1 of an iteration: evaluate (blocks take groups of EV_WARPS
 // nodes), grid barrier, apply (warps take nodes), grid barrier.  Every
@@ -2089,7 +3014,10 @@ __global__ void k_prune(RunArgs a, int64_t n, int64_t ncomm) {
             int32_t o = 0;
             for (int32_t s = 0; s < c; ++s) {
                 int32_t C = row[s];
-                if (__ldcg(&a.comm[C].n) >= 2) row[o++] = C;
+                if (__ldcg(&a.comm[C].n) >= 2) {
+                    if (a.kmem) a.kmem[idx * a.K + o] = a.kmem[idx * a.K + s];
+                    row[o++] = C;
+                }
             }
             if (o != c) a.nmem[idx] = o;
             mc = max(mc, o);
@@ -2390,10 +3318,12 @@ __global__ void k_finalize(DevScalars *ds, Readback *rbd, int advance) {
 }
 
 __global__ void k_regrow(const int32_t *mem, const int32_t *nmem, int64_t n, int32_t K, int32_t *mem2,
-                         int32_t K2) {
+                         int32_t K2, const int32_t *kmem, int32_t *kmem2) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = nmem[x];
         for (int32_t s = 0; s < c; ++s) mem2[x * K2 + s] = mem[x * K + s];
+        if (kmem)
+            for (int32_t s = 0; s < c; ++s) kmem2[x * K2 + s] = kmem[x * K + s];
     }
 }
 
@@ -2465,6 +3395,19 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.tot_done = g->tot_done;
     a.tot_next = g->tot_next;
     a.tot_nchunks = g->tot_nchunks;
+    const bool lit = g->gain_rule == LF_GAIN_LITERAL;
+    a.kmem = lit ? g->kmem : nullptr;
+    a.cm_off = g->cm_off;
+    a.cm_node = g->cm_node;
+    a.jl_head = g->jl_head;
+    a.jl_next = g->jl_next;
+    a.jl_node = g->jl_node;
+    a.jl_count = g->lit_misc;
+    a.litF = g->litF;
+    a.touched = g->touched;
+    a.ntouched = g->lit_ctr;
+    a.tstamp = g->tstamp;
+    if (lit) a.screen = g->screen ? 1 : 0;   // brackets need no FP32 range condition
     return a;
 }
 
@@ -2562,6 +3505,11 @@ void set_eval_attrs() {
     LF_CUDA(cudaFuncSetAttribute(k_eval_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
     LF_CUDA(cudaFuncSetAttribute(k_eval_tdyn<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EV_DYN_SMEM));
     LF_CUDA(cudaFuncSetAttribute(k_huge_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(HUGE_SH * 8)));
+    LF_CUDA(cudaFuncSetAttribute(k_lit_eval<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIT_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_lit_eval<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIT_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_lit_eval<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIT_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_lit_eval<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIT_SMEM));
+    LF_CUDA(cudaFuncSetAttribute(k_lit_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LIT_SMEM));
 }
 
 void drop_graph(lf_graph *g) {
@@ -2684,6 +3632,101 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
     LF_LAUNCHED();
 }
 
+// Per-queue launches under the paper's gain: teams evaluate the queue's nodes
+// (k_lit_eval), blocks take the nodes too large for a team (k_lit_big), then
+// the apply, the neighbours' deg(y,C) updates and the touched communities'
+// sums.
+void launch_batches_lit(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int64_t count,
+                        bool capturing = false) {
+    const bool sched = !g->sched.empty();
+    const int T0 = choose_team(g, q);
+    static const int per_sm_big = blocks_per_sm(k_lit_big, EV_THREADS, LIT_SMEM);
+    const unsigned big_grid = (unsigned)(num_sms() * std::max(1, per_sm_big));
+    LF_CUDA(cudaMemsetAsync(g->lit_ctr + 3 * first, 0, (size_t)(3 * count) * sizeof(uint32_t), g->stream));
+    const bool prof = g->profile && (int64_t)g->prof_ev.size() >= 2 * (first + count);
+    for (int64_t b = first; b < first + count; ++b) {
+        int64_t bstart;
+        int32_t blen;
+        queue_bounds(g, q, b, bstart, blen);
+        const int T = sched ? choose_team(g, blen) : T0;
+        const int teams = EV_WARPS / T;
+        uint32_t *ctr = g->lit_ctr + 3 * b;
+        RunArgs ab = a;
+        ab.ntouched = ctr + 2;
+        if (prof) record_event(g, g->prof_ev[2 * b], capturing);
+        const unsigned grid = (unsigned)((blen + teams - 1) / teams);
+        switch (T) {
+        case 1: launch_pdl(k_lit_eval<1>, grid, EV_THREADS, LIT_SMEM, g->stream, ab, bstart, blen, ctr, g->lit_over); break;
+        case 2: launch_pdl(k_lit_eval<2>, grid, EV_THREADS, LIT_SMEM, g->stream, ab, bstart, blen, ctr, g->lit_over); break;
+        case 4: launch_pdl(k_lit_eval<4>, grid, EV_THREADS, LIT_SMEM, g->stream, ab, bstart, blen, ctr, g->lit_over); break;
+        default: launch_pdl(k_lit_eval<8>, grid, EV_THREADS, LIT_SMEM, g->stream, ab, bstart, blen, ctr, g->lit_over); break;
+        }
+        launch_pdl(k_lit_big, std::min<unsigned>(big_grid, (unsigned)blen), EV_THREADS, LIT_SMEM, g->stream, ab,
+                   bstart, ctr, (const int32_t *)g->lit_over);
+        if (prof) record_event(g, g->prof_ev[2 * b + 1], capturing);
+        const unsigned ag = grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30);
+        launch_pdl(k_lit_apply, ag, AP_THREADS, 0, g->stream, ab, bstart, blen, b);
+        k_lit_kupd<<<ag, AP_THREADS, 0, g->stream>>>(ab, bstart, blen);
+        k_lit_fsum<<<(unsigned)std::min<int64_t>(2 * (int64_t)blen, 8 * (int64_t)num_sms()), 256, 0, g->stream>>>(
+            ab, g->touched, ctr + 2, 0);
+        g->launches += 5;
+    }
+    LF_LAUNCHED();
+}
+
+// Arrays of the paper's gain for queues of up to q nodes and nb queues.
+void ensure_lit(lf_graph *g, int64_t q, int64_t nb) {
+    const int64_t n = std::max<int64_t>(g->n, 1);
+    if (!g->litF) {
+        g->litF = dalloc_n<double>(g, 3 * n);
+        g->cm_off = dalloc_n<unsigned long long>(g, n + 1);
+        g->cm_cur = dalloc_n<unsigned long long>(g, n + 1);
+        g->jl_head = dalloc_n<int32_t>(g, n);
+        g->jl_next = dalloc_n<int32_t>(g, n);
+        g->jl_node = dalloc_n<int32_t>(g, n);
+        g->tstamp = dalloc_n<uint32_t>(g, n);
+        g->lit_misc = dalloc_n<uint32_t>(g, 4);
+    }
+    if (g->cm_cap < n * g->K) {
+        if (g->cm_node) dfree(g, g->cm_node);
+        g->cm_cap = n * g->K;
+        g->cm_node = dalloc_n<int32_t>(g, g->cm_cap);
+    }
+    if (g->lit_qcap < q) {
+        if (g->lit_over) dfree(g, g->lit_over);
+        if (g->touched) dfree(g, g->touched);
+        g->lit_qcap = q;
+        g->lit_over = dalloc_n<int32_t>(g, q);
+        g->touched = dalloc_n<int32_t>(g, 2 * q);
+        drop_graph(g);
+    }
+    if (g->lit_ctr_cap < 3 * nb) {
+        if (g->lit_ctr) dfree(g, g->lit_ctr);
+        g->lit_ctr_cap = 3 * nb;
+        g->lit_ctr = dalloc_n<uint32_t>(g, 3 * nb);
+        drop_graph(g);
+    }
+}
+
+// Start of an iteration under the paper's gain: the member index (members
+// by community), no joiners yet, and every community's sums.
+void lit_iteration_start(lf_graph *g, const RunArgs &a) {
+    const int64_t n = g->n, nc = g->ncomm;
+    if (n == 0 || nc == 0) return;
+    cudaStream_t st = g->stream;
+    LF_CUDA(cudaMemsetAsync(g->cm_cur, 0, (size_t)nc * 8, st));
+    k_lit_count<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(a, n, g->cm_cur);
+    LF_LAUNCHED();
+    scan_exclusive<unsigned long long>(g, g->cm_cur, g->cm_off, nc, g->cm_off + nc);
+    LF_CUDA(cudaMemcpyAsync(g->cm_cur, g->cm_off, (size_t)nc * 8, cudaMemcpyDeviceToDevice, st));
+    k_lit_fill<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(a, n, g->cm_cur, g->cm_node);
+    LF_CUDA(cudaMemsetAsync(g->jl_head, 0xff, (size_t)nc * 4, st));
+    LF_CUDA(cudaMemsetAsync(g->lit_misc, 0, 4 * sizeof(uint32_t), st));
+    k_lit_fsum<<<(unsigned)std::min<int64_t>(nc, 16 * (int64_t)num_sms()), 256, 0, st>>>(a, nullptr, nullptr, nc);
+    g->launches += 3;
+    LF_LAUNCHED();
+}
+
 // Queue order of a batch: segments (source position in the graph-by-graph
 // order, destination, length) copied one warp each.
 __global__ void k_gather_order(const int32_t *order, const long long *seg, int64_t nseg, int32_t *qorder,
@@ -2776,6 +3819,7 @@ void ensure_capacity(lf_graph *g, int64_t q) {
         g->K = std::max(4, (g->member_slots + 3) / 4 * 4);   // rows start on 16-byte boundaries
         g->mem = dalloc_n<int32_t>(g, n * g->K);
     }
+    if (g->gain_rule == LF_GAIN_LITERAL && !g->kmem) g->kmem = dalloc_n<int32_t>(g, n * g->K);
     if (g->qcap < q) {
         if (g->act) dfree(g, g->act);
         g->qcap = (int32_t)q;
@@ -2789,10 +3833,16 @@ void grow_rows(lf_graph *g, int32_t need) {
     while (K2 < need) K2 *= 2;
     if (K2 == g->K) return;
     int32_t *mem2 = dalloc_n<int32_t>(g, g->n * K2);
-    k_regrow<<<grid_for(g->n, 256, 1 << 16), 256, 0, g->stream>>>(g->mem, g->nmem, g->n, g->K, mem2, K2); ++g->launches;
+    int32_t *kmem2 = g->kmem ? dalloc_n<int32_t>(g, g->n * K2) : nullptr;
+    k_regrow<<<grid_for(g->n, 256, 1 << 16), 256, 0, g->stream>>>(g->mem, g->nmem, g->n, g->K, mem2, K2, g->kmem,
+                                                                   kmem2); ++g->launches;
     LF_LAUNCHED();
     dfree(g, g->mem);
     g->mem = mem2;
+    if (g->kmem) {
+        dfree(g, g->kmem);
+        g->kmem = kmem2;
+    }
     g->K = K2;
     drop_graph(g);
 }
@@ -3082,6 +4132,24 @@ void free_run_state(lf_graph *g) {
     g->bar_flags_cap = 0;
     for (auto e : g->prof_ev) cudaEventDestroy(e);
     g->prof_ev.clear();
+    for (int32_t **pp : {&g->kmem, &g->cm_node, &g->jl_head, &g->jl_next, &g->jl_node, &g->lit_over, &g->touched})
+        if (*pp) {
+            dfree(g, *pp);
+            *pp = nullptr;
+        }
+    for (unsigned long long **pp : {&g->cm_off, &g->cm_cur})
+        if (*pp) {
+            dfree(g, *pp);
+            *pp = nullptr;
+        }
+    for (uint32_t **pp : {&g->lit_misc, &g->tstamp, &g->lit_ctr})
+        if (*pp) {
+            dfree(g, *pp);
+            *pp = nullptr;
+        }
+    if (g->litF) dfree(g, g->litF);
+    g->litF = nullptr;
+    g->cm_cap = g->lit_ctr_cap = g->lit_qcap = 0;
     if (g->act) dfree(g, g->act);
     if (g->mem) dfree(g, g->mem);
     if (g->nmem) dfree(g, g->nmem);
@@ -3227,6 +4295,14 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         dfree(g, state);
     }
     g->ncomm = k0;
+    const bool lit = g->gain_rule == LF_GAIN_LITERAL;
+    if (lit && n > 0) {   // deg(x,C) of every membership of the starting state
+        ensure_lit(g, batch ? max_queue(g, q) : q, num_queues(g, q));
+        a = make_args(g, device_readback(g));
+        LF_CUDA(cudaMemsetAsync(g->tstamp, 0, (size_t)n * 4, st));
+        k_lit_kinit<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(a, n); ++g->launches;
+        LF_LAUNCHED();
+    }
     launch_total(g, a);
     k_finalize<<<1, 32, 0, st>>>(g->ds, device_readback(g), 0); ++g->launches;
     LF_LAUNCHED();
@@ -3249,11 +4325,11 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     }
 
     int64_t nb = num_queues(g, q);
-    if (batch) ensure_dyn(g, max_queue(g, q), nb);
-    else if (use_dyn(g, q)) ensure_dyn(g, q, nb);
+    if (batch && !lit) ensure_dyn(g, max_queue(g, q), nb);
+    else if (!lit && use_dyn(g, q)) ensure_dyn(g, q, nb);
     // measured on GB300: the persistent loop wins for small queues (grid
     // barriers over few blocks), launches per queue for large ones
-    const bool persistent = !batch && (g->per_queue == 0 || (g->per_queue < 0 && q <= 256));
+    const bool persistent = !batch && !lit && (g->per_queue == 0 || (g->per_queue < 0 && q <= 256));
     const int team = choose_team(g, q);
     const int grid_max = persistent ? persistent_grid_max(g, team) : 0;
     if (persistent) {
@@ -3285,17 +4361,20 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             if (it > 1) {
                 build_schedule(g, q, gactive);
                 nb = num_queues(g, q);
-                ensure_dyn(g, max_queue(g, q), nb);
+                if (!lit) ensure_dyn(g, max_queue(g, q), nb);
             }
         }
         if (maxcnt + 1 > g->K) grow_rows(g, maxcnt + 1);
-        build_hub_plan(g, q);
+        if (!lit) build_hub_plan(g, q);
         build_total_plan(g);
+        if (lit) ensure_lit(g, batch ? max_queue(g, q) : q, nb);
         a = make_args(g, device_readback(g));
         a.nbatches = nb;
+        if (lit) lit_iteration_start(g, a);
         const bool partial = max_batches >= 0 && batches + nb > max_batches;
         if (partial) {
             if (persistent) launch_persistent(g, a, q, 0, max_batches - batches, grid_max, team, nullptr, nullptr);
+            else if (lit) launch_batches_lit(g, a, q, 0, max_batches - batches);
             else launch_batches(g, a, q, 0, max_batches - batches);
             batches = max_batches;
             LF_CUDA(cudaStreamSynchronize(st));
@@ -3316,7 +4395,8 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
                 const unsigned long long before = g->launches;
                 LF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
                 try {
-                    launch_batches(g, a, q, 0, nb, true);
+                    if (lit) launch_batches_lit(g, a, q, 0, nb, true);
+                    else launch_batches(g, a, q, 0, nb, true);
                     launch_iteration_end(g, a);
                 } catch (...) {
                     cudaGraph_t tmp;
@@ -3340,7 +4420,8 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
             LF_CUDA(cudaGraphLaunch(g->iter_exec, st));
             g->launches += g->graph_kernels;
         } else {
-            launch_batches(g, a, q, 0, nb);
+            if (lit) launch_batches_lit(g, a, q, 0, nb);
+            else launch_batches(g, a, q, 0, nb);
             launch_iteration_end(g, a);
         }
         batches += nb;

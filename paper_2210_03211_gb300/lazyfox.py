@@ -30,6 +30,11 @@ ABI_FUNCTIONS = ("lf_graph_create", "lf_run", "lf_run_partial", "lf_get_communit
                  "lf_server_get_communities", "lf_server_release", "lf_server_destroy", "lf_cover_f1")
 
 
+# lf_options.gain_rule: None = the library default; "literal" = the paper's gain
+# (the change of WCC-hat(P)); "meanfield" = the mean-field departure
+GAIN_RULES = {None: 0, "literal": 1, "meanfield": 2}
+
+
 class LazyFoxError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{_STATUS.get(status, status)}: {message}")
@@ -48,7 +53,7 @@ class Options(C.Structure):
                 ("use_graphs", C.c_int32), ("profile", C.c_int32), ("exhaustive_fp64", C.c_int32),
                 ("per_queue_launches", C.c_int32), ("barrier_timeout_ms", C.c_int32),
                 ("inject_barrier_stall", C.c_int32), ("barrier_mode", C.c_int32),
-                ("warps_per_node", C.c_int32), ("hub_degree", C.c_int32)]
+                ("warps_per_node", C.c_int32), ("hub_degree", C.c_int32), ("gain_rule", C.c_int32)]
 
 
 class RunStatsC(C.Structure):
@@ -201,7 +206,8 @@ class Graph:
                  warp_max_degree: int = 0, use_graphs: bool = True, profile: bool = False,
                  exhaustive_fp64: bool = False, per_queue_launches: bool | None = None,
                  barrier_timeout_ms: int = 0, inject_barrier_stall: bool = False, barrier_mode: int = 0,
-                 warps_per_node: int = 0, hub_degree: int = 0, device=None, edge_offsets=None):
+                 warps_per_node: int = 0, hub_degree: int = 0, gain_rule: str | None = None, device=None,
+                 edge_offsets=None):
         import torch
         self._L = load_library()
         self._h = C.c_void_p()
@@ -235,6 +241,9 @@ class Graph:
         opt.barrier_mode = int(barrier_mode)
         opt.warps_per_node = int(warps_per_node)
         opt.hub_degree = int(hub_degree)
+        if gain_rule not in GAIN_RULES:
+            raise ValueError(f"unknown gain_rule {gain_rule!r}")
+        opt.gain_rule = GAIN_RULES[gain_rule]
         if isinstance(src, torch.Tensor):
             if src.dtype != torch.int32 or dst.dtype != torch.int32 or not src.is_cuda:
                 raise TypeError("device edge lists must be int32 CUDA tensors")
