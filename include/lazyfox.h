@@ -86,7 +86,7 @@ typedef struct lf_options {
     int32_t hub_degree;      /* nodes of higher degree are evaluated with a table in global
                                 memory, in blocks of their own (per-queue launches: on a second
                                 stream); 0 (default) = 384 */
-    int32_t gain_rule;       /* decision rule of a move (LF_GAIN_*); 0: the library default */
+    int32_t gain_rule;       /* decision rule of a move (LF_GAIN_*); 0 (default): LF_GAIN_LITERAL */
 } lf_options;
 
 /* lf_options.gain_rule.  LF_GAIN_LITERAL is the paper's gain (Methods, Node

@@ -131,6 +131,34 @@ def f1_pair(k: int, a: int, b: int) -> float:
     return lib().og_f1_pair(int(k), int(a), int(b))
 
 
+def _run_one(job):
+    src, dst, q, threshold, max_iters, rule = job
+    g = OracleGraph(src, dst)
+    r = g.run(q, threshold, max_iters, rule=rule)
+    r["cc"] = g.cc
+    r["communities"] = [c.tolist() for c in g.communities()]
+    return r
+
+
+def run_many(edge_lists, queue_size, threshold, max_iters, rule=None, processes=None):
+    """Independent oracle runs of many graphs (objects with src/dst), one
+    spawned process per host core (largest graphs first); per graph the run's
+    record with its cc and final communities (lists of original ids), in the
+    order of `edge_lists`."""
+    import multiprocessing as mp
+    jobs = [(el.src, el.dst, queue_size, threshold, max_iters, rule) for el in edge_lists]
+    procs = min(len(jobs), processes or len(os.sched_getaffinity(0)))
+    if procs <= 1:
+        return [_run_one(j) for j in jobs]
+    order = sorted(range(len(jobs)), key=lambda i: -jobs[i][0].shape[0])
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_run_one, [jobs[i] for i in order], chunksize=1)
+    out = [None] * len(jobs)
+    for i, r in zip(order, res):
+        out[i] = r
+    return out
+
+
 class OracleGraph:
     """The oracle's view of one graph: preprocessing, triangles, order, runs."""
 
@@ -217,8 +245,8 @@ class OracleGraph:
 
     def set_gain_rule(self, rule: str):
         """Decision rule of the following runs: "literal" (the paper's gain, the
-        change of \\wcchat(P)) or "meanfield" (the change of the mean-field
-        community score, a departure kept as an option)."""
+        change of \\wcchat(P); the default) or "meanfield" (the change of the
+        mean-field community score, a departure kept as an option)."""
         if rule not in self.GAIN_RULES or lib().og_set_gain_rule(self._h, self.GAIN_RULES[rule]):
             raise ValueError(f"unknown gain rule {rule!r}")
 

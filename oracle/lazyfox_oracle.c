@@ -28,7 +28,8 @@
  *     the move (new size, new internal edge count, and for x's neighbours
  *     their deg(y,C) changed by one) and x's own term, less the same
  *     community's terms before it, added with the correctly rounded sum
- *     (OG_GAIN_LITERAL).  A departure kept as an option (OG_GAIN_MEANFIELD):
+ *     (OG_GAIN_LITERAL, the default).  A departure kept as an option
+ *     (OG_GAIN_MEANFIELD):
  *     the change of the community's mean-field score S(n, m, vol), every
  *     member given the mean internal degree 2m/n and mean total degree vol/n;
  *   - B(z) = C(z,2) for z >= 1, else 0;
@@ -192,7 +193,7 @@ og_graph *og_create(const int32_t *src, const int32_t *dst, int64_t num_edges, i
     og_graph *g = (og_graph *)calloc(1, sizeof(og_graph));
     if (!g) { *status = OG_ERR_OOM; return NULL; }
     g->part_k = -1;
-    g->gain_rule = OG_GAIN_MEANFIELD;
+    g->gain_rule = OG_GAIN_LITERAL;
     for (int64_t e = 0; e < num_edges; ++e) {
         if (src[e] < 0 || dst[e] < 0) { *status = OG_ERR_INVALID; free(g); return NULL; }
     }

@@ -106,7 +106,7 @@ struct lf_graph {
     int32_t barrier_mode = 0;                      // grid barrier: 0 flat flags, 1 central release flag
     int32_t warps_per_node = 0;                    // team size of the move evaluation (0: by queue size)
     int32_t hub_degree = 384;                      // above it a node takes the hub path
-    int32_t gain_rule = LF_GAIN_MEANFIELD;         // decision rule of the move evaluation
+    int32_t gain_rule = LF_GAIN_LITERAL;           // decision rule of the move evaluation (paper's gain)
     unsigned long long launches = 0;               // kernels launched (host count)
     std::vector<std::pair<void *, size_t>> live;   // outstanding allocations
 
@@ -232,7 +232,8 @@ struct lf_graph {
     int32_t *kmem = nullptr;              // n*K
     unsigned long long *cm_off = nullptr; // n+1
     unsigned long long *cm_cur = nullptr; // n+1
-    int32_t *cm_node = nullptr;           // n*K
+    int32_t *cm_node = nullptr;           // regions of (4 members + 32) entries per community
+    uint32_t *cm_cnt = nullptr;           // n: entries used per region
     int64_t cm_cap = 0;
     int32_t *jl_head = nullptr, *jl_next = nullptr, *jl_node = nullptr;   // n each
     uint32_t *lit_misc = nullptr;         // [0]: joiners listed in this iteration
@@ -243,6 +244,11 @@ struct lf_graph {
     int32_t *lit_over = nullptr;          // qcap
     int32_t *touched = nullptr;           // 2 qcap
     int64_t lit_qcap = 0;
+    unsigned long long *lit_used = nullptr;   // per queue: global table slots handed out
+    void *lg_area = nullptr;              // global tables: lg_cap slots of 20 bytes
+    unsigned long long lg_cap = 0;
+    int64_t lg_plan_q = -1, lg_plan_sched = -1;
+    int32_t lg_plan_K = 0;
     // second stream: hub chunks run beside the other evaluation kernels of a queue
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -90,13 +90,21 @@ struct RunArgs {
     // moves touched (null under the mean-field rule)
     int32_t *kmem;
     const unsigned long long *cm_off;
-    const int32_t *cm_node;
-    int32_t *jl_head, *jl_next, *jl_node;
+    int32_t *cm_node;
+    uint32_t *cm_cnt;   // entries used in each community's region (members at the start, then joiners)
+    int32_t *jl_head, *jl_next, *jl_node;   // joiners beyond a region's capacity
     uint32_t *jl_count;
     double *litF;
     int32_t *touched;
     uint32_t *ntouched;
     uint32_t *tstamp;
+    // tables in global memory for nodes with more entries than a block's
+    // shared table holds (bump-allocated per queue, lg_cap slots)
+    int32_t *lg_keys;
+    uint32_t *lg_vals;
+    int32_t *lg_aux;
+    double *lg_dv;
+    unsigned long long lg_cap;
 };
 
 // ---------------------------------------------------------------------------
@@ -1985,6 +1993,23 @@ __device__ __forceinline__ void lit_screen(const RunArgs &a, int32_t C, uint32_t
     E = ((double)(n + k) + 64.0) * 2.3e-16 * M + 1e-300;
 }
 
+// Every entry of C's member index -- the members at the iteration's start
+// and its joiners since, in C's region and, past its capacity, in C's list --
+// handed to f, entry t to thread `tid` of `nthreads` when t % nthreads == tid.
+// Entries of nodes that left C since are included (f checks the row).
+template <typename F>
+__device__ __forceinline__ void lit_members(const RunArgs &a, int32_t C, int tid, int nthreads, F &&f) {
+    const int64_t b0 = (int64_t)a.cm_off[C], cap = (int64_t)a.cm_off[C + 1] - b0;
+    const int64_t used = (int64_t)__ldcg(&a.cm_cnt[C]);
+    const int64_t b1 = b0 + (used < cap ? used : cap);
+    for (int64_t p = b0 + tid; p < b1; p += nthreads) f(__ldcg(&a.cm_node[p]));
+    if (used > cap) {
+        int idx = 0;
+        for (int32_t e = __ldcg(&a.jl_head[C]); e >= 0; e = __ldcg(&a.jl_next[e]), ++idx)
+            if (idx % nthreads == tid) f(__ldcg(&a.jl_node[e]));
+    }
+}
+
 // The exact gain of x joining (own = false) or leaving C: every member's term
 // after and before, x's own term, added into a signed superaccumulator (acc:
 // the warp's, zero on entry and on exit).  One warp.
@@ -2009,11 +2034,7 @@ __device__ double lit_exact_gain(const RunArgs &a, int32_t x, int32_t d, int32_t
         ssacc_add(acc, wcchat_member(k1, dy, n1, m21, cc));
         ssacc_add(acc, -wcchat_member(ky, dy, n0, m20, cc));
     };
-    const int64_t b0 = a.cm_off[C], b1 = a.cm_off[C + 1];
-    for (int64_t p = b0 + lane; p < b1; p += 32) member(__ldcg(&a.cm_node[p]));
-    int idx = 0;
-    for (int32_t e = __ldcg(&a.jl_head[C]); e >= 0; e = __ldcg(&a.jl_next[e]), ++idx)
-        if ((idx & 31) == lane) member(__ldcg(&a.jl_node[e]));
+    lit_members(a, C, lane, 32, member);
     if (lane == 0) ssacc_add(acc, own ? -wcchat_member(k, d, n0, m20, cc) : wcchat_member(k, d, n1, m21, cc));
     __syncwarp();
     double g = 0.0;
@@ -2419,10 +2440,11 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_lit_eval(RunArgs a, int64_t b
 // Listed nodes, one block each, over the block's whole table in as many
 // parts as needed (a part that overflows doubles the parts).
 __global__ void __launch_bounds__(EV_THREADS, 2) k_lit_big(RunArgs a, int64_t bstart, uint32_t *over,
-                                                          const int32_t *over_list) {
+                                                          const int32_t *over_list, unsigned long long *used) {
     extern __shared__ double lit_dyn[];
     __shared__ LitScratch ls;
     __shared__ int s_i;
+    __shared__ long long s_base;
     double *dv;
     int32_t *keys, *aux;
     uint32_t *vals;
@@ -2457,8 +2479,24 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_lit_big(RunArgs a, int64_t bs
         bound = 0;
         for (int k2 = 0; k2 < EV_WARPS; ++k2) bound += ls.part[k2];
         __syncthreads();
+        if (2 * bound > LB_SLOTS) {   // a table of its own in global memory, if the queue's area has room
+            unsigned long long H = 32;
+            while ((long long)H < 2 * bound) H <<= 1;
+            if (threadIdx.x == 0) {
+                const unsigned long long base = atomicAdd(used, H);
+                s_base = base + H <= a.lg_cap ? (long long)base : -1ll;
+            }
+            __syncthreads();
+            const long long base = s_base;
+            __syncthreads();
+            if (base >= 0) {
+                lit_eval_node<EV_WARPS>(a, i, ln, 1, a.lg_keys + base, a.lg_vals + base, a.lg_aux + base,
+                                        a.lg_dv + base, (uint32_t)H, ls, acc + w * SACC_CHUNKS, 0, w);
+                continue;
+            }
+        }
         int P = (int)((bound + LIT_PART_ENTRIES - 1) / LIT_PART_ENTRIES);
-        if (P < 1) P = 1;
+        if (P < 1 || 2 * bound <= LB_SLOTS) P = 1;
         while (!lit_eval_node<EV_WARPS>(a, i, ln, P, keys, vals, aux, dv, (uint32_t)LB_SLOTS, ls,
                                         acc + w * SACC_CHUNKS, 0, w)) {
             P *= 2;
@@ -2549,9 +2587,14 @@ __device__ void lit_apply_node(const RunArgs &a, int64_t bstart, int32_t blen, i
             atomicAdd(&a.comm[j].vol, (uint32_t)d);
             atomicAdd(&a.comm[j].m2, (uint32_t)(2 * kjoin + jj - 2 * jl));
             ++nj;
-            const int32_t e = (int32_t)atomicAdd(a.jl_count, 1u);
-            a.jl_node[e] = x;
-            a.jl_next[e] = atomicExch(&a.jl_head[j], e);
+            const unsigned long long slot = atomicAdd(&a.cm_cnt[j], 1u);
+            if ((long long)slot < (long long)(a.cm_off[j + 1] - a.cm_off[j])) {
+                a.cm_node[a.cm_off[j] + slot] = x;
+            } else {
+                const int32_t e = (int32_t)atomicAdd(a.jl_count, 1u);
+                a.jl_node[e] = x;
+                a.jl_next[e] = atomicExch(&a.jl_head[j], e);
+            }
             if (atomicExch(&a.tstamp[j], serial) != serial) a.touched[atomicAdd(a.ntouched, 1u)] = j;
         }
         a.nmem[x] = c_new;
@@ -2595,51 +2638,81 @@ __global__ void __launch_bounds__(AP_THREADS) k_lit_kupd(RunArgs a, int64_t bsta
 }
 
 // F(n-1), F(n), F(n+1) of communities: list[0 .. *count) (or every id below
-// ncount when list is null), one block per community.
+// ncount when list is null).  Blocks take eight entries at a time: each warp
+// sums a community of up to LIT_FSUM_WARP members alone, larger ones are then
+// summed by the whole block, one after the other.
+constexpr int LIT_FSUM_WARP = 512;
+
+__device__ __forceinline__ void lit_fsum_member(const RunArgs &a, int32_t C, int64_t n, int32_t y, double &f0,
+                                                double &f1, double &f2) {
+    const int32_t cy = __ldcg(&a.nmem[y]);
+    const int s = row_find(a.mem + (int64_t)y * a.K, cy, C);
+    if (s < 0) return;   // left C earlier in this iteration
+    const int64_t ky = __ldcg(&a.kmem[(int64_t)y * a.K + s]);
+    const int64_t dy = a.deg[y];
+    f0 += lit_g(ky, dy, n - 1);
+    f1 += lit_g(ky, dy, n);
+    f2 += lit_g(ky, dy, n + 1);
+}
+
 __global__ void __launch_bounds__(256) k_lit_fsum(RunArgs a, const int32_t *list, const uint32_t *count,
                                                   int64_t ncount) {
     __shared__ double red[3][8];
+    __shared__ int32_t big[8];
+    __shared__ int nbig;
     const int64_t total = list ? (int64_t)__ldcg(count) : ncount;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        const int32_t C = list ? __ldcg(&list[t]) : (int32_t)t;
-        const int64_t n = __ldcg(&a.comm[C].n);
-        double f0 = 0.0, f1 = 0.0, f2 = 0.0;
-        if (n > 0) {
-            auto member = [&](int32_t y) {
-                const int32_t cy = __ldcg(&a.nmem[y]);
-                const int s = row_find(a.mem + (int64_t)y * a.K, cy, C);
-                if (s < 0) return;
-                const int64_t ky = __ldcg(&a.kmem[(int64_t)y * a.K + s]);
-                const int64_t dy = a.deg[y];
-                f0 += lit_g(ky, dy, n - 1);
-                f1 += lit_g(ky, dy, n);
-                f2 += lit_g(ky, dy, n + 1);
-            };
-            const int64_t b0 = a.cm_off[C], b1 = a.cm_off[C + 1];
-            for (int64_t p = b0 + threadIdx.x; p < b1; p += blockDim.x) member(__ldcg(&a.cm_node[p]));
-            int idx = 0;
-            for (int32_t e = __ldcg(&a.jl_head[C]); e >= 0; e = __ldcg(&a.jl_next[e]), ++idx)
-                if (idx % (int)blockDim.x == (int)threadIdx.x) member(__ldcg(&a.jl_node[e]));
-        }
+    for (int64_t t0 = (int64_t)blockIdx.x * 8; t0 < total; t0 += (int64_t)gridDim.x * 8) {
+        if (threadIdx.x == 0) nbig = 0;
+        __syncthreads();
+        const int64_t t = t0 + w;
+        if (t < total) {
+            const int32_t C = list ? __ldcg(&list[t]) : (int32_t)t;
+            const int64_t n = __ldcg(&a.comm[C].n);
+            if (n > LIT_FSUM_WARP) {
+                if (lane == 0) big[atomicAdd(&nbig, 1)] = C;
+            } else {
+                double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+                if (n > 0)
+                    lit_members(a, C, lane, 32, [&](int32_t y) { lit_fsum_member(a, C, n, y, f0, f1, f2); });
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            f0 += __shfl_xor_sync(FULL, f0, o);
-            f1 += __shfl_xor_sync(FULL, f1, o);
-            f2 += __shfl_xor_sync(FULL, f2, o);
-        }
-        if (lane == 0) {
-            red[0][w] = f0;
-            red[1][w] = f1;
-            red[2][w] = f2;
-        }
-        __syncthreads();
-        if (threadIdx.x < 3) {
-            double s = 0.0;
-            for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) s += red[threadIdx.x][k2];
-            a.litF[3 * (int64_t)C + threadIdx.x] = s;
+                for (int o = 16; o > 0; o >>= 1) {
+                    f0 += __shfl_xor_sync(FULL, f0, o);
+                    f1 += __shfl_xor_sync(FULL, f1, o);
+                    f2 += __shfl_xor_sync(FULL, f2, o);
+                }
+                if (lane == 0) {
+                    a.litF[3 * (int64_t)C] = f0;
+                    a.litF[3 * (int64_t)C + 1] = f1;
+                    a.litF[3 * (int64_t)C + 2] = f2;
+                }
+            }
         }
         __syncthreads();
+        for (int b = 0; b < nbig; ++b) {
+            const int32_t C = big[b];
+            const int64_t n = __ldcg(&a.comm[C].n);
+            double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+            lit_members(a, C, threadIdx.x, blockDim.x, [&](int32_t y) { lit_fsum_member(a, C, n, y, f0, f1, f2); });
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                f0 += __shfl_xor_sync(FULL, f0, o);
+                f1 += __shfl_xor_sync(FULL, f1, o);
+                f2 += __shfl_xor_sync(FULL, f2, o);
+            }
+            if (lane == 0) {
+                red[0][w] = f0;
+                red[1][w] = f1;
+                red[2][w] = f2;
+            }
+            __syncthreads();
+            if (threadIdx.x < 3) {
+                double sum = 0.0;
+                for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) sum += red[threadIdx.x][k2];
+                a.litF[3 * (int64_t)C + threadIdx.x] = sum;
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -2665,12 +2738,19 @@ __global__ void k_lit_kinit(RunArgs a, int64_t n) {
 
 // Member index at an iteration's start: members per community, then (after
 // a scan into cm_off) every node listed under each of its communities.
-__global__ void k_lit_count(RunArgs a, int64_t n, unsigned long long *cnt) {
+__global__ void k_lit_count(RunArgs a, int64_t n, uint32_t *cnt) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
         const int32_t cx = a.nmem[x];
         const int32_t *row = a.mem + x * a.K;
-        for (int32_t s = 0; s < cx; ++s) atomicAdd(&cnt[row[s]], 1ull);
+        for (int32_t s = 0; s < cx; ++s) atomicAdd(&cnt[row[s]], 1u);
     }
+}
+
+// Region capacity of each community: its members at the start plus room
+// for 3 n + 32 joiners (more joiners go to the community's list).
+__global__ void k_lit_caps(const uint32_t *cnt, int64_t nc, unsigned long long *cap) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+        cap[c] = 4ull * cnt[c] + 32ull;
 }
 
 __global__ void k_lit_fill(RunArgs a, int64_t n, unsigned long long *cursor, int32_t *cm_node) {
@@ -3399,6 +3479,7 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.kmem = lit ? g->kmem : nullptr;
     a.cm_off = g->cm_off;
     a.cm_node = g->cm_node;
+    a.cm_cnt = g->cm_cnt;
     a.jl_head = g->jl_head;
     a.jl_next = g->jl_next;
     a.jl_node = g->jl_node;
@@ -3407,6 +3488,11 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.touched = g->touched;
     a.ntouched = g->lit_ctr;
     a.tstamp = g->tstamp;
+    a.lg_cap = g->lg_cap;
+    a.lg_dv = static_cast<double *>(g->lg_area);
+    a.lg_keys = reinterpret_cast<int32_t *>(a.lg_dv + g->lg_cap);
+    a.lg_vals = reinterpret_cast<uint32_t *>(a.lg_keys + g->lg_cap);
+    a.lg_aux = reinterpret_cast<int32_t *>(a.lg_vals + g->lg_cap);
     if (lit) a.screen = g->screen ? 1 : 0;   // brackets need no FP32 range condition
     return a;
 }
@@ -3643,6 +3729,7 @@ void launch_batches_lit(lf_graph *g, const RunArgs &a, int64_t q, int64_t first,
     static const int per_sm_big = blocks_per_sm(k_lit_big, EV_THREADS, LIT_SMEM);
     const unsigned big_grid = (unsigned)(num_sms() * std::max(1, per_sm_big));
     LF_CUDA(cudaMemsetAsync(g->lit_ctr + 3 * first, 0, (size_t)(3 * count) * sizeof(uint32_t), g->stream));
+    LF_CUDA(cudaMemsetAsync(g->lit_used + first, 0, (size_t)count * sizeof(unsigned long long), g->stream));
     const bool prof = g->profile && (int64_t)g->prof_ev.size() >= 2 * (first + count);
     for (int64_t b = first; b < first + count; ++b) {
         int64_t bstart;
@@ -3662,13 +3749,13 @@ void launch_batches_lit(lf_graph *g, const RunArgs &a, int64_t q, int64_t first,
         default: launch_pdl(k_lit_eval<8>, grid, EV_THREADS, LIT_SMEM, g->stream, ab, bstart, blen, ctr, g->lit_over); break;
         }
         launch_pdl(k_lit_big, std::min<unsigned>(big_grid, (unsigned)blen), EV_THREADS, LIT_SMEM, g->stream, ab,
-                   bstart, ctr, (const int32_t *)g->lit_over);
+                   bstart, ctr, (const int32_t *)g->lit_over, g->lit_used + b);
         if (prof) record_event(g, g->prof_ev[2 * b + 1], capturing);
         const unsigned ag = grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30);
         launch_pdl(k_lit_apply, ag, AP_THREADS, 0, g->stream, ab, bstart, blen, b);
         k_lit_kupd<<<ag, AP_THREADS, 0, g->stream>>>(ab, bstart, blen);
-        k_lit_fsum<<<(unsigned)std::min<int64_t>(2 * (int64_t)blen, 8 * (int64_t)num_sms()), 256, 0, g->stream>>>(
-            ab, g->touched, ctr + 2, 0);
+        k_lit_fsum<<<(unsigned)std::min<int64_t>((2 * (int64_t)blen + 7) / 8, 8 * (int64_t)num_sms()), 256, 0,
+                     g->stream>>>(ab, g->touched, ctr + 2, 0);
         g->launches += 5;
     }
     LF_LAUNCHED();
@@ -3686,11 +3773,13 @@ void ensure_lit(lf_graph *g, int64_t q, int64_t nb) {
         g->jl_node = dalloc_n<int32_t>(g, n);
         g->tstamp = dalloc_n<uint32_t>(g, n);
         g->lit_misc = dalloc_n<uint32_t>(g, 4);
+        g->cm_cnt = dalloc_n<uint32_t>(g, n);
     }
-    if (g->cm_cap < n * g->K) {
+    if (g->cm_cap < (4 * (int64_t)g->K + 32) * n) {   // regions: 4 (members) + 32 per community
         if (g->cm_node) dfree(g, g->cm_node);
-        g->cm_cap = n * g->K;
+        g->cm_cap = (4 * (int64_t)g->K + 32) * n;
         g->cm_node = dalloc_n<int32_t>(g, g->cm_cap);
+        drop_graph(g);
     }
     if (g->lit_qcap < q) {
         if (g->lit_over) dfree(g, g->lit_over);
@@ -3702,9 +3791,50 @@ void ensure_lit(lf_graph *g, int64_t q, int64_t nb) {
     }
     if (g->lit_ctr_cap < 3 * nb) {
         if (g->lit_ctr) dfree(g, g->lit_ctr);
+        if (g->lit_used) dfree(g, g->lit_used);
         g->lit_ctr_cap = 3 * nb;
         g->lit_ctr = dalloc_n<uint32_t>(g, 3 * nb);
+        g->lit_used = dalloc_n<unsigned long long>(g, nb);
         drop_graph(g);
+    }
+    // global tables: per queue, every node whose entries can exceed half a
+    // block's table gets pow2 >= 2 (d+1) K slots (K bounds every row, so
+    // (d+1) K bounds its entries); queues run one after the other and share
+    // the area, sized for the largest queue
+    if (g->lg_plan_q != q || g->lg_plan_K != g->K || g->lg_plan_sched != g->sched_version) {
+        g->lg_plan_q = q;
+        g->lg_plan_K = g->K;
+        g->lg_plan_sched = g->sched_version;
+        unsigned long long cap = 0;
+        if (g->n > 0 && (long long)(g->max_deg + 1) * g->K * 2 > LB_SLOTS) {
+            const int64_t len = g->sched.empty() ? g->n : g->sched.back();
+            std::vector<int32_t> order((size_t)std::max<int64_t>(len, 1)), deg((size_t)g->n);
+            if (len > 0)
+                LF_CUDA(cudaMemcpyAsync(order.data(), g->sched.empty() ? g->order : g->qorder, (size_t)len * 4,
+                                        cudaMemcpyDeviceToHost, g->stream));
+            LF_CUDA(cudaMemcpyAsync(deg.data(), g->deg, (size_t)g->n * 4, cudaMemcpyDeviceToHost, g->stream));
+            LF_CUDA(cudaStreamSynchronize(g->stream));
+            for (int64_t b = 0; b < nb; ++b) {
+                int64_t qs;
+                int32_t ql;
+                queue_bounds(g, q, b, qs, ql);
+                unsigned long long used = 0;
+                for (int64_t p2 = qs; p2 < qs + ql; ++p2) {
+                    const unsigned long long e = (unsigned long long)(deg[(size_t)order[(size_t)p2]] + 1) * g->K;
+                    if (2 * e <= (unsigned long long)LB_SLOTS) continue;
+                    unsigned long long H = 32;
+                    while (H < 2 * e) H <<= 1;
+                    used += H;
+                }
+                cap = std::max(cap, used);
+            }
+        }
+        if (cap != g->lg_cap) {
+            if (g->lg_area) dfree(g, g->lg_area);
+            g->lg_area = cap ? dalloc(g, (size_t)cap * 20) : nullptr;
+            g->lg_cap = cap;
+            drop_graph(g);
+        }
     }
 }
 
@@ -3714,16 +3844,22 @@ void lit_iteration_start(lf_graph *g, const RunArgs &a) {
     const int64_t n = g->n, nc = g->ncomm;
     if (n == 0 || nc == 0) return;
     cudaStream_t st = g->stream;
-    LF_CUDA(cudaMemsetAsync(g->cm_cur, 0, (size_t)nc * 8, st));
-    k_lit_count<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(a, n, g->cm_cur);
+    LF_CUDA(cudaMemsetAsync(g->cm_cnt, 0, (size_t)nc * 4, st));
+    k_lit_count<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(a, n, g->cm_cnt);
+    k_lit_caps<<<grid_for(nc, 256, 1 << 16), 256, 0, st>>>(g->cm_cnt, nc, g->cm_cur);
     LF_LAUNCHED();
     scan_exclusive<unsigned long long>(g, g->cm_cur, g->cm_off, nc, g->cm_off + nc);
     LF_CUDA(cudaMemcpyAsync(g->cm_cur, g->cm_off, (size_t)nc * 8, cudaMemcpyDeviceToDevice, st));
     k_lit_fill<<<grid_for(n, 256, 1 << 16), 256, 0, st>>>(a, n, g->cm_cur, g->cm_node);
     LF_CUDA(cudaMemsetAsync(g->jl_head, 0xff, (size_t)nc * 4, st));
     LF_CUDA(cudaMemsetAsync(g->lit_misc, 0, 4 * sizeof(uint32_t), st));
-    k_lit_fsum<<<(unsigned)std::min<int64_t>(nc, 16 * (int64_t)num_sms()), 256, 0, st>>>(a, nullptr, nullptr, nc);
-    g->launches += 3;
+    // touched-list stamps are queue serials of this iteration (a batch's queue
+    // count changes between iterations, so serials of different iterations
+    // may coincide): clear them
+    LF_CUDA(cudaMemsetAsync(g->tstamp, 0, (size_t)n * 4, st));
+    k_lit_fsum<<<(unsigned)std::min<int64_t>((nc + 7) / 8, 16 * (int64_t)num_sms()), 256, 0, st>>>(a, nullptr, nullptr,
+                                                                                                   nc);
+    g->launches += 4;
     LF_LAUNCHED();
 }
 
@@ -4142,7 +4278,14 @@ void free_run_state(lf_graph *g) {
             dfree(g, *pp);
             *pp = nullptr;
         }
-    for (uint32_t **pp : {&g->lit_misc, &g->tstamp, &g->lit_ctr})
+    if (g->lit_used) dfree(g, g->lit_used);
+    g->lit_used = nullptr;
+    if (g->lg_area) dfree(g, g->lg_area);
+    g->lg_area = nullptr;
+    g->lg_cap = 0;
+    g->lg_plan_q = g->lg_plan_sched = -1;
+    g->lg_plan_K = 0;
+    for (uint32_t **pp : {&g->lit_misc, &g->tstamp, &g->lit_ctr, &g->cm_cnt})
         if (*pp) {
             dfree(g, *pp);
             *pp = nullptr;
@@ -4299,7 +4442,6 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
     if (lit && n > 0) {   // deg(x,C) of every membership of the starting state
         ensure_lit(g, batch ? max_queue(g, q) : q, num_queues(g, q));
         a = make_args(g, device_readback(g));
-        LF_CUDA(cudaMemsetAsync(g->tstamp, 0, (size_t)n * 4, st));
         k_lit_kinit<<<grid_for(n * 32, 256, 1 << 16), 256, 0, st>>>(a, n); ++g->launches;
         LF_LAUNCHED();
     }

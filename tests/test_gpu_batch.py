@@ -1,7 +1,8 @@
 """Batches of independent graphs (lf_batch_create): one run covers all of
 them, and every graph must come out bit for bit as it does alone, against the
 oracle run on that graph alone (same totals per iteration, iterations,
-stopping, final communities)."""
+stopping, final communities) -- under the paper's gain (the default) and the
+mean-field departure."""
 import math
 
 import numpy as np
@@ -36,36 +37,39 @@ def mixed_graphs():
     return gs
 
 
-def check_batch(lf, oracle_lib, graphs, q, thr, max_iters):
-    with lf.Batch(graphs) as b:
+def check_batch(lf, oracle_lib, graphs, q, thr, max_iters, rule=None):
+    """Every graph of the batch against the oracle run on it alone (the
+    oracle runs in parallel, one process per host core)."""
+    refs = oracle_lib.run_many(graphs, q, thr, max_iters, rule=rule)
+    with lf.Batch(graphs, gain_rule=rule) as b:
         b.run(q, thr, max_iters)
         info = b.info()
         comms = b.graph_communities()
-        for i, el in enumerate(graphs):
-            og = oracle_lib.OracleGraph(el.src, el.dst)
-            ref = og.run(q, thr, max_iters)
-            assert info["cc"][i] == og.cc, i
+        for i, ref in enumerate(refs):
+            assert info["cc"][i] == ref["cc"], i
             assert info["iterations"][i] == ref["iterations"], i
             assert bool(info["converged"][i]) == ref["converged"], i
             assert info["wcc_initial"][i] == ref["T0"], i
             h = b.history(i)
             assert np.array_equal(h, ref["T"]), i
-            assert [c.tolist() for c in comms[i]] == [c.tolist() for c in og.communities()], i
+            assert [c.tolist() for c in comms[i]] == ref["communities"], i
 
 
+@pytest.mark.parametrize("rule", ["literal", "meanfield"])
 @pytest.mark.parametrize("q", [1, 64, 256, 1 << 20])
-def test_batch_equals_each_graph_alone(lf, oracle_lib, q):
-    check_batch(lf, oracle_lib, mixed_graphs(), q, 0.01, 50)
+def test_batch_equals_each_graph_alone(lf, oracle_lib, q, rule):
+    check_batch(lf, oracle_lib, mixed_graphs(), q, 0.01, 50, rule)
 
 
 def test_batch_fixed_iterations(lf, oracle_lib):
     check_batch(lf, oracle_lib, mixed_graphs(), 256, -math.inf, 4)
 
 
-def test_batch_of_the_batched_shape(lf, oracle_lib):
+@pytest.mark.parametrize("rule", ["literal", "meanfield"])
+def test_batch_of_the_batched_shape(lf, oracle_lib, rule):
     """The batched workload's shape (log-uniform sizes, degree 8-40) at 48
-    graphs of 200-5,000 nodes, queue size 256."""
-    check_batch(lf, oracle_lib, W.batched_planted(48, seed=9, n_lo=200, n_hi=5000), 256, 0.01, 50)
+    graphs of 200-4,000 nodes, queue size 256."""
+    check_batch(lf, oracle_lib, W.batched_planted(48, seed=9, n_lo=200, n_hi=4000), 256, 0.01, 50, rule)
 
 
 def test_batch_matches_single_graph_gpu_runs(lf):

@@ -185,3 +185,53 @@ def test_literal_full_power_law_workload(lf, oracle_lib):
     takes about half a minute)."""
     el = W.dblp_like()
     check_run(lf, oracle_lib.OracleGraph(el.src, el.dst), el, 1024)
+
+
+def test_literal_is_the_default_rule(lf, oracle_lib):
+    """Without a gain_rule option the library decides with the paper's gain,
+    as the oracle does by default."""
+    el = W.dblp_like(seed=3, scale=0.03)
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    assert og.gain_rule == "literal"
+    ref = og.run(64, 0.01, 50)
+    with lf.Graph(el.src, el.dst) as g:
+        compare_run(g.run(64, 0.01, 50), ref)
+        compare_state(g, og)
+
+
+def test_literal_full_power_law_workload_q64(lf, oracle_lib):
+    """The whole 335k-node power-law workload at queue size 64."""
+    el = W.dblp_like()
+    check_run(lf, oracle_lib.OracleGraph(el.src, el.dst), el, 64)
+
+
+def test_literal_edge_cases(lf, oracle_lib):
+    """Empty input, self-loops and repeated pairs only, ids near the int32
+    limit, max_iters = 0, and invalid arguments, with the default rule."""
+    with lf.Graph(np.zeros(0, np.int32), np.zeros(0, np.int32)) as g:
+        assert (g.n, g.m) == (0, 0)
+        st = g.run(4, 0.01, 5)
+        assert st.iterations == 1 and st.wcc_initial == 0.0
+        off, mem = g.communities()
+        assert off.tolist() == [0] and mem.shape[0] == 0
+    big = 2**31 - 1
+    src = np.array([5, 5, big, big - 7, big], np.int32)
+    dst = np.array([5, 5, big - 7, big, big - 7], np.int32)
+    og = oracle_lib.OracleGraph(src, dst)
+    with lf.Graph(src, dst) as g:
+        assert (g.n, g.m) == (2, 1)
+        compare_run(g.run(1, 0.01, 10), og.run(1, 0.01, 10))
+    el = W.from_pairs(W.clique(4) + [(0, 4)])
+    og = oracle_lib.OracleGraph(el.src, el.dst)
+    ref = og.run(1, 0.01, 0)
+    with lf.Graph(el.src, el.dst) as g:
+        st = g.run(1, 0.01, 0)
+        assert st.iterations == 0 and st.wcc_initial == ref["T0"]
+        assert [c.tolist() for c in g.community_list()] == [[0, 1, 2, 3], [4]]
+    with pytest.raises(ValueError):
+        lf.Graph(el.src, el.dst, gain_rule="bogus")
+    with lf.Graph(el.src, el.dst) as g:
+        with pytest.raises(lf.LazyFoxError):
+            g.run(0, 0.01, 5)
+        with pytest.raises(lf.LazyFoxError):
+            g.communities()

@@ -1,4 +1,9 @@
-"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, under the
+mean-field gain rule (the departure kept as an option; the paper's gain has
+its own file, tests/test_gpu_literal.py).  The preprocessing checks do not
+depend on the rule; the run checks cover the mean-field kernels: the
+persistent queue loop and its bounded barrier, the FP32 screen, the team,
+block and hub tiers.
 
 Integer and index results must be bit-exact: CSR, labels, orientation,
 t(x,V), vt(x,V), node order, initial clustering, per-queue and per-iteration
@@ -19,6 +24,25 @@ pytestmark = pytest.mark.gpu
 T_REL = 1e-9
 
 
+class _MeanField:
+    """The binding (or the oracle) with every graph on the mean-field rule."""
+
+    def __init__(self, mod):
+        self._m = mod
+
+    def __getattr__(self, k):
+        return getattr(self._m, k)
+
+    def Graph(self, *a, **kw):
+        kw.setdefault("gain_rule", "meanfield")
+        return self._m.Graph(*a, **kw)
+
+    def OracleGraph(self, *a, **kw):
+        g = self._m.OracleGraph(*a, **kw)
+        g.set_gain_rule("meanfield")
+        return g
+
+
 @pytest.fixture(scope="module")
 def lf():
     import torch
@@ -28,7 +52,14 @@ def lf():
     build.build()
     from paper_2210_03211_gb300 import lazyfox
     lazyfox.load_library()
-    return lazyfox
+    return _MeanField(lazyfox)
+
+
+@pytest.fixture(scope="module")
+def oracle_lib():
+    import oracle
+    oracle.build()
+    return _MeanField(oracle)
 
 
 def small_cases():

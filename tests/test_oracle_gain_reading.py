@@ -1,11 +1,12 @@
-"""Pins of the oracle's diagnostic of the gain reading.  The run's decisions use
-the mean-field community score (the reading of Joining / Leaving a Community
-that needs only per-community aggregates); the diagnostic takes the same
-decisions with the literal gain -- the change of the paper's \\wcchat(P), the
-sum of the per-node estimator over all memberships -- and counts how often the
-two agree.  The literal gain is pinned here to differences of the oracle's
-own totals on inserted covers (Methods, Initial Clustering: inserted
-divisions), to a hand derivation on the bowtie, and to a brute-force choice."""
+"""Pins of the paper's gain and of the diagnostic that compares the two gain
+rules.  The literal gain -- the change of the paper's \\wcchat(P), the sum of
+the per-node estimator over all memberships (Joining / Leaving a Community)
+-- decides runs by default; the mean-field departure scores a community from
+its aggregates alone.  The diagnostic takes every decision with both rules on
+the same snapshot and counts how often they agree.  The literal gain is
+pinned here to differences of the oracle's own totals on inserted covers
+(Methods, Initial Clustering: inserted divisions), to a hand derivation on
+the bowtie, and to a brute-force choice."""
 import math
 
 import numpy as np
@@ -122,7 +123,7 @@ def test_diagnostic_sees_the_run_decisions(oracle_lib):
     el = W.planted_er(n=120, num_comms=6, size_lo=10, size_hi=30, p_in=0.3, seed=3)
     og = oracle_lib.OracleGraph(el.src, el.dst)
     og.set_literal_diagnostic(True)
-    r = og.run(4, 0.01, 50)
+    r = og.run(4, 0.01, 50, rule="meanfield")
     d = og.literal_diagnostic()
     assert d["evaluations"] == og.n * r["iterations"]
     assert d["joins_meanfield"] == int(r["joins"].sum())
@@ -130,7 +131,7 @@ def test_diagnostic_sees_the_run_decisions(oracle_lib):
     assert d["same_both"] <= min(d["same_join"], d["same_leave"]) <= d["evaluations"]
     # the diagnostic changes nothing in the run
     og.set_literal_diagnostic(False)
-    r2 = og.run(4, 0.01, 50)
+    r2 = og.run(4, 0.01, 50, rule="meanfield")
     assert r2["iterations"] == r["iterations"] and np.array_equal(r2["T"], r["T"])
     assert og.literal_diagnostic()["evaluations"] == 0
 
