@@ -35,6 +35,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -43,23 +45,35 @@ METRIC = "edges/s per Fox iteration + triangle-count GB/s; batched graphs/s & p9
 UNIT = "edges/s per iteration"
 FALLBACK_HBM_GBS = 6800.0
 
+# cpu_sample: the bounded sample of the workload the oracle is timed on (the
+# cpu_baseline leg and the reference arm), when a whole run is too long.
 WORKLOADS = {
+    # 3.07M nodes, ~115M edges, Chung-Lu gamma 2.2, max degree ~33k, planted
+    # communities of 10-5,000 nodes; queue size 65536, 20 iterations
+    "large": dict(name="large_like_3.07M_nodes_115M_edges", gen=("large_like", {}), q=65536,
+                  threshold=-math.inf, max_iters=20,
+                  cpu_sample=dict(gen=("large_like", {"scale": 0.02}), max_iters=1,
+                                  what="the same generator at 2% scale (61,400 nodes, 2.07M edges): preprocessing "
+                                       "and the first iteration at queue size 65536 (one queue holds every node)"),
+                  secondary=[dict(workload="large", q=65536, rule="meanfield"),
+                             dict(workload="dblp", q=1024, rule="literal"),
+                             dict(workload="dblp", q=64, rule="literal"),
+                             dict(workload="dblp", q=1024, rule="meanfield")]),
     # 335k nodes, ~0.93M edges, Chung-Lu gamma 2.5, max degree ~550, planted
     # overlapping communities (sizes 6-2,000, 1-4 per node), seed 1
-    "dblp": dict(name="dblp_like_335k_nodes_0.93M_edges", gen=("dblp_like", {}), q=1024, q2=64,
-                 threshold=0.01, max_iters=50),
+    "dblp": dict(name="dblp_like_335k_nodes_0.93M_edges", gen=("dblp_like", {}), q=1024, threshold=0.01,
+                 max_iters=50, cpu_sample=None,
+                 secondary=[dict(workload="dblp", q=64, rule="literal"),
+                            dict(workload="dblp", q=1024, rule="meanfield")]),
     # 1,000 nodes, 20 planted communities, Fox (queue size 1)
-    "eu": dict(name="eu_core_like_1k_nodes_planted_er", gen=("eu_core_like", {}), q=1, q2=0,
-               threshold=0.01, max_iters=50),
-    # 3.07M nodes, Chung-Lu gamma 2.2, max degree ~33k, 20 iterations
-    "large": dict(name="large_like_3.07M_nodes", gen=("large_like", {}), q=65536, q2=1024,
-                  threshold=-math.inf, max_iters=20),
+    "eu": dict(name="eu_core_like_1k_nodes_planted_er", gen=("eu_core_like", {}), q=1, threshold=0.01,
+               max_iters=50, cpu_sample=None, secondary=[]),
     # 4,096 planted graphs, nodes log-uniform 200-20k, average degree 8-40,
     # one batch per step against one graph per call
-    "batched": dict(name="batched_planted_graphs_200-20k_nodes_deg_8-40", gen=None, q=256, q2=0,
+    "batched": dict(name="batched_planted_graphs_200-20k_nodes_deg_8-40", gen=None, q=256,
                     threshold=0.01, max_iters=50),
     # Poisson stream of planted graphs, nodes log-uniform 1k-2M, degree 10-80
-    "serving": dict(name="serving_poisson_planted_graphs_1k-2M_nodes_deg_10-80", gen=None, q=1024, q2=0,
+    "serving": dict(name="serving_poisson_planted_graphs_1k-2M_nodes_deg_10-80", gen=None, q=1024,
                     threshold=0.01, max_iters=50),
 }
 
@@ -67,12 +81,14 @@ WORKLOADS = {
 def parse_args():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lazyfox", "reference"], default="lazyfox")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dblp")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
+    ap.add_argument("--gain-rule", choices=["literal", "meanfield"], default="literal",
+                    help="decision rule of a move: the paper's gain (change of WCC-hat(P)) or the mean-field departure")
     ap.add_argument("--queue-size", type=int, default=None)
-    ap.add_argument("--no-secondary", action="store_true", help="skip the second queue size")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the secondary lines (other rule, other workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=4096, help="graphs per batch (batched workload)")
@@ -90,6 +106,14 @@ def make_workload(spec):
     from paper_2210_03211_gb300 import workloads as W
     fn, kw = spec["gen"]
     return getattr(W, fn)(**kw)
+
+
+def cpu_sample_graph(spec):
+    """The graph the oracle is timed on, its iteration limit and what it is."""
+    smp = spec.get("cpu_sample")
+    if smp is None:
+        return make_workload(spec), spec["max_iters"], "one full run (preprocessing and every iteration) of the workload"
+    return make_workload(smp), smp["max_iters"], smp["what"]
 
 
 def measured_hbm():
@@ -209,12 +233,12 @@ def barrier(world: int):
         dist.barrier()
 
 
-def time_oracle(el, q, threshold, max_iters):
+def time_oracle(el, q, threshold, max_iters, rule="literal"):
     import oracle
     oracle.build()
     t0 = time.perf_counter()
     og = oracle.OracleGraph(el.src, el.dst)
-    r = og.run(q, threshold, max_iters)
+    r = og.run(q, threshold, max_iters, rule=rule)
     dt = time.perf_counter() - t0
     return og.m * r["iterations"], dt, r["iterations"]
 
@@ -227,11 +251,11 @@ def _oracle_worker_ready(_):
 
 
 def _oracle_graph_seconds(job):
-    src, dst, q, threshold, max_iters = job
+    src, dst, q, threshold, max_iters, rule = job
     import oracle
     t0 = time.perf_counter()
     og = oracle.OracleGraph(src, dst)
-    og.run(q, threshold, max_iters)
+    og.run(q, threshold, max_iters, rule=rule)
     return time.perf_counter() - t0
 
 
@@ -257,7 +281,7 @@ def host_info() -> dict:
     return {"nproc": host_cores(), "machine": platform.machine(), "cpu_model": model}
 
 
-def oracle_graphs_per_s(graphs, q, threshold, max_iters, cores):
+def oracle_graphs_per_s(graphs, q, threshold, max_iters, cores, rule="literal"):
     """The oracle on independent graphs, one process per host core: a 'spawn'
     pool (safe after GPU calls), every worker started and the oracle loaded
     before the clock starts, the largest graphs handed out first.  Returns
@@ -265,13 +289,26 @@ def oracle_graphs_per_s(graphs, q, threshold, max_iters, cores):
     import multiprocessing as mp
     import oracle
     oracle.build()
-    jobs = sorted(((g.src, g.dst, q, threshold, max_iters) for g in graphs), key=lambda j: -j[0].shape[0])
+    jobs = sorted(((g.src, g.dst, q, threshold, max_iters, rule) for g in graphs), key=lambda j: -j[0].shape[0])
     with mp.get_context("spawn").Pool(cores) as pool:
         pool.map(_oracle_worker_ready, range(cores), chunksize=1)
         t0 = time.perf_counter()
         secs = list(pool.imap_unordered(_oracle_graph_seconds, jobs, chunksize=1))
         wall = time.perf_counter() - t0
     return len(jobs) / wall, sum(secs)
+
+
+def oracle_batch_sample(graphs, cores):
+    """The CPU baseline's sample of a batch: its first 2 x cores graphs of at
+    most 5,000 nodes (the paper's gain costs the oracle a pass over each
+    candidate community, so larger planted graphs take minutes each)."""
+    out = []
+    for g in graphs:
+        if np.unique(np.concatenate([g.src, g.dst])).shape[0] <= 5000:
+            out.append(g)
+            if len(out) == max(8, 2 * cores):
+                break
+    return out
 
 
 def run_reference(args, spec, q):
@@ -281,10 +318,11 @@ def run_reference(args, spec, q):
     if spec["gen"] is None:   # batched / serving: the oracle on a sample of the graphs, one process per core
         from paper_2210_03211_gb300 import workloads as W
         cores = host_cores()
-        graphs = (W.batched_planted(min(args.batch_graphs, max(32, 2 * cores)), seed=5)
-                  if args.workload == "batched" else W.serving_jobs(max(8, cores), seed=7, n_hi=20000)[0])
-        value, cpu_s = oracle_graphs_per_s(graphs, q, spec["threshold"], spec["max_iters"], cores)
-        what = "batch" if args.workload == "batched" else "job stream (nodes capped at 20k)"
+        graphs = (oracle_batch_sample(W.batched_planted(args.batch_graphs, seed=5), cores)
+                  if args.workload == "batched" else W.serving_jobs(max(8, cores), seed=7, n_hi=5000)[0])
+        value, cpu_s = oracle_graphs_per_s(graphs, q, spec["threshold"], spec["max_iters"], cores, args.gain_rule)
+        what = ("batch with at most 5,000 nodes" if args.workload == "batched"
+                else "job stream (nodes capped at 5k)")
         line = {"metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": args.gpus, "steps": 1,
                 "warmup": 0, "ms_per_step": 1e3 * len(graphs) / value, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
@@ -296,12 +334,12 @@ def run_reference(args, spec, q):
                 "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
-    el = make_workload(spec)
-    for _ in range(args.warmup):
-        time_oracle(el, q, spec["threshold"], spec["max_iters"])
+    el, max_iters, what = cpu_sample_graph(spec)
+    for _ in range(min(args.warmup, 1)):   # the oracle has no caches to warm; one untimed run loads it
+        time_oracle(el, q, spec["threshold"], max_iters, args.gain_rule)
     units, secs, iters = 0.0, 0.0, []
     for _ in range(args.steps):
-        u, dt, it = time_oracle(el, q, spec["threshold"], spec["max_iters"])
+        u, dt, it = time_oracle(el, q, spec["threshold"], max_iters, args.gain_rule)
         units += u
         secs += dt
         iters.append(it)
@@ -312,10 +350,9 @@ def run_reference(args, spec, q):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
         "impl": "reference",
         "config": {"workload": spec["name"], "queue_size": q, "threshold": spec["threshold"],
-                   "max_iters": spec["max_iters"], "iterations": iters},
+                   "max_iters": spec["max_iters"], "gain_rule": args.gain_rule, "iterations": iters},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full runs (preprocessing + all iterations) of the workload",
-                         "host": host_info()},
+                         "sample": f"each step: {what}", "host": host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -348,7 +385,8 @@ def run_batched(args, spec, q):
     edges = sum(int(g.src.shape[0]) for g in graphs)
     stream = torch.cuda.Stream(dev)
     # the launch shape, chosen once by the library's autotuner on this batch
-    with lazyfox.Batch(graphs, stream=stream) as b:
+    rule = args.gain_rule
+    with lazyfox.Batch(graphs, stream=stream, gain_rule=rule) as b:
         tune = b.autotune(q, 1)
     shape = dict(warps_per_node=tune["warps_per_node"], warp_max_degree=tune["warp_max_degree"],
                  hub_degree=tune["hub_degree"])
@@ -357,7 +395,7 @@ def run_batched(args, spec, q):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        with lazyfox.Batch(graphs, stream=stream, **shape) as b:
+        with lazyfox.Batch(graphs, stream=stream, gain_rule=rule, **shape) as b:
             b.run(q, spec["threshold"], spec["max_iters"])
             comms = b.graph_communities()
             it = b.info()["iterations"]
@@ -382,14 +420,14 @@ def run_batched(args, spec, q):
     sample = graphs[:max(1, min(args.plain_sample, G))]
     lat = []
     for el in sample[:2]:   # warm-up
-        with lazyfox.Graph(el.src, el.dst, stream=stream) as g:
+        with lazyfox.Graph(el.src, el.dst, stream=stream, gain_rule=rule) as g:
             g.run(q, spec["threshold"], spec["max_iters"])
             g.communities()
     for el in sample:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        with lazyfox.Graph(el.src, el.dst, stream=stream) as g:
+        with lazyfox.Graph(el.src, el.dst, stream=stream, gain_rule=rule) as g:
             g.run(q, spec["threshold"], spec["max_iters"])
             g.communities()
             e1.record(stream)
@@ -400,24 +438,24 @@ def run_batched(args, spec, q):
     # the sampled graphs' results, alone and in the batch, must agree
     same = True
     for i, el in enumerate(sample[:32]):
-        with lazyfox.Graph(el.src, el.dst, stream=stream) as g:
+        with lazyfox.Graph(el.src, el.dst, stream=stream, gain_rule=rule) as g:
             g.run(q, spec["threshold"], spec["max_iters"])
             same &= [c.tolist() for c in g.community_list()] == [c.tolist() for c in res[-1][1][i]]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
-        cpu_sample = graphs[:max(32, 2 * cores)]
-        cpu_gps, cpu_s = oracle_graphs_per_s(cpu_sample, q, spec["threshold"], spec["max_iters"], cores)
+        cpu_sample = oracle_batch_sample(graphs, cores)
+        cpu_gps, cpu_s = oracle_graphs_per_s(cpu_sample, q, spec["threshold"], spec["max_iters"], cores, rule)
         cpu = {"value": cpu_gps, "unit": "graphs/s", "cores": cores, "kind": "oracle",
-               "sample": f"the first {len(cpu_sample)} graphs of the batch, one oracle process per host core "
-                         f"({cpu_s:.1f} CPU seconds)", "host": host_info()}
+               "sample": f"the first {len(cpu_sample)} graphs of the batch with at most 5,000 nodes, one oracle "
+                         f"process per host core ({cpu_s:.1f} CPU seconds; gain rule {rule})", "host": host_info()}
     if rank == 0:
         batch_ms = np.array([r[0] for r in res])
         line = {
             "metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
-            "config": {"workload": spec["name"], "graphs": G, "edges": edges, "queue_size": q,
+            "config": {"workload": spec["name"], "graphs": G, "edges": edges, "queue_size": q, "gain_rule": rule,
                        "threshold": spec["threshold"], "max_iters": spec["max_iters"],
                        "iterations_max": int(max(res[-1][2])), "parallelism": f"replicas x{world}",
                        "timed": "lf_batch_create (host edge lists, copied in) + lf_run + communities of every graph",
@@ -526,6 +564,7 @@ def run_serving(args, spec, q):
             "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": total_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
             "config": {"workload": spec["name"], "jobs": J, "rate_per_s": args.rate, "max_nodes": args.max_nodes,
+                       "gain_rule": "literal (the library default, in the server and the plain calls)",
                        "edges": int(sum(g.src.shape[0] for g in graphs)), "queue_size": q, "threshold": thr,
                        "max_iters": it, "max_active": args.max_active, "parallelism": f"replicas x{world}",
                        "timed": "first arrival to last result; each job from host edge list to host communities"},
@@ -570,6 +609,7 @@ def main():
         lf_build.build()
     barrier(world)
     lazyfox.load_library()
+    rule = args.gain_rule
     el = make_workload(spec)
     src_d = torch.from_numpy(el.src).to(dev)
     dst_d = torch.from_numpy(el.dst).to(dev)
@@ -577,35 +617,38 @@ def main():
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize(dev)
     # launch shape chosen once by the library's autotuner (two-iteration trials, untimed)
-    with lazyfox.Graph(src_d, dst_d, stream=stream) as g0:
+    with lazyfox.Graph(src_d, dst_d, stream=stream, gain_rule=rule) as g0:
         tune = g0.autotune(q, 2)
     shape = dict(warps_per_node=tune["warps_per_node"], warp_max_degree=tune["warp_max_degree"],
                  hub_degree=tune["hub_degree"])
 
-    def one_step(queue, profile, use_graphs=True):
+    def one_step(s_d, d_d, queue, thr, iters, gain_rule, profile=False, use_graphs=True, shp=None):
         with torch.cuda.stream(stream):
             flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        g = lazyfox.Graph(src_d, dst_d, stream=stream, profile=profile, use_graphs=use_graphs,
-                          **(shape if queue == q else {}))
-        st = g.run(queue, spec["threshold"], spec["max_iters"])
+        g = lazyfox.Graph(s_d, d_d, stream=stream, profile=profile, use_graphs=use_graphs, gain_rule=gain_rule,
+                          **(shp or {}))
+        st = g.run(queue, thr, iters)
         e1.record(stream)
         cs = g.create_stats()
         g.close()
         stream.synchronize()
         return e0.elapsed_time(e1), st, cs
 
-    def timed(queue, steps, warmup, mark=False):
+    def step(profile=False, use_graphs=True):
+        return one_step(src_d, dst_d, q, spec["threshold"], spec["max_iters"], rule, profile, use_graphs, shape)
+
+    def timed(fn, steps, warmup, mark=False):
         for _ in range(warmup):
-            one_step(queue, False)
+            fn()
         torch.cuda.synchronize(dev)
         barrier(world)
         torch.cuda.synchronize(dev)
         if mark:   # a profiler attached with --profile-from-start off sees the timed steps only
             torch.cuda.profiler.start()
-        res = [one_step(queue, False) for _ in range(steps)]
+        res = [fn() for _ in range(steps)]
         torch.cuda.synchronize(dev)
         if mark:
             torch.cuda.profiler.stop()
@@ -620,7 +663,7 @@ def main():
         pass
     sampler = ClockSampler(gpu_id)
     sampler.start()
-    res = timed(q, args.steps, args.warmup, mark=True)
+    res = timed(step, args.steps, args.warmup, mark=True)
     clocks = sampler.stop()
 
     m = res[0][2]["num_edges"]
@@ -629,28 +672,38 @@ def main():
     total_ms = reduce_max(local_ms, world, dev)
     units = reduce_sum(local_units, world, dev)
     value = units / (total_ms / 1e3)
-    # triangle-count throughput: merge-stream bytes / triangle kernel time
+    step_s = local_ms / 1e3 / len(res)
+    # triangle counting: merge-stream elements per second (a work rate, not
+    # an HBM fraction: the kernels are issue-bound and re-read lists from L2)
     tri_gbs = statistics.median(r[2]["merge_bytes"] / (r[2]["ms_triangles"] / 1e3) / 1e9 for r in res
                                 if r[2]["ms_triangles"] > 0) if m > 0 else 0.0
     launches = sum(r[2]["num_launches"] + r[1].num_launches for r in res)
-    # the queue kernels' launch times come from profiled steps of the same
+    # the move evaluation's launch times come from profiled steps of the same
     # workload right after the timed region (profile mode records CUDA events
-    # around every such launch and counts their algorithmic bytes; it is kept
-    # out of the timed steps because the events and the byte counter cost time)
-    prof = [one_step(q, True) for _ in range(max(1, min(args.steps, 2)))]
+    # around each queue's evaluation launches and counts their algorithmic
+    # bytes; it is kept out of the timed steps because the events and the byte
+    # counter cost time)
+    nprof = 1 if step_s > 5 else max(1, min(args.steps, 2))
+    prof = [step(profile=True) for _ in range(nprof)]
     roofline_src = "profiled steps of the same workload right after the timed region"
     if any(math.isnan(r[1].prof_move_ms) for r in prof):
-        prof = [one_step(q, True, use_graphs=False) for _ in range(max(1, min(args.steps, 2)))]
+        prof = [step(profile=True, use_graphs=False) for _ in range(nprof)]
         roofline_src = "profiled steps with direct launches right after the timed region"
-    qpct = list(prof[-1][1].prof_queue_us) if q <= 256 else None
+    persistent = rule == "meanfield" and q <= 256
+    qpct = list(prof[-1][1].prof_queue_us) if persistent else None
     ev_bytes = sum(r[1].prof_move_bytes for r in prof)
     ev_ms = sum(r[1].prof_move_ms for r in prof)
     ev_launches = sum(r[1].prof_move_launches for r in prof)
     peak, peak_kind = measured_hbm()
     achieved = (ev_bytes / (ev_ms / 1e3) / 1e9) if ev_ms > 0 else 0.0
-    traffic = ncu_traffic("k_eval")
-    kname = ("k_eval (move evaluation, one launch per queue)" if q > 256 else
-             "k_iterate (persistent kernel: evaluate + apply of every queue, one launch per iteration)")
+    if rule == "literal":
+        kname = ("k_lit_eval + k_lit_big (move evaluation under the paper's gain; one launch = one queue's "
+                 "evaluation kernels)")
+        traffic = ncu_traffic("k_lit_eval")
+    else:
+        kname = ("k_eval (move evaluation, one launch per queue)" if not persistent else
+                 "k_iterate (persistent kernel: evaluate + apply of every queue, one launch per iteration)")
+        traffic = ncu_traffic("k_eval")
     roofline = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": achieved / peak, "bytes_per_launch": ev_bytes / max(1, ev_launches),
@@ -659,13 +712,26 @@ def main():
     if qpct:
         roofline["queue_us_p50_p90_p99_max"] = qpct
 
-    secondary = None
-    if spec["q2"] and not args.no_secondary:
-        res2 = timed(spec["q2"], args.steps, 1)
-        u2 = sum(m * r[1].iterations for r in res2)
-        ms2 = reduce_max(sum(r[0] for r in res2), world, dev)
-        secondary = {"queue_size": spec["q2"], "value": reduce_sum(u2, world, dev) / (ms2 / 1e3),
-                     "ms_per_step": ms2 / len(res2), "iterations": [r[1].iterations for r in res2]}
+    secondary = []
+    if not args.no_secondary:
+        graphs = {args.workload: (src_d, dst_d)}
+        for sec in spec.get("secondary", []):
+            wl = sec["workload"]
+            sspec = WORKLOADS[wl]
+            if wl not in graphs:
+                sel = make_workload(sspec)
+                graphs[wl] = (torch.from_numpy(sel.src).to(dev), torch.from_numpy(sel.dst).to(dev))
+            s_d, d_d = graphs[wl]
+            fn = (lambda s_d=s_d, d_d=d_d, sec=sec, sspec=sspec:
+                  one_step(s_d, d_d, sec["q"], sspec["threshold"], sspec["max_iters"], sec["rule"]))
+            r2 = timed(fn, max(1, min(args.steps, 2)), 1)
+            m2 = r2[0][2]["num_edges"]
+            u2 = sum(m2 * r[1].iterations for r in r2)
+            ms2 = reduce_max(sum(r[0] for r in r2), world, dev)
+            secondary.append({"workload": sspec["name"], "queue_size": sec["q"], "gain_rule": sec["rule"],
+                              "value": reduce_sum(u2, world, dev) / (ms2 / 1e3), "unit": UNIT,
+                              "ms_per_step": ms2 / len(r2), "iterations": [r[1].iterations for r in r2]})
+        del graphs
 
     e2e = None
     if not args.no_e2e:
@@ -673,11 +739,11 @@ def main():
         dst_h = torch.from_numpy(el.dst).pin_memory()
         src_np, dst_np = src_h.numpy(), dst_h.numpy()
         e_units, e_secs, d2h = 0.0, 0.0, 0
-        nsteps = max(1, min(args.steps, 3))
+        nsteps = 1 if step_s > 5 else max(1, min(args.steps, 3))
         for i in range(nsteps + 1):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            g = lazyfox.Graph(src_np, dst_np, **shape)
+            g = lazyfox.Graph(src_np, dst_np, gain_rule=rule, **shape)
             st = g.run(q, spec["threshold"], spec["max_iters"])
             off, mem = g.communities()
             t1 = time.perf_counter()
@@ -694,9 +760,10 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        u, dt, it = time_oracle(el, q, spec["threshold"], spec["max_iters"])
+        cel, citers, what = cpu_sample_graph(spec)
+        u, dt, it = time_oracle(cel, q, spec["threshold"], citers, rule)
         cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one full run (preprocessing + {it} iterations) of the same workload at queue size {q}",
+               "sample": f"{what} ({it} iteration(s), queue size {q}, gain rule {rule})",
                "seconds": dt, "host": host_info()}
 
     if rank == 0:
@@ -707,9 +774,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64", "data": "synthetic",
             "config": {"workload": spec["name"], "n": r0[2]["num_nodes"], "m": m, "queue_size": q,
                        "threshold": spec["threshold"], "max_iters": spec["max_iters"],
+                       "gain_rule": rule + (" (the paper's: change of WCC-hat(P))" if rule == "literal" else
+                                            " (departure: mean-field community score)"),
                        "iterations": [r[1].iterations for r in res], "parallelism": f"replicas x{world}",
                        "l2": "flushed before every step (256 MiB write); inputs resident in HBM"},
             "triangle_gbs": tri_gbs,
+            "triangle_gbs_kind": ("work rate: merge-stream bytes (4 per list element streamed) per second of the "
+                                  "triangle kernels; not DRAM traffic -- the kernels are issue-bound and re-read "
+                                  "lists from L2 (ncu: DRAM at 10-12% of peak)"),
             "breakdown_ms": {"create": statistics.median(
                 r[2]["ms_csr"] + r[2]["ms_orient"] + r[2]["ms_triangles"] + r[2]["ms_vt"] + r[2]["ms_order"]
                 for r in res),

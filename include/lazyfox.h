@@ -336,7 +336,9 @@ lf_status lf_batch_get_communities(lf_graph *g, int64_t *graph_offsets, int64_t 
  * runs: warps per evaluated node (1, 2, 4 or the automatic choice) and the
  * degree above which a node is evaluated by a whole block instead of warps
  * (no limit, 96 or 192) and the degree above which it takes the hub path
- * (384 or 128).  Every candidate computes the same result (the shape
+ * (384 or 128) -- 24 shapes under LF_GAIN_MEANFIELD; under LF_GAIN_LITERAL
+ * only the warps per node (4 shapes; the degree limits belong to the
+ * mean-field kernels).  Every candidate computes the same result (the shape
  * changes only which threads do the work), so the choice affects speed only.
  * queue_size: the queue size the later runs will use; trial_iters (>= 1)
  * iterations per trial.  result (may be NULL): the chosen shape, its time and

@@ -454,10 +454,15 @@ lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_t
         cudaEvent_t e0, e1;
         LF_CUDA(cudaEventCreate(&e0));
         LF_CUDA(cudaEventCreate(&e1));
+        // under the paper's gain only the team size shapes the launches (the
+        // degree thresholds belong to the mean-field kernels)
+        const bool lit = g->gain_rule == LF_GAIN_LITERAL;
+        const int nh = lit ? 1 : 2, nl = lit ? 1 : 3;
         try {
-            for (int32_t H : hubs)
+            for (int ih = 0; ih < nh; ++ih)
             for (int32_t T : teams)
-                for (int32_t L : limits) {
+                for (int il = 0; il < nl; ++il) {
+                    const int32_t H = lit ? keep_h : hubs[ih], L = lit ? keep_l : limits[il];
                     g->warps_per_node = T;
                     g->warp_max_degree = L;
                     g->hub_degree = H;
@@ -467,7 +472,7 @@ lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_t
                     LF_CUDA(cudaEventSynchronize(e1));
                     float ms = 0.f;
                     LF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                    if (T == 0 && L == 0 && H == 384) dflt = ms;
+                    if (T == 0 && (lit || (L == 0 && H == 384))) dflt = ms;
                     if (trials == 0 || ms < best) {
                         best = ms;
                         bt = T;

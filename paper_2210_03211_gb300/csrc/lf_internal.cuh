@@ -237,7 +237,7 @@ struct lf_graph {
     int64_t cm_cap = 0;
     int32_t *jl_head = nullptr, *jl_next = nullptr, *jl_node = nullptr;   // n each
     uint32_t *lit_misc = nullptr;         // [0]: joiners listed in this iteration
-    double *litF = nullptr;               // 3n
+    double *litF = nullptr;               // 6n: F(n-1), F(n), F(n+1), WCC-hat(C), 1/((n+1)n cc), 1/((n-1)(n-2) cc)
     uint32_t *tstamp = nullptr;           // n
     uint32_t *lit_ctr = nullptr;          // 3 per queue
     int64_t lit_ctr_cap = 0;

@@ -1793,15 +1793,20 @@ __global__ void __launch_bounds__(AP_THREADS) k_apply(RunArgs a, int64_t bstart,
 // g_y(nu), so in real arithmetic
 //   join:  gain = p'/cc [F(n+1) + sum_{y in N(x)&C} h+_y + g_x(n+1)] - p/cc F(n)
 //   leave: gain = p'/cc [F(n-1) - g_x(n-1) + sum_{y in N(x)&C} h-_y] - p/cc F(n)
-// with F(nu) = sum_{y in C} g_y(nu) (litF: three sums per community, kept
-// current after every queue for the communities it touched), p, p' the
+// with F(nu) = sum_{y in C} g_y(nu) (litF: the three sums per community and
+// the factors p/cc F(n), 1/((n+1) n cc), 1/((n-1)(n-2) cc), kept current
+// after every queue for the communities it touched), p, p' the
 // densities before and after, and h+_y = g_y(n+1; k_y+1) - g_y(n+1; k_y),
 // h-_y = g_y(n-1; k_y-1) - g_y(n-1; k_y) in closed forms free of
-// cancellation.  Every term is non-negative except the h-, so the FP64 value
-// of this expression and the exact value of the rounded terms both lie within
-// (n + k + 64) 2.07u M of the real one (M: the same expression with every
-// term's magnitude; at most 2n + k + 40 roundings of non-negative sums and a
-// handful of products).  Per kind, candidates whose upper end cannot reach
+// cancellation.  Every term is non-negative except the h-.  The F sums and
+// the factors are FP64; the corrections and g_x are FP32 (GB300's FP64 pipe
+// is the scarce one) and summed in FP32.  The exact value of the rounded
+// terms and the computed value both lie within
+//   E = (n + k + 64) 2.3e-16 M + (k + 16) 1.2e-7 p'/cc (|sum h| + g_x)
+// of the real one (M: the same expression with every term's magnitude; the
+// FP64 part is at most 2n + k + 40 roundings of non-negative sums and a
+// handful of products, the FP32 part about ten roundings per correction plus
+// one per addition, each term counted twice over).  Per kind, candidates whose upper end cannot reach
 // the best lower end (or 0) are dropped; one surviving candidate with a
 // positive lower end is the answer; otherwise the survivors' gains are
 // computed exactly (a signed integer superaccumulator over C's members) and
@@ -1958,39 +1963,64 @@ __device__ __forceinline__ double lit_h_leave(int64_t k, int64_t d, int64_t n) {
     return -((double)d * (bk1 + (double)(k - 1) * (D + 1.0))) / (bd * (D * (D + 1.0)));
 }
 
+// The same corrections and x's own g in FP32 (about ten roundings each,
+// relative error < 16 x 2^-24; a sum of k of them adds k roundings): used
+// only in the bracket, whose bound E carries a term for them.
+__device__ __forceinline__ float lit_h_join32(int64_t k, int64_t d, int64_t n) {
+    if (d < 2 || k < 1) return 0.f;
+    const float D = (float)(n + d - k), kf = (float)k, df = (float)d;
+    const float bk = 0.5f * (kf * (kf - 1.f));
+    const float bd = 0.5f * (df * (df - 1.f));
+    return (df * (kf * D + bk)) / (bd * (D * (D - 1.f)));
+}
+
+__device__ __forceinline__ float lit_h_leave32(int64_t k, int64_t d, int64_t n) {
+    if (d < 2 || k < 2 || n < 3) return 0.f;
+    const float D = (float)(n - 2 + d - k), kf = (float)k, df = (float)d;
+    const float bk1 = 0.5f * ((kf - 1.f) * (kf - 2.f));
+    const float bd = 0.5f * (df * (df - 1.f));
+    return -(df * (bk1 + (kf - 1.f) * (D + 1.f))) / (bd * (D * (D + 1.f)));
+}
+
+__device__ __forceinline__ float lit_g32(int64_t k, int64_t d, int64_t nu) {
+    if (k < 2 || d < 2) return 0.f;
+    const int64_t den = nu - 1 + d - k;
+    if (den <= 0) return 0.f;
+    const float kf = (float)k, df = (float)d;
+    return (0.5f * (kf * (kf - 1.f)) * df) / (0.5f * (df * (df - 1.f)) * (float)den);
+}
+
 // Bracket of one candidate: FP64 value X of the expression above and a bound
 // E on its distance from the exactly summed, once rounded gain.
-__device__ __forceinline__ void lit_screen(const RunArgs &a, int32_t C, uint32_t v, int32_t d, double Hs, double &X,
+__device__ __forceinline__ void lit_screen(const RunArgs &a, int32_t C, uint32_t v, int32_t d, float Hs, double &X,
                                            double &E) {
+    // per community (k_lit_fsum): F(n-1), F(n), F(n+1), WCC-hat(C) = p/cc F(n),
+    // 1/((n+1) n cc) and 1/((n-1)(n-2) cc) (0 where no term can be non-zero)
     const bool own = (v & OWN_FLAG) != 0;
     const int64_t k = (int64_t)(v & CNT_MASK);
     const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
     const int64_t n = r.x;
     const double m2 = (double)(uint32_t)r.y;
-    const double cc = a.gcc ? a.gcc[r.w] : a.cc;
-    if (!(cc > 0.0) || n < 1) {   // every estimator term is 0
-        X = 0.0;
-        E = 0.0;
-        return;
-    }
-    const double Fm = __ldcg(&a.litF[3 * (int64_t)C]);
-    const double F0 = __ldcg(&a.litF[3 * (int64_t)C + 1]);
-    const double Fp = __ldcg(&a.litF[3 * (int64_t)C + 2]);
-    const double Bc = n >= 2 ? (m2 / ((double)n * (double)(n - 1))) / cc : 0.0;
-    double A = 0.0, S1 = 0.0, Sm = 0.0;
+    const double *f = a.litF + 6 * (int64_t)C;
+    const double B0 = __ldcg(&f[3]);
+    double A, S1, Sm, Eh;
     if (!own) {
-        A = ((m2 + 2.0 * (double)k) / ((double)(n + 1) * (double)n)) / cc;
-        S1 = (Fp + Hs) + lit_g(k, d, n + 1);
+        A = (m2 + 2.0 * (double)k) * __ldcg(&f[4]);
+        const double gx = (double)lit_g32(k, d, n + 1);
+        S1 = (__ldcg(&f[2]) + (double)Hs) + gx;
         Sm = S1;
-    } else if (n - 1 >= 2) {
-        A = ((m2 - 2.0 * (double)k) / ((double)(n - 1) * (double)(n - 2))) / cc;
-        const double gx = lit_g(k, d, n - 1);
-        S1 = (Fm - gx) + Hs;
-        Sm = (Fm + gx) - Hs;
+        Eh = (double)Hs + gx;
+    } else {
+        A = (m2 - 2.0 * (double)k) * __ldcg(&f[5]);
+        const double gx = A != 0.0 ? (double)lit_g32(k, d, n - 1) : 0.0;
+        const double Fm = __ldcg(&f[0]);
+        S1 = (Fm - gx) + (double)Hs;
+        Sm = (Fm + gx) - (double)Hs;
+        Eh = gx - (double)Hs;
     }
-    X = A * S1 - Bc * F0;
-    const double M = A * Sm + Bc * F0;
-    E = ((double)(n + k) + 64.0) * 2.3e-16 * M + 1e-300;
+    X = A * S1 - B0;
+    const double M = A * Sm + B0;
+    E = ((double)(n + k) + 64.0) * 2.3e-16 * M + ((double)k + 16.0) * 1.2e-7 * (A * Eh) + 1e-300;
 }
 
 // Every entry of C's member index -- the members at the iteration's start
@@ -2077,11 +2107,27 @@ __device__ __forceinline__ int lit_find(const int32_t *keys, uint32_t hm, int32_
     return -1;
 }
 
-// One pass over the node's candidates of part p (of P): fill the table
-// (keys, counts with the own flag), the candidates' sizes (aux), the
-// neighbour corrections (dv), then each candidate's bracket: dv <- X,
-// aux <- E (as a float rounded up).  Per lane: the largest lower ends of the
-// two kinds.  Returns false (team-wide) if the table overflowed.
+// Open-addressing insert of one neighbour entry: the slot of key (claimed if
+// new) with its count raised by one, or -1 if the table is full.
+__device__ __forceinline__ int lit_insert(int32_t *keys, uint32_t *vals, uint32_t hm, int32_t key) {
+    uint32_t h = hash32((uint32_t)key) & hm;
+    for (uint32_t probe = 0; probe <= hm; ++probe) {
+        const int32_t prev = atomicCAS(&keys[h], EMPTY_KEY, key);
+        if (prev == EMPTY_KEY || prev == key) {
+            atomicAdd(&vals[h], 1u);
+            return (int)h;
+        }
+        h = (h + 1) & hm;
+    }
+    return -1;
+}
+
+// One pass over the node's candidates of part p (of P): the table gets x's
+// own communities (own flag), then every neighbour membership (y, C) adds
+// one to C's count and its correction h(y) (by C's size before the queue and
+// whether C is x's own) to C's sum (dv); then each candidate's bracket:
+// dv <- X, aux <- E (as a float rounded up).  Per lane: the largest lower
+// ends of the two kinds.  Returns false (team-wide) if the table overflowed.
 template <int T>
 __device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int32_t *keys, uint32_t *vals,
                          int32_t *aux, double *dv, uint32_t H, LitScratch &ls, int tm, int w_in, double &lbj,
@@ -2090,10 +2136,11 @@ __device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int3
     const int tl = w_in * 32 + lane;
     constexpr int NT = T * 32;
     const uint32_t hm = H - 1;
+    float *hs = reinterpret_cast<float *>(aux);   // corrections, then (as bits) the bound E
     for (uint32_t s = tl; s < H; s += NT) {
         keys[s] = EMPTY_KEY;
         vals[s] = 0u;
-        dv[s] = 0.0;
+        hs[s] = 0.f;
     }
     team_sync<T>(tm);
     bool ok = true;
@@ -2107,10 +2154,21 @@ __device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int3
         const int32_t y = a.adj[q];
         const int32_t cy = __ldcg(&a.nmem[y]);
         const int32_t *rowy = a.mem + (int64_t)y * a.K;
+        const int32_t *krow = a.kmem + (int64_t)y * a.K;
+        const int64_t dy = a.deg[y];
         if (count_bytes) pb += 12ull + 8ull * (unsigned long long)cy;
         for (int s = 0; s < cy; ++s) {
             const int32_t C = __ldcg(&rowy[s]);
-            if (P == 1 || (int)part_of(C, P) == p) ok &= ht_insert(keys, vals, hm, C, 1u, false);
+            if (P > 1 && (int)part_of(C, P) != p) continue;
+            const int64_t ky = __ldcg(&krow[s]);
+            const int64_t n = __ldcg(&a.comm[C].n);
+            const int slot = lit_insert(keys, vals, hm, C);
+            if (slot < 0) {
+                ok = false;
+                continue;
+            }
+            const float h = (vals[slot] & OWN_FLAG) ? lit_h_leave32(ky, dy, n) : lit_h_join32(ky, dy, n);
+            if (h != 0.f) atomicAdd(&hs[slot], h);
         }
     }
     // a full table: the whole team starts over with more parts
@@ -2126,33 +2184,10 @@ __device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int3
     if (!ok) return false;
     for (uint32_t s = tl; s < H; s += NT) {
         const int32_t C = keys[s];
-        if (C != EMPTY_KEY) aux[s] = __ldcg(&a.comm[C].n);
-    }
-    team_sync<T>(tm);
-    for (int64_t q = ln.beg + tl; q < ln.end; q += NT) {
-        const int32_t y = a.adj[q];
-        const int32_t cy = __ldcg(&a.nmem[y]);
-        const int32_t *rowy = a.mem + (int64_t)y * a.K;
-        const int32_t *krow = a.kmem + (int64_t)y * a.K;
-        const int64_t dy = a.deg[y];
-        for (int s = 0; s < cy; ++s) {
-            const int32_t C = __ldcg(&rowy[s]);
-            if (P > 1 && (int)part_of(C, P) != p) continue;
-            const int slot = lit_find(keys, hm, C);
-            if (slot < 0) continue;
-            const int64_t ky = __ldcg(&krow[s]);
-            const int64_t n = aux[slot];
-            const double h = (vals[slot] & OWN_FLAG) ? lit_h_leave(ky, dy, n) : lit_h_join(ky, dy, n);
-            if (h != 0.0) atomicAdd(&dv[slot], h);
-        }
-    }
-    team_sync<T>(tm);
-    for (uint32_t s = tl; s < H; s += NT) {
-        const int32_t C = keys[s];
         if (C == EMPTY_KEY) continue;
         const uint32_t v = vals[s];
         double X, E;
-        lit_screen(a, C, v, ln.d, dv[s], X, E);
+        lit_screen(a, C, v, ln.d, hs[s], X, E);
         const float Ef = __double2float_ru(E * (1.0 + 1e-6));
         dv[s] = X;
         aux[s] = __float_as_int(Ef);
@@ -2655,6 +2690,22 @@ __device__ __forceinline__ void lit_fsum_member(const RunArgs &a, int32_t C, int
     f2 += lit_g(ky, dy, n + 1);
 }
 
+// The six per-community values of the bracket from the member sums.
+__device__ __forceinline__ void lit_fsum_store(const RunArgs &a, int32_t C, double f0, double f1, double f2) {
+    const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
+    const int64_t n = r.x;
+    const double m2 = (double)(uint32_t)r.y;
+    const double cc = a.gcc ? a.gcc[r.w] : a.cc;
+    const bool on = cc > 0.0 && n >= 1;
+    double *f = a.litF + 6 * (int64_t)C;
+    f[0] = f0;
+    f[1] = f1;
+    f[2] = f2;
+    f[3] = on && n >= 2 ? ((m2 / ((double)n * (double)(n - 1))) / cc) * f1 : 0.0;
+    f[4] = on ? (1.0 / ((double)(n + 1) * (double)n)) / cc : 0.0;
+    f[5] = on && n - 1 >= 2 ? (1.0 / ((double)(n - 1) * (double)(n - 2))) / cc : 0.0;
+}
+
 __global__ void __launch_bounds__(256) k_lit_fsum(RunArgs a, const int32_t *list, const uint32_t *count,
                                                   int64_t ncount) {
     __shared__ double red[3][8];
@@ -2681,11 +2732,7 @@ __global__ void __launch_bounds__(256) k_lit_fsum(RunArgs a, const int32_t *list
                     f1 += __shfl_xor_sync(FULL, f1, o);
                     f2 += __shfl_xor_sync(FULL, f2, o);
                 }
-                if (lane == 0) {
-                    a.litF[3 * (int64_t)C] = f0;
-                    a.litF[3 * (int64_t)C + 1] = f1;
-                    a.litF[3 * (int64_t)C + 2] = f2;
-                }
+                if (lane == 0) lit_fsum_store(a, C, f0, f1, f2);
             }
         }
         __syncthreads();
@@ -2706,10 +2753,11 @@ __global__ void __launch_bounds__(256) k_lit_fsum(RunArgs a, const int32_t *list
                 red[2][w] = f2;
             }
             __syncthreads();
-            if (threadIdx.x < 3) {
-                double sum = 0.0;
-                for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) sum += red[threadIdx.x][k2];
-                a.litF[3 * (int64_t)C + threadIdx.x] = sum;
+            if (threadIdx.x == 0) {
+                double sum[3] = {0.0, 0.0, 0.0};
+                for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2)
+                    for (int t2 = 0; t2 < 3; ++t2) sum[t2] += red[t2][k2];
+                lit_fsum_store(a, C, sum[0], sum[1], sum[2]);
             }
             __syncthreads();
         }
@@ -3765,7 +3813,7 @@ void launch_batches_lit(lf_graph *g, const RunArgs &a, int64_t q, int64_t first,
 void ensure_lit(lf_graph *g, int64_t q, int64_t nb) {
     const int64_t n = std::max<int64_t>(g->n, 1);
     if (!g->litF) {
-        g->litF = dalloc_n<double>(g, 3 * n);
+        g->litF = dalloc_n<double>(g, 6 * n);
         g->cm_off = dalloc_n<unsigned long long>(g, n + 1);
         g->cm_cur = dalloc_n<unsigned long long>(g, n + 1);
         g->jl_head = dalloc_n<int32_t>(g, n);
