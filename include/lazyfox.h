@@ -129,6 +129,10 @@ typedef struct lf_run_stats {
                                 the neighbour scan runs */
     double prof_queue_us[4]; /* profile mode, persistent kernel: p50, p90, p99 and max of the
                                 time per queue (evaluate + apply + barriers), last iteration */
+    int64_t prof_candidates; /* profile mode, LF_GAIN_LITERAL: candidate (node, community) pairs
+                                bracketed */
+    int64_t prof_exact;      /* profile mode, LF_GAIN_LITERAL: of these, the ones whose gain was
+                                summed exactly (the bracket could not decide) */
 } lf_run_stats;
 
 /* Device times of the phases of lf_graph_create. */

@@ -62,6 +62,8 @@ struct DevScalars {
     unsigned long long live_comms;          // communities with n >= 2 after pruning
     unsigned long long memberships;         // sum of row counts after pruning
     unsigned long long prof_bytes;          // profile mode: move-evaluation algorithmic bytes
+    unsigned long long prof_cands;          // profile mode, paper's gain: candidates bracketed
+    unsigned long long prof_exact;          // profile mode, paper's gain: candidates summed exactly
     int32_t maxcnt;                         // max memberships of a node (after pruning)
     int32_t kb;                             // bound on memberships during an iteration
     int32_t err;                            // DERR_* bits
@@ -249,6 +251,23 @@ struct lf_graph {
     unsigned long long lg_cap = 0;
     int64_t lg_plan_q = -1, lg_plan_sched = -1;
     int32_t lg_plan_K = 0;
+    // hubs under the paper's gain: per hub its queue position, table offset
+    // and size, survivor-list offset, slot items, best lower ends, counters;
+    // fill items and slot items of all queues (offsets per queue on the host);
+    // the tables and survivor lists shared by the queues
+    int64_t lh_plan_q = -1, lh_plan_sched = -1;
+    int32_t lh_plan_K = 0;
+    int64_t lh_n = 0;
+    std::vector<int64_t> lh_fq, lh_sq, lh_hq;
+    uint32_t *lh_heff = nullptr;
+    int32_t *lh_pos = nullptr, *lh_nsr = nullptr, *lh_fh = nullptr, *lh_fc = nullptr, *lh_sh = nullptr,
+            *lh_sr = nullptr, *lh_svc = nullptr;
+    int64_t *lh_toff = nullptr, *lh_soff = nullptr;
+    uint32_t *lh_tcap = nullptr, *lh_done = nullptr, *lh_ns = nullptr, *lh_svv = nullptr;
+    unsigned long long *lh_lb = nullptr;
+    double *lh_svl = nullptr;
+    void *lh_tab = nullptr;               // tables: 20 bytes per slot
+    int64_t lh_tab_cap = 0;
     // second stream: hub chunks run beside the other evaluation kernels of a queue
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

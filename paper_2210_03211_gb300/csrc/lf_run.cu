@@ -105,6 +105,7 @@ struct RunArgs {
     int32_t *lg_aux;
     double *lg_dv;
     unsigned long long lg_cap;
+    int32_t lit_hub_deg;   // nodes of higher degree take the hub kernels (INT_MAX: none)
 };
 
 // ---------------------------------------------------------------------------
@@ -2194,7 +2195,10 @@ __device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int3
         const double L = X - (double)Ef;
         if (v & OWN_FLAG) lbl = fmax(lbl, L);
         else lbj = fmax(lbj, L);
-        if (count_bytes) pb += 40ull;
+        if (count_bytes) {
+            pb += 40ull;
+            atomicAdd(&a.ds->prof_cands, 1ull);
+        }
     }
     team_sync<T>(tm);
     return true;
@@ -2331,6 +2335,7 @@ __device__ void lit_exact_survivors(const RunArgs &a, const LitNode &ln, const i
             const bool own = (v1 & OWN_FLAG) != 0;
             const int64_t k = (int64_t)(v1 & CNT_MASK);
             const double g = lit_exact_gain(a, ln.x, ln.d, c1, own, k, acc);
+            if (a.profile && lane == 0) atomicAdd(&a.ds->prof_exact, 1ull);
             if (g > 0.0) {
                 Best &b = own ? bl : bj;
                 if (better(g, c1, b.g, b.c)) b = Best{g, c1, (int32_t)k};
@@ -2444,6 +2449,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_lit_eval(RunArgs a, int64_t b
     ln.beg = a.off[ln.x];
     ln.end = a.off[ln.x + 1];
     ln.d = (int32_t)(ln.end - ln.beg);
+    if (ln.d > a.lit_hub_deg) return;   // the hub kernels decide it
     ln.cx = __ldcg(&a.nmem[ln.x]);
     long long bound = w_in == 0 && lane == 0 ? ln.cx : 0;
     for (int64_t q = ln.beg + w_in * 32 + lane; q < ln.end; q += T * 32) bound += __ldcg(&a.nmem[a.adj[q]]);
@@ -2531,15 +2537,279 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_lit_big(RunArgs a, int64_t bs
             }
         }
         int P = (int)((bound + LIT_PART_ENTRIES - 1) / LIT_PART_ENTRIES);
-        if (P < 1 || 2 * bound <= LB_SLOTS) P = 1;
-        while (!lit_eval_node<EV_WARPS>(a, i, ln, P, keys, vals, aux, dv, (uint32_t)LB_SLOTS, ls,
-                                        acc + w * SACC_CHUNKS, 0, w)) {
+        uint32_t Hs = (uint32_t)LB_SLOTS;
+        if (P < 1 || 2 * bound <= LB_SLOTS) {   // one pass over a table of pow2 >= 2 x entries
+            P = 1;
+            Hs = 32;
+            while ((long long)Hs < 2 * bound) Hs <<= 1;
+        }
+        while (!lit_eval_node<EV_WARPS>(a, i, ln, P, keys, vals, aux, dv, Hs, ls, acc + w * SACC_CHUNKS, 0, w)) {
+            Hs = (uint32_t)LB_SLOTS;
             P *= 2;
             if (P > (1 << 22)) {   // cannot happen for < 2^31 entries; leave an error, not a loop
                 if (threadIdx.x == 0) atomicOr(&a.ds->err, DERR_CHECK);
                 break;
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Hubs under the paper's gain: a queued node of degree > LIT_HUB_DEG is
+// evaluated by many blocks over one table in global memory (planned per
+// queue for the worst case, pow2 >= 2 (d+1) K slots): k_lh_fill (one block per
+// 1024 neighbours: counts, own flags, FP32 corrections), k_lh_bound (one
+// block per 4096 slots: brackets, the hub's best lower ends by an
+// order-preserving integer max), k_lh_mark (one block per 4096 slots:
+// survivors listed, slots cleared; the hub's last block decides, summing the
+// undecided survivors exactly).  Team and block kernels skip these nodes.
+// ---------------------------------------------------------------------------
+constexpr int LIT_HUB_DEG = 1024;
+constexpr int LH_CHUNK = 1024;       // neighbours per fill block
+constexpr int LH_SLOTS = 4096;       // table slots per bracket / mark block
+
+__device__ __forceinline__ unsigned long long d2ord(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord2d(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+struct LitHubPlan {
+    const int32_t *pos;       // per hub: its position in the queue
+    const int64_t *toff;      // per hub: first slot of its table
+    const uint32_t *tcap;     // per hub: table slots
+    const int64_t *soff;      // per hub: first entry of its survivor list (tcap/2 entries)
+    const int32_t *fh, *fc;   // fill items of every queue: hub, chunk
+    const int32_t *sh, *sr;   // slot items of every queue: hub, range
+    const int32_t *nsr;       // per hub: its slot items (worst case)
+    uint32_t *heff;           // per hub: table slots used in this queue
+    unsigned long long *lb;   // per hub: best lower ends (join, leave), order-preserving
+    uint32_t *done;           // per hub: slot items marked
+    uint32_t *ns;             // per hub: survivors listed
+    int32_t *sv_c;            // survivor lists: community, count word, lower end
+    uint32_t *sv_v;
+    double *sv_l;
+    int32_t *keys;            // tables: keys, counts, FP32 corrections (then E), X
+    uint32_t *vals;
+    float *hs;
+    double *dv;
+};
+
+// Each hub's table size for this queue: pow2 >= 2 (own row + neighbours'
+// rows), at least LH_SLOTS, at most the planned worst case (one block per hub).
+__global__ void __launch_bounds__(256) k_lh_size(RunArgs a, LitHubPlan hp, int64_t bstart, int64_t h0, int64_t nh) {
+    __shared__ long long part[8];
+    const int64_t h = h0 + blockIdx.x;
+    if (blockIdx.x >= nh) return;
+    const int32_t x = a.order[bstart + hp.pos[h]];
+    long long b = threadIdx.x == 0 ? __ldcg(&a.nmem[x]) : 0;
+    for (int64_t q = a.off[x] + threadIdx.x; q < a.off[x + 1]; q += blockDim.x) b += __ldcg(&a.nmem[a.adj[q]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(FULL, b, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) t += part[k2];
+        unsigned long long H = LH_SLOTS;
+        while ((long long)H < 2 * t && H < hp.tcap[h]) H <<= 1;
+        hp.heff[h] = (uint32_t)H;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_lh_fill(RunArgs a, LitHubPlan hp, int64_t bstart, int64_t first) {
+    const int64_t it = first + blockIdx.x;
+    const int h = hp.fh[it], c = hp.fc[it];
+    const int32_t x = a.order[bstart + hp.pos[h]];
+    const int64_t beg = a.off[x], end = a.off[x + 1];
+    const int64_t t0 = hp.toff[h];
+    const uint32_t hm = __ldcg(&hp.heff[h]) - 1;
+    int32_t *keys = hp.keys + t0;
+    uint32_t *vals = hp.vals + t0;
+    float *hs = hp.hs + t0;
+    const int32_t cx = __ldcg(&a.nmem[x]);
+    const int32_t *rowx = a.mem + (int64_t)x * a.K;
+    if (c == 0)
+        for (int j = threadIdx.x; j < cx; j += blockDim.x)
+            if (!ht_insert(keys, vals, hm, __ldcg(&rowx[j]), 0u, true)) atomicOr(&a.ds->err, DERR_CHECK);
+    unsigned long long pb = 0;
+    const int64_t cb = beg + (int64_t)c * LH_CHUNK, ce = min(end, cb + LH_CHUNK);
+    for (int64_t q = cb + threadIdx.x; q < ce; q += blockDim.x) {
+        const int32_t y = a.adj[q];
+        const int32_t cy = __ldcg(&a.nmem[y]);
+        const int32_t *rowy = a.mem + (int64_t)y * a.K;
+        const int32_t *krow = a.kmem + (int64_t)y * a.K;
+        const int64_t dy = a.deg[y];
+        if (a.profile) pb += 12ull + 8ull * (unsigned long long)cy;
+        for (int s = 0; s < cy; ++s) {
+            const int32_t C = __ldcg(&rowy[s]);
+            const int64_t ky = __ldcg(&krow[s]);
+            const int64_t n = __ldcg(&a.comm[C].n);
+            const int slot = lit_insert(keys, vals, hm, C);
+            if (slot < 0) {   // cannot happen: the table holds 2 (d+1) K slots
+                atomicOr(&a.ds->err, DERR_CHECK);
+                continue;
+            }
+            const float hv = row_find(rowx, cx, C) >= 0 ? lit_h_leave32(ky, dy, n) : lit_h_join32(ky, dy, n);
+            if (hv != 0.f) atomicAdd(&hs[slot], hv);
+        }
+    }
+    if (a.profile) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pb += __shfl_down_sync(FULL, pb, o);
+        if ((threadIdx.x & 31) == 0 && pb) atomicAdd(&a.ds->prof_bytes, pb);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_lh_bound(RunArgs a, LitHubPlan hp, int64_t bstart, int64_t first) {
+    __shared__ double red[2][8];
+    const int64_t it = first + blockIdx.x;
+    const int h = hp.sh[it], r = hp.sr[it];
+    const int32_t x = a.order[bstart + hp.pos[h]];
+    const int32_t d = (int32_t)(a.off[x + 1] - a.off[x]);
+    const int64_t t0 = hp.toff[h];
+    const uint32_t lo = (uint32_t)r * LH_SLOTS, hi = min(__ldcg(&hp.heff[h]), lo + LH_SLOTS);
+    if (lo >= hi) return;   // beyond this queue's table
+    double lbj = -INFINITY, lbl = -INFINITY;
+    unsigned long long nc = 0;
+    for (uint32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
+        const int32_t C = hp.keys[t0 + s];
+        if (C == EMPTY_KEY) continue;
+        const uint32_t v = hp.vals[t0 + s];
+        double X, E;
+        lit_screen(a, C, v, d, hp.hs[t0 + s], X, E);
+        const float Ef = __double2float_ru(E * (1.0 + 1e-6));
+        hp.dv[t0 + s] = X;
+        hp.hs[t0 + s] = Ef;
+        const double L = X - (double)Ef;
+        if (v & OWN_FLAG) lbl = fmax(lbl, L);
+        else lbj = fmax(lbj, L);
+        ++nc;
+    }
+    lbj = warp_max_d(lbj);
+    lbl = warp_max_d(lbl);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][w] = lbj;
+        red[1][w] = lbl;
+    }
+    if (a.profile) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nc += __shfl_down_sync(FULL, nc, o);
+        if (lane == 0 && nc) {
+            atomicAdd(&a.ds->prof_cands, nc);
+            atomicAdd(&a.ds->prof_bytes, 40ull * nc);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double m = -INFINITY;
+        for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) m = fmax(m, red[threadIdx.x][k2]);
+        if (m > -INFINITY) atomicMax(&hp.lb[2 * h + threadIdx.x], d2ord(m));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_lh_mark(RunArgs a, LitHubPlan hp, int64_t bstart, int64_t first) {
+    __shared__ int s_last;
+    __shared__ unsigned long long acc_s[8 * SACC_CHUNKS];
+    __shared__ double bg[2][8];
+    __shared__ int32_t bc[2][8], bk[2][8];
+    const int64_t it = first + blockIdx.x;
+    const int h = hp.sh[it], r = hp.sr[it];
+    const int32_t i = hp.pos[h];
+    const int32_t x = a.order[bstart + i];
+    const int32_t d = (int32_t)(a.off[x + 1] - a.off[x]);
+    const int64_t t0 = hp.toff[h], so = hp.soff[h];
+    const double lbj = ord2d(__ldcg(&hp.lb[2 * h])), lbl = ord2d(__ldcg(&hp.lb[2 * h + 1]));
+    const uint32_t heff = __ldcg(&hp.heff[h]);
+    const uint32_t lo = (uint32_t)r * LH_SLOTS, hi = min(heff, lo + LH_SLOTS);
+    if (lo >= hi) return;   // beyond this queue's table
+    for (uint32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
+        const int32_t C = hp.keys[t0 + s];
+        if (C == EMPTY_KEY) continue;
+        const uint32_t v = hp.vals[t0 + s];
+        const double X = hp.dv[t0 + s], E = (double)hp.hs[t0 + s];
+        const double U = X + E;
+        const bool own = (v & OWN_FLAG) != 0;
+        if (!a.screen || (U > 0.0 && U >= (own ? lbl : lbj))) {
+            const uint32_t e = atomicAdd(&hp.ns[h], 1u);
+            hp.sv_c[so + e] = C;
+            hp.sv_v[so + e] = v;
+            hp.sv_l[so + e] = X - E;
+        }
+        hp.keys[t0 + s] = EMPTY_KEY;   // the table is left clean for the hub's next queue
+        hp.vals[t0 + s] = 0u;
+        hp.hs[t0 + s] = 0.f;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&hp.done[h], 1u) + 1u == heff / LH_SLOTS;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the hub's last block: the survivors decide
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t ns = __ldcg(&hp.ns[h]);
+    int cj = 0, cl = 0;
+    int32_t Cj = -1, Cl = -1, kj = 0, kl = 0;
+    double Lj = 0.0, Ll = 0.0;
+    for (uint32_t e = 0; e < ns; ++e) {   // every thread reads the (short) list
+        const uint32_t v = __ldcg(&hp.sv_v[so + e]);
+        const int32_t C = __ldcg(&hp.sv_c[so + e]);
+        const double L = __ldcg(&hp.sv_l[so + e]);
+        if (v & OWN_FLAG) {
+            if (cl++ == 0) { Cl = C; kl = (int32_t)(v & CNT_MASK); Ll = L; }
+        } else {
+            if (cj++ == 0) { Cj = C; kj = (int32_t)(v & CNT_MASK); Lj = L; }
+        }
+    }
+    Best bj{0.0, -1, 0}, bl{0.0, -1, 0};
+    bool do_j = cj > 0, do_l = cl > 0;
+    if (a.screen && cj == 1 && Lj > 0.0) {
+        bj = Best{INFINITY, Cj, kj};
+        do_j = false;
+    }
+    if (a.screen && cl == 1 && Ll > 0.0) {
+        bl = Best{INFINITY, Cl, kl};
+        do_l = false;
+    }
+    if (do_j || do_l) {
+        unsigned long long *acc = acc_s + w * SACC_CHUNKS;
+        for (int c2 = lane; c2 < SACC_CHUNKS; c2 += 32) acc[c2] = 0ull;
+        __syncwarp();
+        for (uint32_t e = w; e < ns; e += blockDim.x >> 5) {
+            const uint32_t v = __ldcg(&hp.sv_v[so + e]);
+            const bool own = (v & OWN_FLAG) != 0;
+            if (own ? !do_l : !do_j) continue;
+            const int32_t C = __ldcg(&hp.sv_c[so + e]);
+            const int64_t k = (int64_t)(v & CNT_MASK);
+            const double g = lit_exact_gain(a, x, d, C, own, k, acc);
+            if (a.profile && lane == 0) atomicAdd(&a.ds->prof_exact, 1ull);
+            if (g > 0.0) {
+                Best &b = own ? bl : bj;
+                if (better(g, C, b.g, b.c)) b = Best{g, C, (int32_t)k};
+            }
+        }
+        if (lane == 0) {
+            bg[0][w] = bj.g; bc[0][w] = bj.c; bk[0][w] = bj.k;
+            bg[1][w] = bl.g; bc[1][w] = bl.c; bk[1][w] = bl.k;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k2 = 1; k2 < (int)(blockDim.x >> 5); ++k2) {
+                if (better(bg[0][k2], bc[0][k2], bj.g, bj.c)) bj = Best{bg[0][k2], bc[0][k2], bk[0][k2]};
+                if (better(bg[1][k2], bc[1][k2], bl.g, bl.c)) bl = Best{bg[1][k2], bc[1][k2], bk[1][k2]};
+            }
+    }
+    if (threadIdx.x == 0) {
+        write_action(a, i, bj, bl, 0ull);
+        if (a.profile) atomicAdd(&a.ds->prof_bytes, 44ull + 8ull * (unsigned long long)__ldcg(&a.nmem[x]));
+        hp.done[h] = 0u;   // ready for the hub's next queue
+        hp.ns[h] = 0u;
+        hp.lb[2 * h] = d2ord(-INFINITY);
+        hp.lb[2 * h + 1] = d2ord(-INFINITY);
     }
 }
 
@@ -3541,6 +3811,7 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.lg_keys = reinterpret_cast<int32_t *>(a.lg_dv + g->lg_cap);
     a.lg_vals = reinterpret_cast<uint32_t *>(a.lg_keys + g->lg_cap);
     a.lg_aux = reinterpret_cast<int32_t *>(a.lg_vals + g->lg_cap);
+    a.lit_hub_deg = g->lh_n > 0 ? LIT_HUB_DEG : 0x7fffffff;
     if (lit) a.screen = g->screen ? 1 : 0;   // brackets need no FP32 range condition
     return a;
 }
@@ -3766,6 +4037,161 @@ void launch_batches(lf_graph *g, const RunArgs &a, int64_t q, int64_t first, int
     LF_LAUNCHED();
 }
 
+void free_lit_hub_plan(lf_graph *g) {
+    for (int32_t **pp : {&g->lh_pos, &g->lh_nsr, &g->lh_fh, &g->lh_fc, &g->lh_sh, &g->lh_sr, &g->lh_svc})
+        if (*pp) {
+            dfree(g, *pp);
+            *pp = nullptr;
+        }
+    for (int64_t **pp : {&g->lh_toff, &g->lh_soff})
+        if (*pp) {
+            dfree(g, *pp);
+            *pp = nullptr;
+        }
+    for (uint32_t **pp : {&g->lh_tcap, &g->lh_done, &g->lh_ns, &g->lh_svv, &g->lh_heff})
+        if (*pp) {
+            dfree(g, *pp);
+            *pp = nullptr;
+        }
+    if (g->lh_lb) dfree(g, g->lh_lb);
+    if (g->lh_svl) dfree(g, g->lh_svl);
+    if (g->lh_tab) dfree(g, g->lh_tab);
+    g->lh_lb = nullptr;
+    g->lh_svl = nullptr;
+    g->lh_tab = nullptr;
+    g->lh_tab_cap = 0;
+    g->lh_n = 0;
+    g->lh_fq.clear();
+    g->lh_sq.clear();
+    g->lh_hq.clear();
+    g->lh_plan_q = g->lh_plan_sched = -1;
+    g->lh_plan_K = 0;
+}
+
+// The hubs of every queue (degree > LIT_HUB_DEG): worst-case tables of
+// pow2 >= 2 (d+1) K slots (K bounds every row), fill items of LH_CHUNK
+// neighbours, slot items of LH_SLOTS slots.  Queues run one after the other,
+// so their tables and survivor lists share one area.
+void build_lit_hub_plan(lf_graph *g, int64_t q, int64_t nb) {
+    if (g->lh_plan_q == q && g->lh_plan_K == g->K && g->lh_plan_sched == g->sched_version) return;
+    free_lit_hub_plan(g);
+    drop_graph(g);
+    g->lh_plan_q = q;
+    g->lh_plan_K = g->K;
+    g->lh_plan_sched = g->sched_version;
+    g->lh_fq.assign((size_t)nb + 1, 0);
+    g->lh_sq.assign((size_t)nb + 1, 0);
+    g->lh_hq.assign((size_t)nb + 1, 0);
+    if (g->n == 0 || g->max_deg <= LIT_HUB_DEG) return;
+    const int64_t len = g->sched.empty() ? g->n : g->sched.back();
+    std::vector<int32_t> order((size_t)std::max<int64_t>(len, 1)), deg((size_t)g->n);
+    if (len > 0)
+        LF_CUDA(cudaMemcpyAsync(order.data(), g->sched.empty() ? g->order : g->qorder, (size_t)len * 4,
+                                cudaMemcpyDeviceToHost, g->stream));
+    LF_CUDA(cudaMemcpyAsync(deg.data(), g->deg, (size_t)g->n * 4, cudaMemcpyDeviceToHost, g->stream));
+    LF_CUDA(cudaStreamSynchronize(g->stream));
+    std::vector<int32_t> pos, nsr, fh, fc, sh, sr;
+    std::vector<int64_t> toff, soff;
+    std::vector<uint32_t> tcap;
+    int64_t area = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        int64_t qs;
+        int32_t ql;
+        queue_bounds(g, q, b, qs, ql);
+        int64_t used = 0;
+        for (int64_t p = qs; p < qs + ql; ++p) {
+            const int32_t d = deg[(size_t)order[(size_t)p]];
+            if (d <= LIT_HUB_DEG) continue;
+            uint64_t cap = LH_SLOTS;
+            while (cap < 2ull * (uint64_t)(d + 1) * (uint64_t)g->K) cap <<= 1;
+            const int32_t h = (int32_t)pos.size();
+            pos.push_back((int32_t)(p - qs));
+            toff.push_back(used);
+            soff.push_back(used / 2);
+            tcap.push_back((uint32_t)cap);
+            const int32_t nf = (d + LH_CHUNK - 1) / LH_CHUNK, ns = (int32_t)(cap / LH_SLOTS);
+            nsr.push_back(ns);
+            for (int32_t c = 0; c < nf; ++c) {
+                fh.push_back(h);
+                fc.push_back(c);
+            }
+            for (int32_t r = 0; r < ns; ++r) {
+                sh.push_back(h);
+                sr.push_back(r);
+            }
+            used += (int64_t)cap;
+        }
+        g->lh_fq[(size_t)b + 1] = (int64_t)fh.size();
+        g->lh_sq[(size_t)b + 1] = (int64_t)sh.size();
+        g->lh_hq[(size_t)b + 1] = (int64_t)pos.size();
+        area = std::max(area, used);
+    }
+    const int64_t H = (int64_t)pos.size();
+    g->lh_n = H;
+    if (H == 0) return;
+    auto up = [&](auto *&dst, const auto &v) {
+        using E = typename std::decay<decltype(v[0])>::type;
+        dst = dalloc_n<E>(g, (int64_t)v.size());
+        LF_CUDA(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(E), cudaMemcpyHostToDevice, g->stream));
+    };
+    up(g->lh_pos, pos);
+    up(g->lh_nsr, nsr);
+    up(g->lh_fh, fh);
+    up(g->lh_fc, fc);
+    up(g->lh_sh, sh);
+    up(g->lh_sr, sr);
+    up(g->lh_toff, toff);
+    up(g->lh_soff, soff);
+    up(g->lh_tcap, tcap);
+    g->lh_done = dalloc_n<uint32_t>(g, H);
+    g->lh_heff = dalloc_n<uint32_t>(g, H);
+    g->lh_ns = dalloc_n<uint32_t>(g, H);
+    LF_CUDA(cudaMemsetAsync(g->lh_done, 0, (size_t)H * 4, g->stream));
+    LF_CUDA(cudaMemsetAsync(g->lh_ns, 0, (size_t)H * 4, g->stream));
+    {
+        // best lower ends start at -inf (order-preserving: ~bits of -inf)
+        const unsigned long long ninf = ~0xfff0000000000000ull;
+        std::vector<unsigned long long> lb((size_t)(2 * H), ninf);
+        up(g->lh_lb, lb);
+    }
+    g->lh_tab_cap = area;
+    g->lh_tab = dalloc(g, (size_t)area * 20);
+    // keys empty, counts and corrections zero (the X area needs no start value)
+    char *t = static_cast<char *>(g->lh_tab);
+    LF_CUDA(cudaMemsetAsync(t + (size_t)area * 8, 0xff, (size_t)area * 4, g->stream));
+    LF_CUDA(cudaMemsetAsync(t + (size_t)area * 12, 0, (size_t)area * 8, g->stream));
+    g->lh_svc = dalloc_n<int32_t>(g, area / 2);
+    g->lh_svv = dalloc_n<uint32_t>(g, area / 2);
+    g->lh_svl = dalloc_n<double>(g, area / 2);
+    LF_CUDA(cudaStreamSynchronize(g->stream));
+}
+
+LitHubPlan lit_hub_plan(lf_graph *g) {
+    LitHubPlan hp;
+    hp.pos = g->lh_pos;
+    hp.toff = g->lh_toff;
+    hp.tcap = g->lh_tcap;
+    hp.soff = g->lh_soff;
+    hp.fh = g->lh_fh;
+    hp.fc = g->lh_fc;
+    hp.sh = g->lh_sh;
+    hp.sr = g->lh_sr;
+    hp.nsr = g->lh_nsr;
+    hp.heff = g->lh_heff;
+    hp.lb = g->lh_lb;
+    hp.done = g->lh_done;
+    hp.ns = g->lh_ns;
+    hp.sv_c = g->lh_svc;
+    hp.sv_v = g->lh_svv;
+    hp.sv_l = g->lh_svl;
+    const int64_t cap = g->lh_tab_cap;
+    hp.dv = static_cast<double *>(g->lh_tab);
+    hp.keys = reinterpret_cast<int32_t *>(hp.dv + cap);
+    hp.vals = reinterpret_cast<uint32_t *>(hp.keys + cap);
+    hp.hs = reinterpret_cast<float *>(hp.vals + cap);
+    return hp;
+}
+
 // Per-queue launches under the paper's gain: teams evaluate the queue's nodes
 // (k_lit_eval), blocks take the nodes too large for a team (k_lit_big), then
 // the apply, the neighbours' deg(y,C) updates and the touched communities'
@@ -3798,6 +4224,18 @@ void launch_batches_lit(lf_graph *g, const RunArgs &a, int64_t q, int64_t first,
         }
         launch_pdl(k_lit_big, std::min<unsigned>(big_grid, (unsigned)blen), EV_THREADS, LIT_SMEM, g->stream, ab,
                    bstart, ctr, (const int32_t *)g->lit_over, g->lit_used + b);
+        const int64_t f0 = g->lh_fq.empty() ? 0 : g->lh_fq[(size_t)b];
+        const int64_t nf = g->lh_fq.empty() ? 0 : g->lh_fq[(size_t)b + 1] - f0;
+        if (nf > 0) {
+            const LitHubPlan hp = lit_hub_plan(g);
+            const int64_t s0 = g->lh_sq[(size_t)b], nsl = g->lh_sq[(size_t)b + 1] - s0;
+            const int64_t h0 = g->lh_hq[(size_t)b], nh = g->lh_hq[(size_t)b + 1] - h0;
+            k_lh_size<<<(unsigned)nh, 256, 0, g->stream>>>(ab, hp, bstart, h0, nh);
+            k_lh_fill<<<(unsigned)nf, 256, 0, g->stream>>>(ab, hp, bstart, f0);
+            k_lh_bound<<<(unsigned)nsl, 256, 0, g->stream>>>(ab, hp, bstart, s0);
+            k_lh_mark<<<(unsigned)nsl, 256, 0, g->stream>>>(ab, hp, bstart, s0);
+            g->launches += 4;
+        }
         if (prof) record_event(g, g->prof_ev[2 * b + 1], capturing);
         const unsigned ag = grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30);
         launch_pdl(k_lit_apply, ag, AP_THREADS, 0, g->stream, ab, bstart, blen, b);
@@ -3845,6 +4283,7 @@ void ensure_lit(lf_graph *g, int64_t q, int64_t nb) {
         g->lit_used = dalloc_n<unsigned long long>(g, nb);
         drop_graph(g);
     }
+    build_lit_hub_plan(g, q, nb);
     // global tables: per queue, every node whose entries can exceed half a
     // block's table gets pow2 >= 2 (d+1) K slots (K bounds every row, so
     // (d+1) K bounds its entries); queues run one after the other and share
@@ -4326,6 +4765,7 @@ void free_run_state(lf_graph *g) {
             dfree(g, *pp);
             *pp = nullptr;
         }
+    free_lit_hub_plan(g);
     if (g->lit_used) dfree(g, g->lit_used);
     g->lit_used = nullptr;
     if (g->lg_area) dfree(g, g->lg_area);
@@ -4711,11 +5151,14 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         stats->num_launches = (int64_t)(g->launches - launches0);
         stats->prof_move_launches = prof_launches;
         stats->prof_move_ms = prof_ms;
-        unsigned long long pbytes = 0;
+        unsigned long long pbytes = 0, pc[2] = {0, 0};
         if (g->profile) {
             LF_CUDA(cudaMemcpy(&pbytes, &g->ds->prof_bytes, 8, cudaMemcpyDeviceToHost));
+            LF_CUDA(cudaMemcpy(pc, &g->ds->prof_cands, 16, cudaMemcpyDeviceToHost));
         }
         stats->prof_move_bytes = (int64_t)pbytes;
+        stats->prof_candidates = (int64_t)pc[0];
+        stats->prof_exact = (int64_t)pc[1];
         for (int k = 0; k < 4; ++k) stats->prof_queue_us[k] = qpct[k];
     }
 }

@@ -64,7 +64,8 @@ class RunStatsC(C.Structure):
                 ("wcc_history", C.POINTER(C.c_double)), ("joins_history", C.POINTER(C.c_int64)),
                 ("leaves_history", C.POINTER(C.c_int64)), ("num_launches", C.c_int64),
                 ("prof_move_launches", C.c_int64), ("prof_move_ms", C.c_double),
-                ("prof_move_bytes", C.c_int64), ("prof_queue_us", C.c_double * 4)]
+                ("prof_move_bytes", C.c_int64), ("prof_queue_us", C.c_double * 4),
+                ("prof_candidates", C.c_int64), ("prof_exact", C.c_int64)]
 
 
 class TuneResultC(C.Structure):
@@ -192,6 +193,8 @@ class RunStats:
     prof_move_ms: float = 0.0
     prof_move_bytes: int = 0
     prof_queue_us: tuple = (0.0, 0.0, 0.0, 0.0)
+    prof_candidates: int = 0
+    prof_exact: int = 0
 
 
 class Graph:
@@ -373,7 +376,7 @@ class Graph:
         return RunStats(k, bool(st.converged), st.num_batches, st.wcc_initial, T[:k].copy(), J[:k].copy(),
                         Lv[:k].copy(), st.num_communities, st.num_memberships, st.ms_total, st.ms_init,
                         st.ms_iterations, st.num_launches, st.prof_move_launches, st.prof_move_ms,
-                        st.prof_move_bytes, tuple(st.prof_queue_us))
+                        st.prof_move_bytes, tuple(st.prof_queue_us), st.prof_candidates, st.prof_exact)
 
     def communities(self):
         """(offsets int64[k+1], members int32[...]) in original node ids."""

@@ -57,7 +57,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(lazyfox.TuneResultC) == 4 * 4 + 2 * 8
     assert C.sizeof(lazyfox.ServerOptionsC) == 8 + 4 + 4
     assert C.sizeof(lazyfox.JobResultC) == 4 * 4 + 2 * 8 + 4 * 8 + 3 * 8
-    assert C.sizeof(lazyfox.RunStatsC) == 4 + 4 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 3 * 8 + 4 * 8 + 4 * 8
+    assert C.sizeof(lazyfox.RunStatsC) == 4 + 4 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 3 * 8 + 4 * 8 + 4 * 8 + 2 * 8
 
 
 def test_product_path_has_no_oracle_or_fallback():
