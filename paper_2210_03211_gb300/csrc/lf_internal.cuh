@@ -239,7 +239,7 @@ struct lf_graph {
     int64_t cm_cap = 0;
     int32_t *jl_head = nullptr, *jl_next = nullptr, *jl_node = nullptr;   // n each
     uint32_t *lit_misc = nullptr;         // [0]: joiners listed in this iteration
-    double *litF = nullptr;               // 6n: F(n-1), F(n), F(n+1), WCC-hat(C), 1/((n+1)n cc), 1/((n-1)(n-2) cc)
+    float *litF = nullptr;                // 8n: F(n-1), F(n+1), WCC-hat(C), 1/((n+1)n cc), 1/((n-1)(n-2) cc)
     uint32_t *tstamp = nullptr;           // n
     uint32_t *lit_ctr = nullptr;          // 3 per queue
     int64_t lit_ctr_cap = 0;
@@ -247,7 +247,7 @@ struct lf_graph {
     int32_t *touched = nullptr;           // 2 qcap
     int64_t lit_qcap = 0;
     unsigned long long *lit_used = nullptr;   // per queue: global table slots handed out
-    void *lg_area = nullptr;              // global tables: lg_cap slots of 20 bytes
+    void *lg_area = nullptr;              // global tables: lg_cap slots of 16 bytes
     unsigned long long lg_cap = 0;
     int64_t lg_plan_q = -1, lg_plan_sched = -1;
     int32_t lg_plan_K = 0;
@@ -264,9 +264,9 @@ struct lf_graph {
             *lh_sr = nullptr, *lh_svc = nullptr;
     int64_t *lh_toff = nullptr, *lh_soff = nullptr;
     uint32_t *lh_tcap = nullptr, *lh_done = nullptr, *lh_ns = nullptr, *lh_svv = nullptr;
-    unsigned long long *lh_lb = nullptr;
-    double *lh_svl = nullptr;
-    void *lh_tab = nullptr;               // tables: 20 bytes per slot
+    int32_t *lh_lb = nullptr;
+    float *lh_svl = nullptr;
+    void *lh_tab = nullptr;               // tables: 16 bytes per slot
     int64_t lh_tab_cap = 0;
     // second stream: hub chunks run beside the other evaluation kernels of a queue
     cudaStream_t side = nullptr;

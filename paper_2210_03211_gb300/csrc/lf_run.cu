@@ -94,7 +94,7 @@ struct RunArgs {
     uint32_t *cm_cnt;   // entries used in each community's region (members at the start, then joiners)
     int32_t *jl_head, *jl_next, *jl_node;   // joiners beyond a region's capacity
     uint32_t *jl_count;
-    double *litF;
+    float *litF;   // 8 per community: F(n-1), F(n+1), WCC-hat(C), 1/((n+1)n cc), 1/((n-1)(n-2) cc)
     int32_t *touched;
     uint32_t *ntouched;
     uint32_t *tstamp;
@@ -103,7 +103,7 @@ struct RunArgs {
     int32_t *lg_keys;
     uint32_t *lg_vals;
     int32_t *lg_aux;
-    double *lg_dv;
+    float *lg_dv;
     unsigned long long lg_cap;
     int32_t lit_hub_deg;   // nodes of higher degree take the hub kernels (INT_MAX: none)
 };
@@ -1799,15 +1799,17 @@ __global__ void __launch_bounds__(AP_THREADS) k_apply(RunArgs a, int64_t bstart,
 // after every queue for the communities it touched), p, p' the
 // densities before and after, and h+_y = g_y(n+1; k_y+1) - g_y(n+1; k_y),
 // h-_y = g_y(n-1; k_y-1) - g_y(n-1; k_y) in closed forms free of
-// cancellation.  Every term is non-negative except the h-.  The F sums and
-// the factors are FP64; the corrections and g_x are FP32 (GB300's FP64 pipe
-// is the scarce one) and summed in FP32.  The exact value of the rounded
+// cancellation.  Every term is non-negative except the h-.  The F sums are
+// taken in FP64 and stored, with the factors, as floats; the corrections and
+// g_x are FP32 and summed in FP32; the bracket itself is evaluated in FP32
+// (GB300's FP64 pipe is the scarce one).  The exact value of the rounded
 // terms and the computed value both lie within
-//   E = (n + k + 64) 2.3e-16 M + (k + 16) 1.2e-7 p'/cc (|sum h| + g_x)
+//   E = (1.5e-6 + (n + k + 64) 2.3e-16) M + (k + 16) 1.2e-7 p'/cc (|sum h| + g_x)
 // of the real one (M: the same expression with every term's magnitude; the
-// FP64 part is at most 2n + k + 40 roundings of non-negative sums and a
-// handful of products, the FP32 part about ten roundings per correction plus
-// one per addition, each term counted twice over).  Per kind, candidates whose upper end cannot reach
+// FP64 sums are at most 2n + k + 40 roundings of non-negative terms, the
+// float path about ten roundings of 2^-24 on terms bounded by M (1.5e-6 is
+// 25 of them), a correction about ten roundings plus one per addition --
+// every count taken about twice over).  Per kind, candidates whose upper end cannot reach
 // the best lower end (or 0) are dropped; one surviving candidate with a
 // positive lower end is the answer; otherwise the survivors' gains are
 // computed exactly (a signed integer superaccumulator over C's members) and
@@ -1818,7 +1820,7 @@ constexpr int LW = 512;                            // table slots of one warp
 constexpr int LB_SLOTS = EV_WARPS * LW;            // table slots of a block
 constexpr uint32_t SURV_FLAG = 0x40000000u;        // candidate survives the bracket test
 constexpr uint32_t CNT_MASK = 0x3fffffffu;
-constexpr size_t LIT_SMEM = (size_t)LB_SLOTS * (8 + 4 + 4 + 4) + (size_t)EV_WARPS * SACC_CHUNKS * 8;
+constexpr size_t LIT_SMEM = (size_t)LB_SLOTS * 16 + (size_t)EV_WARPS * SACC_CHUNKS * 8;
 constexpr int LIT_PART_ENTRIES = 1024;             // entries per pass of a multi-pass node
 
 // Signed exact accumulation: like sacc_add, with negative values added as
@@ -1993,35 +1995,38 @@ __device__ __forceinline__ float lit_g32(int64_t k, int64_t d, int64_t nu) {
 
 // Bracket of one candidate: FP64 value X of the expression above and a bound
 // E on its distance from the exactly summed, once rounded gain.
-__device__ __forceinline__ void lit_screen(const RunArgs &a, int32_t C, uint32_t v, int32_t d, float Hs, double &X,
-                                           double &E) {
-    // per community (k_lit_fsum): F(n-1), F(n), F(n+1), WCC-hat(C) = p/cc F(n),
-    // 1/((n+1) n cc) and 1/((n-1)(n-2) cc) (0 where no term can be non-zero)
+__device__ __forceinline__ void lit_screen(const RunArgs &a, int32_t C, uint32_t v, int32_t d, float Hs, float &X,
+                                           float &E) {
+    // per community (k_lit_fsum, rounded to float): F(n-1), F(n+1),
+    // WCC-hat(C) = p/cc F(n), 1/((n+1) n cc), 1/((n-1)(n-2) cc)
     const bool own = (v & OWN_FLAG) != 0;
     const int64_t k = (int64_t)(v & CNT_MASK);
     const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
     const int64_t n = r.x;
-    const double m2 = (double)(uint32_t)r.y;
-    const double *f = a.litF + 6 * (int64_t)C;
-    const double B0 = __ldcg(&f[3]);
-    double A, S1, Sm, Eh;
+    const float m2 = (float)(uint32_t)r.y;
+    const float *fp = a.litF + 8 * (int64_t)C;
+    const float4 f = __ldcg(reinterpret_cast<const float4 *>(fp));
+    float A, S1, Sm, Eh;
     if (!own) {
-        A = (m2 + 2.0 * (double)k) * __ldcg(&f[4]);
-        const double gx = (double)lit_g32(k, d, n + 1);
-        S1 = (__ldcg(&f[2]) + (double)Hs) + gx;
+        A = (m2 + 2.f * (float)k) * f.w;
+        const float gx = lit_g32(k, d, n + 1);
+        S1 = (f.y + Hs) + gx;
         Sm = S1;
-        Eh = (double)Hs + gx;
+        Eh = Hs + gx;
     } else {
-        A = (m2 - 2.0 * (double)k) * __ldcg(&f[5]);
-        const double gx = A != 0.0 ? (double)lit_g32(k, d, n - 1) : 0.0;
-        const double Fm = __ldcg(&f[0]);
-        S1 = (Fm - gx) + (double)Hs;
-        Sm = (Fm + gx) - (double)Hs;
-        Eh = gx - (double)Hs;
+        A = (m2 - 2.f * (float)k) * __ldcg(&fp[4]);
+        const float gx = A != 0.f ? lit_g32(k, d, n - 1) : 0.f;
+        S1 = (f.x - gx) + Hs;
+        Sm = (f.x + gx) - Hs;
+        Eh = gx - Hs;
     }
-    X = A * S1 - B0;
-    const double M = A * Sm + B0;
-    E = ((double)(n + k) + 64.0) * 2.3e-16 * M + ((double)k + 16.0) * 1.2e-7 * (A * Eh) + 1e-300;
+    X = A * S1 - f.z;
+    const float M = A * Sm + f.z;
+    E = (1.5e-6f + ((float)(n + k) + 64.f) * 2.3e-16f) * M + ((float)k + 16.f) * 1.2e-7f * (A * Eh) + 1e-30f;
+    if (!isfinite(X) || !isfinite(E)) {   // out of float range: only the exact sum can decide
+        X = 0.f;
+        E = INFINITY;
+    }
 }
 
 // Every entry of C's member index -- the members at the iteration's start
@@ -2076,10 +2081,10 @@ __device__ double lit_exact_gain(const RunArgs &a, int32_t x, int32_t d, int32_t
 
 // Per-warp values a literal team exchanges.
 struct LitScratch {
-    double lbj[EV_WARPS], lbl[EV_WARPS];
+    float lbj[EV_WARPS], lbl[EV_WARPS];
     int cj[EV_WARPS], cl[EV_WARPS];
     int32_t sCj[EV_WARPS], sCl[EV_WARPS], skj[EV_WARPS], skl[EV_WARPS];
-    double sLj[EV_WARPS], sLl[EV_WARPS];
+    float sLj[EV_WARPS], sLl[EV_WARPS];
     double bgj[EV_WARPS], bgl[EV_WARPS];
     int32_t bcj[EV_WARPS], bcl[EV_WARPS], bkj[EV_WARPS], bkl[EV_WARPS];
     int flag[EV_WARPS];
@@ -2131,8 +2136,8 @@ __device__ __forceinline__ int lit_insert(int32_t *keys, uint32_t *vals, uint32_
 // ends of the two kinds.  Returns false (team-wide) if the table overflowed.
 template <int T>
 __device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int32_t *keys, uint32_t *vals,
-                         int32_t *aux, double *dv, uint32_t H, LitScratch &ls, int tm, int w_in, double &lbj,
-                         double &lbl, unsigned long long &pb, bool count_bytes) {
+                         int32_t *aux, float *dv, uint32_t H, LitScratch &ls, int tm, int w_in, float &lbj,
+                         float &lbl, unsigned long long &pb, bool count_bytes) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int tl = w_in * 32 + lane;
     constexpr int NT = T * 32;
@@ -2187,14 +2192,13 @@ __device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int3
         const int32_t C = keys[s];
         if (C == EMPTY_KEY) continue;
         const uint32_t v = vals[s];
-        double X, E;
+        float X, E;
         lit_screen(a, C, v, ln.d, hs[s], X, E);
-        const float Ef = __double2float_ru(E * (1.0 + 1e-6));
         dv[s] = X;
-        aux[s] = __float_as_int(Ef);
-        const double L = X - (double)Ef;
-        if (v & OWN_FLAG) lbl = fmax(lbl, L);
-        else lbj = fmax(lbj, L);
+        aux[s] = __float_as_int(E);
+        const float L = X - E;
+        if (v & OWN_FLAG) lbl = fmaxf(lbl, L);
+        else lbj = fmaxf(lbj, L);
         if (count_bytes) {
             pb += 40ull;
             atomicAdd(&a.ds->prof_cands, 1ull);
@@ -2206,10 +2210,10 @@ __device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int3
 
 // The largest value of a team (through ls.lbj/lbl slots of its warps).
 template <int T>
-__device__ __forceinline__ void team_max2(LitScratch &ls, int tm, double &x1, double &x2) {
+__device__ __forceinline__ void team_max2(LitScratch &ls, int tm, float &x1, float &x2) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    x1 = warp_max_d(x1);
-    x2 = warp_max_d(x2);
+    x1 = warp_max_f(x1);
+    x2 = warp_max_f(x2);
     if constexpr (T > 1) {
         if (lane == 0) {
             ls.lbj[w] = x1;
@@ -2217,8 +2221,8 @@ __device__ __forceinline__ void team_max2(LitScratch &ls, int tm, double &x1, do
         }
         team_sync<T>(tm);
         for (int k2 = 0; k2 < T; ++k2) {
-            x1 = fmax(x1, ls.lbj[tm * T + k2]);
-            x2 = fmax(x2, ls.lbl[tm * T + k2]);
+            x1 = fmaxf(x1, ls.lbj[tm * T + k2]);
+            x2 = fmaxf(x2, ls.lbl[tm * T + k2]);
         }
         team_sync<T>(tm);
     }
@@ -2227,28 +2231,28 @@ __device__ __forceinline__ void team_max2(LitScratch &ls, int tm, double &x1, do
 // Mark the survivors of the bracket test in the table (SURV_FLAG) and count
 // them per kind; for a lone survivor, its id, count and lower end.
 template <int T>
-__device__ void lit_mark(const RunArgs &a, int32_t *keys, uint32_t *vals, const int32_t *aux, const double *dv,
-                         uint32_t H, double lbj, double lbl, LitScratch &ls, int tm, int w_in, int &cj, int &cl,
-                         int32_t &Cj, int32_t &Cl, int32_t &kj, int32_t &kl, double &Lj, double &Ll) {
+__device__ void lit_mark(const RunArgs &a, int32_t *keys, uint32_t *vals, const int32_t *aux, const float *dv,
+                         uint32_t H, float lbj, float lbl, LitScratch &ls, int tm, int w_in, int &cj, int &cl,
+                         int32_t &Cj, int32_t &Cl, int32_t &kj, int32_t &kl, float &Lj, float &Ll) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int nj = 0, nl = 0;
     int32_t fCj = -1, fCl = -1, fkj = 0, fkl = 0;
-    double fLj = 0.0, fLl = 0.0;
+    float fLj = 0.f, fLl = 0.f;
     for (uint32_t b0 = (uint32_t)w_in * 32; b0 < H; b0 += T * 32) {
         const uint32_t s = b0 + lane;
         bool sj = false, sl = false;
         int32_t C = EMPTY_KEY;
         uint32_t v = 0;
-        double L = 0.0;
+        float L = 0.f;
         if (s < H) {
             C = keys[s];
             if (C != EMPTY_KEY) {
                 v = vals[s];
-                const double X = dv[s], E = (double)__int_as_float(aux[s]);
-                const double U = X + E;
+                const float X = dv[s], E = __int_as_float(aux[s]);
+                const float U = X + E;
                 L = X - E;
                 const bool own = (v & OWN_FLAG) != 0;
-                const bool surv = !a.screen || (U > 0.0 && U >= (own ? lbl : lbj));
+                const bool surv = !a.screen || (U > 0.f && U >= (own ? lbl : lbj));
                 if (surv) {
                     vals[s] = v | SURV_FLAG;
                     if (own) sl = true;
@@ -2263,7 +2267,7 @@ __device__ void lit_mark(const RunArgs &a, int32_t *keys, uint32_t *vals, const 
             const int src = __ffs(mj) - 1;
             const int32_t c1 = __shfl_sync(FULL, C, src);
             const uint32_t v1 = __shfl_sync(FULL, v, src);
-            const double l1 = __shfl_sync(FULL, L, src);
+            const float l1 = __shfl_sync(FULL, L, src);
             if (nj == 0) {
                 fCj = c1;
                 fkj = (int32_t)(v1 & CNT_MASK);
@@ -2275,7 +2279,7 @@ __device__ void lit_mark(const RunArgs &a, int32_t *keys, uint32_t *vals, const 
             const int src = __ffs(ml) - 1;
             const int32_t c1 = __shfl_sync(FULL, C, src);
             const uint32_t v1 = __shfl_sync(FULL, v, src);
-            const double l1 = __shfl_sync(FULL, L, src);
+            const float l1 = __shfl_sync(FULL, L, src);
             if (nl == 0) {
                 fCl = c1;
                 fkl = (int32_t)(v1 & CNT_MASK);
@@ -2349,18 +2353,18 @@ __device__ void lit_exact_survivors(const RunArgs &a, const LitNode &ln, const i
 // overflowed the table (the caller retries with more parts).
 template <int T>
 __device__ bool lit_eval_node(const RunArgs &a, int i, const LitNode &ln, int P, int32_t *keys, uint32_t *vals,
-                              int32_t *aux, double *dv, uint32_t H, LitScratch &ls, unsigned long long *acc,
+                              int32_t *aux, float *dv, uint32_t H, LitScratch &ls, unsigned long long *acc,
                               int tm, int w_in) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned long long pb = 0;
-    double lbj = -INFINITY, lbl = -INFINITY;
+    float lbj = -INFINITY, lbl = -INFINITY;
     for (int p = 0; p < P; ++p)
         if (!lit_pass<T>(a, ln, P, p, keys, vals, aux, dv, H, ls, tm, w_in, lbj, lbl, pb, a.profile != 0))
             return false;
     team_max2<T>(ls, tm, lbj, lbl);
     int cj = 0, cl = 0;
     int32_t Cj = -1, Cl = -1, kj = 0, kl = 0;
-    double Lj = 0.0, Ll = 0.0;
+    float Lj = 0.f, Ll = 0.f;
     for (int p = 0; p < P; ++p) {
         if (P > 1 && !lit_pass<T>(a, ln, P, p, keys, vals, aux, dv, H, ls, tm, w_in, lbj, lbl, pb, false))
             return false;
@@ -2368,22 +2372,22 @@ __device__ bool lit_eval_node(const RunArgs &a, int i, const LitNode &ln, int P,
     }
     Best bj{0.0, -1, 0}, bl{0.0, -1, 0};
     bool do_j = cj > 0, do_l = cl > 0;
-    if (a.screen && cj == 1 && Lj > 0.0) {
+    if (a.screen && cj == 1 && Lj > 0.f) {
         bj = Best{INFINITY, Cj, kj};
         do_j = false;
     }
-    if (a.screen && cl == 1 && Ll > 0.0) {
+    if (a.screen && cl == 1 && Ll > 0.f) {
         bl = Best{INFINITY, Cl, kl};
         do_l = false;
     }
     if (do_j || do_l) {
         for (int p = 0; p < P; ++p) {
             if (P > 1) {
-                double d1 = -INFINITY, d2 = -INFINITY;
+                float d1 = -INFINITY, d2 = -INFINITY;
                 if (!lit_pass<T>(a, ln, P, p, keys, vals, aux, dv, H, ls, tm, w_in, d1, d2, pb, false)) return false;
                 int c1 = 0, c2 = 0;
                 int32_t e1 = -1, e2 = -1, e3 = 0, e4 = 0;
-                double e5 = 0.0, e6 = 0.0;
+                float e5 = 0.f, e6 = 0.f;
                 lit_mark<T>(a, keys, vals, aux, dv, H, lbj, lbl, ls, tm, w_in, c1, c2, e1, e2, e3, e4, e5, e6);
             }
             lit_exact_survivors<T>(a, ln, keys, vals, H, do_j, do_l, acc, w_in, bj, bl);
@@ -2415,10 +2419,10 @@ __device__ bool lit_eval_node(const RunArgs &a, int i, const LitNode &ln, int P,
     return true;
 }
 
-__device__ __forceinline__ void lit_smem(double *base, double *&dv, int32_t *&keys, uint32_t *&vals, int32_t *&aux,
+__device__ __forceinline__ void lit_smem(double *base, float *&dv, int32_t *&keys, uint32_t *&vals, int32_t *&aux,
                                          unsigned long long *&acc) {
-    dv = base;
-    keys = reinterpret_cast<int32_t *>(base + LB_SLOTS);
+    dv = reinterpret_cast<float *>(base);
+    keys = reinterpret_cast<int32_t *>(dv + LB_SLOTS);
     vals = reinterpret_cast<uint32_t *>(keys + LB_SLOTS);
     aux = reinterpret_cast<int32_t *>(vals + LB_SLOTS);
     acc = reinterpret_cast<unsigned long long *>(aux + LB_SLOTS);
@@ -2432,7 +2436,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_lit_eval(RunArgs a, int64_t b
                                                            int32_t *over_list) {
     extern __shared__ double lit_dyn[];
     __shared__ LitScratch ls;
-    double *dv;
+    float *dv;
     int32_t *keys, *aux;
     uint32_t *vals;
     unsigned long long *acc;
@@ -2486,7 +2490,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_lit_big(RunArgs a, int64_t bs
     __shared__ LitScratch ls;
     __shared__ int s_i;
     __shared__ long long s_base;
-    double *dv;
+    float *dv;
     int32_t *keys, *aux;
     uint32_t *vals;
     unsigned long long *acc;
@@ -2568,14 +2572,6 @@ constexpr int LIT_HUB_DEG = 1024;
 constexpr int LH_CHUNK = 1024;       // neighbours per fill block
 constexpr int LH_SLOTS = 4096;       // table slots per bracket / mark block
 
-__device__ __forceinline__ unsigned long long d2ord(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double ord2d(unsigned long long k) {
-    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
-}
-
 struct LitHubPlan {
     const int32_t *pos;       // per hub: its position in the queue
     const int64_t *toff;      // per hub: first slot of its table
@@ -2585,16 +2581,16 @@ struct LitHubPlan {
     const int32_t *sh, *sr;   // slot items of every queue: hub, range
     const int32_t *nsr;       // per hub: its slot items (worst case)
     uint32_t *heff;           // per hub: table slots used in this queue
-    unsigned long long *lb;   // per hub: best lower ends (join, leave), order-preserving
+    int32_t *lb;              // per hub: best lower ends (join, leave), order-preserving
     uint32_t *done;           // per hub: slot items marked
     uint32_t *ns;             // per hub: survivors listed
     int32_t *sv_c;            // survivor lists: community, count word, lower end
     uint32_t *sv_v;
-    double *sv_l;
+    float *sv_l;
     int32_t *keys;            // tables: keys, counts, FP32 corrections (then E), X
     uint32_t *vals;
     float *hs;
-    double *dv;
+    float *dv;
 };
 
 // Each hub's table size for this queue: pow2 >= 2 (own row + neighbours'
@@ -2664,7 +2660,7 @@ __global__ void __launch_bounds__(256) k_lh_fill(RunArgs a, LitHubPlan hp, int64
 }
 
 __global__ void __launch_bounds__(256) k_lh_bound(RunArgs a, LitHubPlan hp, int64_t bstart, int64_t first) {
-    __shared__ double red[2][8];
+    __shared__ float red[2][8];
     const int64_t it = first + blockIdx.x;
     const int h = hp.sh[it], r = hp.sr[it];
     const int32_t x = a.order[bstart + hp.pos[h]];
@@ -2672,24 +2668,23 @@ __global__ void __launch_bounds__(256) k_lh_bound(RunArgs a, LitHubPlan hp, int6
     const int64_t t0 = hp.toff[h];
     const uint32_t lo = (uint32_t)r * LH_SLOTS, hi = min(__ldcg(&hp.heff[h]), lo + LH_SLOTS);
     if (lo >= hi) return;   // beyond this queue's table
-    double lbj = -INFINITY, lbl = -INFINITY;
+    float lbj = -INFINITY, lbl = -INFINITY;
     unsigned long long nc = 0;
     for (uint32_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
         const int32_t C = hp.keys[t0 + s];
         if (C == EMPTY_KEY) continue;
         const uint32_t v = hp.vals[t0 + s];
-        double X, E;
+        float X, E;
         lit_screen(a, C, v, d, hp.hs[t0 + s], X, E);
-        const float Ef = __double2float_ru(E * (1.0 + 1e-6));
         hp.dv[t0 + s] = X;
-        hp.hs[t0 + s] = Ef;
-        const double L = X - (double)Ef;
-        if (v & OWN_FLAG) lbl = fmax(lbl, L);
-        else lbj = fmax(lbj, L);
+        hp.hs[t0 + s] = E;
+        const float L = X - E;
+        if (v & OWN_FLAG) lbl = fmaxf(lbl, L);
+        else lbj = fmaxf(lbj, L);
         ++nc;
     }
-    lbj = warp_max_d(lbj);
-    lbl = warp_max_d(lbl);
+    lbj = warp_max_f(lbj);
+    lbl = warp_max_f(lbl);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
         red[0][w] = lbj;
@@ -2705,9 +2700,9 @@ __global__ void __launch_bounds__(256) k_lh_bound(RunArgs a, LitHubPlan hp, int6
     }
     __syncthreads();
     if (threadIdx.x < 2) {
-        double m = -INFINITY;
-        for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) m = fmax(m, red[threadIdx.x][k2]);
-        if (m > -INFINITY) atomicMax(&hp.lb[2 * h + threadIdx.x], d2ord(m));
+        float m = -INFINITY;
+        for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) m = fmaxf(m, red[threadIdx.x][k2]);
+        if (m > -INFINITY) atomicMax(&hp.lb[2 * h + threadIdx.x], f2ord(m));
     }
 }
 
@@ -2722,7 +2717,7 @@ __global__ void __launch_bounds__(256) k_lh_mark(RunArgs a, LitHubPlan hp, int64
     const int32_t x = a.order[bstart + i];
     const int32_t d = (int32_t)(a.off[x + 1] - a.off[x]);
     const int64_t t0 = hp.toff[h], so = hp.soff[h];
-    const double lbj = ord2d(__ldcg(&hp.lb[2 * h])), lbl = ord2d(__ldcg(&hp.lb[2 * h + 1]));
+    const float lbj = ord2f(__ldcg(&hp.lb[2 * h])), lbl = ord2f(__ldcg(&hp.lb[2 * h + 1]));
     const uint32_t heff = __ldcg(&hp.heff[h]);
     const uint32_t lo = (uint32_t)r * LH_SLOTS, hi = min(heff, lo + LH_SLOTS);
     if (lo >= hi) return;   // beyond this queue's table
@@ -2730,10 +2725,10 @@ __global__ void __launch_bounds__(256) k_lh_mark(RunArgs a, LitHubPlan hp, int64
         const int32_t C = hp.keys[t0 + s];
         if (C == EMPTY_KEY) continue;
         const uint32_t v = hp.vals[t0 + s];
-        const double X = hp.dv[t0 + s], E = (double)hp.hs[t0 + s];
-        const double U = X + E;
+        const float X = hp.dv[t0 + s], E = hp.hs[t0 + s];
+        const float U = X + E;
         const bool own = (v & OWN_FLAG) != 0;
-        if (!a.screen || (U > 0.0 && U >= (own ? lbl : lbj))) {
+        if (!a.screen || (U > 0.f && U >= (own ? lbl : lbj))) {
             const uint32_t e = atomicAdd(&hp.ns[h], 1u);
             hp.sv_c[so + e] = C;
             hp.sv_v[so + e] = v;
@@ -2754,11 +2749,11 @@ __global__ void __launch_bounds__(256) k_lh_mark(RunArgs a, LitHubPlan hp, int64
     const uint32_t ns = __ldcg(&hp.ns[h]);
     int cj = 0, cl = 0;
     int32_t Cj = -1, Cl = -1, kj = 0, kl = 0;
-    double Lj = 0.0, Ll = 0.0;
+    float Lj = 0.f, Ll = 0.f;
     for (uint32_t e = 0; e < ns; ++e) {   // every thread reads the (short) list
         const uint32_t v = __ldcg(&hp.sv_v[so + e]);
         const int32_t C = __ldcg(&hp.sv_c[so + e]);
-        const double L = __ldcg(&hp.sv_l[so + e]);
+        const float L = __ldcg(&hp.sv_l[so + e]);
         if (v & OWN_FLAG) {
             if (cl++ == 0) { Cl = C; kl = (int32_t)(v & CNT_MASK); Ll = L; }
         } else {
@@ -2767,11 +2762,11 @@ __global__ void __launch_bounds__(256) k_lh_mark(RunArgs a, LitHubPlan hp, int64
     }
     Best bj{0.0, -1, 0}, bl{0.0, -1, 0};
     bool do_j = cj > 0, do_l = cl > 0;
-    if (a.screen && cj == 1 && Lj > 0.0) {
+    if (a.screen && cj == 1 && Lj > 0.f) {
         bj = Best{INFINITY, Cj, kj};
         do_j = false;
     }
-    if (a.screen && cl == 1 && Ll > 0.0) {
+    if (a.screen && cl == 1 && Ll > 0.f) {
         bl = Best{INFINITY, Cl, kl};
         do_l = false;
     }
@@ -2808,8 +2803,8 @@ __global__ void __launch_bounds__(256) k_lh_mark(RunArgs a, LitHubPlan hp, int64
         if (a.profile) atomicAdd(&a.ds->prof_bytes, 44ull + 8ull * (unsigned long long)__ldcg(&a.nmem[x]));
         hp.done[h] = 0u;   // ready for the hub's next queue
         hp.ns[h] = 0u;
-        hp.lb[2 * h] = d2ord(-INFINITY);
-        hp.lb[2 * h + 1] = d2ord(-INFINITY);
+        hp.lb[2 * h] = f2ord(-INFINITY);
+        hp.lb[2 * h + 1] = f2ord(-INFINITY);
     }
 }
 
@@ -2960,20 +2955,20 @@ __device__ __forceinline__ void lit_fsum_member(const RunArgs &a, int32_t C, int
     f2 += lit_g(ky, dy, n + 1);
 }
 
-// The six per-community values of the bracket from the member sums.
+// The per-community values of the bracket from the member sums (rounded
+// to float; the bound E allows for it).
 __device__ __forceinline__ void lit_fsum_store(const RunArgs &a, int32_t C, double f0, double f1, double f2) {
     const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
     const int64_t n = r.x;
     const double m2 = (double)(uint32_t)r.y;
     const double cc = a.gcc ? a.gcc[r.w] : a.cc;
     const bool on = cc > 0.0 && n >= 1;
-    double *f = a.litF + 6 * (int64_t)C;
-    f[0] = f0;
-    f[1] = f1;
-    f[2] = f2;
-    f[3] = on && n >= 2 ? ((m2 / ((double)n * (double)(n - 1))) / cc) * f1 : 0.0;
-    f[4] = on ? (1.0 / ((double)(n + 1) * (double)n)) / cc : 0.0;
-    f[5] = on && n - 1 >= 2 ? (1.0 / ((double)(n - 1) * (double)(n - 2))) / cc : 0.0;
+    float *f = a.litF + 8 * (int64_t)C;
+    f[0] = (float)f0;
+    f[1] = (float)f2;
+    f[2] = on && n >= 2 ? (float)(((m2 / ((double)n * (double)(n - 1))) / cc) * f1) : 0.f;
+    f[3] = on ? (float)((1.0 / ((double)(n + 1) * (double)n)) / cc) : 0.f;
+    f[4] = on && n - 1 >= 2 ? (float)((1.0 / ((double)(n - 1) * (double)(n - 2))) / cc) : 0.f;
 }
 
 __global__ void __launch_bounds__(256) k_lit_fsum(RunArgs a, const int32_t *list, const uint32_t *count,
@@ -3807,7 +3802,7 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.ntouched = g->lit_ctr;
     a.tstamp = g->tstamp;
     a.lg_cap = g->lg_cap;
-    a.lg_dv = static_cast<double *>(g->lg_area);
+    a.lg_dv = static_cast<float *>(g->lg_area);
     a.lg_keys = reinterpret_cast<int32_t *>(a.lg_dv + g->lg_cap);
     a.lg_vals = reinterpret_cast<uint32_t *>(a.lg_keys + g->lg_cap);
     a.lg_aux = reinterpret_cast<int32_t *>(a.lg_vals + g->lg_cap);
@@ -4149,20 +4144,20 @@ void build_lit_hub_plan(lf_graph *g, int64_t q, int64_t nb) {
     LF_CUDA(cudaMemsetAsync(g->lh_done, 0, (size_t)H * 4, g->stream));
     LF_CUDA(cudaMemsetAsync(g->lh_ns, 0, (size_t)H * 4, g->stream));
     {
-        // best lower ends start at -inf (order-preserving: ~bits of -inf)
-        const unsigned long long ninf = ~0xfff0000000000000ull;
-        std::vector<unsigned long long> lb((size_t)(2 * H), ninf);
+        // best lower ends start at -inf (order-preserving: -inf's bits ^ 0x7fffffff)
+        const int32_t ninf = (int32_t)(0xff800000u ^ 0x7fffffffu);
+        std::vector<int32_t> lb((size_t)(2 * H), ninf);
         up(g->lh_lb, lb);
     }
     g->lh_tab_cap = area;
-    g->lh_tab = dalloc(g, (size_t)area * 20);
+    g->lh_tab = dalloc(g, (size_t)area * 16);
     // keys empty, counts and corrections zero (the X area needs no start value)
     char *t = static_cast<char *>(g->lh_tab);
-    LF_CUDA(cudaMemsetAsync(t + (size_t)area * 8, 0xff, (size_t)area * 4, g->stream));
-    LF_CUDA(cudaMemsetAsync(t + (size_t)area * 12, 0, (size_t)area * 8, g->stream));
+    LF_CUDA(cudaMemsetAsync(t + (size_t)area * 4, 0xff, (size_t)area * 4, g->stream));
+    LF_CUDA(cudaMemsetAsync(t + (size_t)area * 8, 0, (size_t)area * 8, g->stream));
     g->lh_svc = dalloc_n<int32_t>(g, area / 2);
     g->lh_svv = dalloc_n<uint32_t>(g, area / 2);
-    g->lh_svl = dalloc_n<double>(g, area / 2);
+    g->lh_svl = dalloc_n<float>(g, area / 2);
     LF_CUDA(cudaStreamSynchronize(g->stream));
 }
 
@@ -4185,7 +4180,7 @@ LitHubPlan lit_hub_plan(lf_graph *g) {
     hp.sv_v = g->lh_svv;
     hp.sv_l = g->lh_svl;
     const int64_t cap = g->lh_tab_cap;
-    hp.dv = static_cast<double *>(g->lh_tab);
+    hp.dv = static_cast<float *>(g->lh_tab);
     hp.keys = reinterpret_cast<int32_t *>(hp.dv + cap);
     hp.vals = reinterpret_cast<uint32_t *>(hp.keys + cap);
     hp.hs = reinterpret_cast<float *>(hp.vals + cap);
@@ -4251,7 +4246,7 @@ void launch_batches_lit(lf_graph *g, const RunArgs &a, int64_t q, int64_t first,
 void ensure_lit(lf_graph *g, int64_t q, int64_t nb) {
     const int64_t n = std::max<int64_t>(g->n, 1);
     if (!g->litF) {
-        g->litF = dalloc_n<double>(g, 6 * n);
+        g->litF = dalloc_n<float>(g, 8 * n);
         g->cm_off = dalloc_n<unsigned long long>(g, n + 1);
         g->cm_cur = dalloc_n<unsigned long long>(g, n + 1);
         g->jl_head = dalloc_n<int32_t>(g, n);
@@ -4318,7 +4313,7 @@ void ensure_lit(lf_graph *g, int64_t q, int64_t nb) {
         }
         if (cap != g->lg_cap) {
             if (g->lg_area) dfree(g, g->lg_area);
-            g->lg_area = cap ? dalloc(g, (size_t)cap * 20) : nullptr;
+            g->lg_area = cap ? dalloc(g, (size_t)cap * 16) : nullptr;
             g->lg_cap = cap;
             drop_graph(g);
         }
