@@ -2484,7 +2484,7 @@ __global__ void __launch_bounds__(EV_THREADS, 2) k_lit_eval(RunArgs a, int64_t b
 
 // Listed nodes, one block each, over the block's whole table in as many
 // parts as needed (a part that overflows doubles the parts).
-__global__ void __launch_bounds__(EV_THREADS, 2) k_lit_big(RunArgs a, int64_t bstart, uint32_t *over,
+__global__ void __launch_bounds__(EV_THREADS, 3) k_lit_big(RunArgs a, int64_t bstart, uint32_t *over,
                                                           const int32_t *over_list, unsigned long long *used) {
     extern __shared__ double lit_dyn[];
     __shared__ LitScratch ls;
