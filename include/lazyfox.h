@@ -454,10 +454,16 @@ lf_status lf_run_partial(lf_graph *g, int32_t queue_size, double wcc_threshold, 
  * t, vt           : device outputs, num_nodes each (overwritten);
  * stream          : cudaStream_t the work is queued on (NULL: legacy default).
  * Limit: num_edges + 4 num_nodes + ~1 KiB must fit in the 16 MiB array, else
- * LF_ERR_CAPACITY (nothing is launched).  The call returns when the work is
- * queued; results are ready when the stream reaches them.
- * The first call on each device looks the array up (with that device
- * current); make that first call before any stream capture.  Every call uses
+ * LF_ERR_CAPACITY (nothing is launched).  The input is checked on the device
+ * first (offsets from 0 to num_edges, non-decreasing, neighbour ids in
+ * [0, num_nodes)); the call waits for that check (one 4-byte read) and
+ * returns LF_ERR_INVALID for a malformed CSR without launching the counting.
+ * Otherwise it returns when the counting is queued; results are ready when
+ * the stream reaches them.  Because of that wait the call cannot be captured
+ * in a CUDA graph.
+ * Every call looks the array's device address up (with the call's device
+ * current; the first call on a device also raises the kernels' shared-memory
+ * limits).  Every call uses
  * the same array, which keeps the previous call's contents (the call clears
  * what must start at zero): calls whose work overlaps on a GPU race with each
  * other and must be ordered by the caller (e.g. one stream).

@@ -51,16 +51,21 @@ void *dalloc(lf_graph *g, size_t bytes) {
     return p;
 }
 
+// Frees only what this handle holds: a pointer already freed (a member left
+// dangling when the allocation that was to replace it failed) is ignored.
 void dfree(lf_graph *g, void *p) {
     if (!p) return;
     size_t bytes = 0;
+    bool held = false;
     for (size_t i = 0; i < g->live.size(); ++i)
         if (g->live[i].first == p) {
             bytes = g->live[i].second;
             g->live[i] = g->live.back();
             g->live.pop_back();
+            held = true;
             break;
         }
+    if (!held) return;
     if (g->free_cb) g->free_cb(p, bytes, (void *)g->stream, g->alloc_ctx);
     else cudaFreeAsync(p, g->stream);
 }
@@ -133,6 +138,7 @@ lf_status call_guarded(F &&fn) {
 
 void release_all(lf_graph *g) {
     if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);   // no kernel may still use what is freed
     free_run_state(g);
     while (!g->live.empty()) dfree(g, g->live.back().first);
     if (g->stream) cudaStreamSynchronize(g->stream);
@@ -142,6 +148,26 @@ void release_all(lf_graph *g) {
     g->gT_host = nullptr;
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     g->stream = nullptr;
+}
+
+// After a run that failed part way (an allocation that returned NULL, a
+// CUDA error, a device-side timeout), the run state may be half built: wait
+// for the stream, drop all of it, and let the next run start from scratch.
+void abandon_run(lf_graph *g) {
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    try {
+        free_run_state(g);
+    } catch (...) {
+    }
+    g->ran = false;
+}
+
+template <typename F>
+lf_status run_guarded(lf_graph *g, F &&fn) {
+    const lf_status st = call_guarded(fn);
+    if (st != LF_OK) abandon_run(g);
+    return st;
 }
 
 }  // namespace
@@ -369,7 +395,7 @@ lf_status lf_run(lf_graph *g, int32_t queue_size, double wcc_threshold, int32_t 
         set_error(LF_ERR_STATE, "lf_run inside an iteration callback");
         return LF_ERR_STATE;
     }
-    return call_guarded([&] { run_impl(g, queue_size, wcc_threshold, max_iters, -1, stats); });
+    return run_guarded(g, [&] { run_impl(g, queue_size, wcc_threshold, max_iters, -1, stats); });
 }
 
 lf_status lf_set_partition(lf_graph *g, const int64_t *offsets, const int32_t *members, int64_t num_communities) {
@@ -442,7 +468,7 @@ lf_status lf_autotune(lf_graph *g, int32_t queue_size, int32_t trial_iters, lf_t
         set_error(LF_ERR_INVALID, "queue_size and trial_iters must be >= 1");
         return LF_ERR_INVALID;
     }
-    return call_guarded([&] {
+    return run_guarded(g, [&] {
         const int32_t teams[4] = {0, 1, 2, 4};
         const int32_t limits[3] = {0, 96, 192};
         const int32_t hubs[2] = {384, 128};
@@ -527,7 +553,7 @@ lf_status lf_run_partial(lf_graph *g, int32_t queue_size, double wcc_threshold, 
         set_error(LF_ERR_STATE, "lf_run inside an iteration callback");
         return LF_ERR_STATE;
     }
-    return call_guarded([&] { run_impl(g, queue_size, wcc_threshold, max_iters, max_batches, stats); });
+    return run_guarded(g, [&] { run_impl(g, queue_size, wcc_threshold, max_iters, max_batches, stats); });
 }
 
 lf_status lf_get_sizes(lf_graph *g, int64_t *num_nodes, int64_t *num_edges) {

@@ -1589,24 +1589,39 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES]
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
-unsigned char *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+bool g_noalloc_attrs[NOALLOC_MAX_DEVICES] = {};
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Device address of the array on the current device (the host-side symbol is
-// only a stand-in), looked up once per device with that device current.
+// only a stand-in), looked up on every call with that device current (so a
+// device reset between calls does not leave a stale address); the kernels'
+// shared-memory limits are raised once per device.
 unsigned char *noalloc_scratch() {
     int dev = 0;
     LF_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) fail(LF_ERR_CAPACITY, "device %d beyond %d", dev, NOALLOC_MAX_DEVICES);
+    void *p = nullptr;
+    LF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        LF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    if (!g_noalloc_attrs[dev]) {
         set_triangle_attrs();
-        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+        g_noalloc_attrs[dev] = true;
     }
-    return g_noalloc_ptr[dev];
+    return static_cast<unsigned char *>(p);
+}
+
+// The oriented CSR must be well formed before the counting kernels index
+// the array with it: offsets from 0 to m, non-decreasing, ids in [0, n).
+// Any violation sets *bad.
+__global__ void k_noalloc_check(const int64_t *ooff, const int32_t *oadj, int64_t n, int64_t m, int32_t *bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0 && (ooff[0] != 0 || ooff[n] != m)) atomicOr(bad, 1);
+    for (int64_t x = i0; x < n; x += stride)
+        if (ooff[x + 1] < ooff[x]) atomicOr(bad, 1);
+    for (int64_t e = i0; e < m; e += stride)
+        if (oadj[e] < 0 || (int64_t)oadj[e] >= n) atomicOr(bad, 1);
 }
 
 }  // namespace
@@ -1635,6 +1650,16 @@ void triangles_noalloc(const int64_t *ooff, const int32_t *oadj, int64_t n, int6
     LF_CUDA(cudaMemsetAsync(nh, 0, 2 * sizeof(uint32_t), st));
     if (m > 0) LF_CUDA(cudaMemsetAsync(sup, 0, (size_t)m, st));
     if (n == 0) return;
+    // validate the input first (its flag is a word of the array; the host
+    // waits for it: a malformed CSR is rejected before anything indexes with it)
+    k_noalloc_check<<<grid_for(std::max(n, m), 256, 1 << 14), 256, 0, st>>>(ooff, oadj, n, m, &ds->err);
+    LF_LAUNCHED();
+    int32_t bad = 0;
+    LF_CUDA(cudaMemcpyAsync(&bad, &ds->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    LF_CUDA(cudaStreamSynchronize(st));
+    if (bad)
+        fail(LF_ERR_INVALID, "malformed oriented CSR: offsets must run from 0 to num_edges without decreasing "
+                             "and every neighbour id must lie in [0, num_nodes)");
     LF_CUDA(cudaMemsetAsync(t, 0, (size_t)n * sizeof(int64_t), st));
     LF_CUDA(cudaMemsetAsync(vt, 0, (size_t)n * sizeof(int32_t), st));
     unsigned long long *utri = reinterpret_cast<unsigned long long *>(t);

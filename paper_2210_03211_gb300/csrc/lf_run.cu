@@ -4311,6 +4311,9 @@ void ensure_lit(lf_graph *g, int64_t q, int64_t nb) {
                 cap = std::max(cap, used);
             }
         }
+        // the area is a reservation for the worst case; past 32 MiB + 64 bytes
+        // per edge a node that finds no room takes the multi-pass shared path
+        cap = std::min<unsigned long long>(cap, ((32ull << 20) + 64ull * (unsigned long long)g->m) / 16);
         if (cap != g->lg_cap) {
             if (g->lg_area) dfree(g, g->lg_area);
             g->lg_area = cap ? dalloc(g, (size_t)cap * 16) : nullptr;

@@ -174,6 +174,37 @@ class _TorchAllocator:
             self._torch.cuda.caching_allocator_delete(ptr)
 
 
+class CountingAllocator(_TorchAllocator):
+    """The torch allocator bridge with accounting: allocations made, bytes live
+    and their peak.  ``fail_at`` (1-based) makes that allocation return NULL,
+    as a failing device allocator would (the library then reports
+    LF_ERR_OOM).  Pass it as ``Graph(..., allocator=CountingAllocator(dev))``."""
+
+    def __init__(self, device, fail_at=None):
+        super().__init__(device)
+        self.fail_at = fail_at
+        self.calls = 0
+        self.live = 0
+        self.peak = 0
+        self._sizes = {}
+
+    def _alloc(self, nbytes, stream, ctx):
+        self.calls += 1
+        if self.fail_at is not None and self.calls == self.fail_at:
+            return None
+        ptr = super()._alloc(nbytes, stream, ctx)
+        if ptr:
+            self._sizes[ptr] = int(nbytes)
+            self.live += int(nbytes)
+            self.peak = max(self.peak, self.live)
+        return ptr
+
+    def _free(self, ptr, nbytes, stream, ctx):
+        if ptr:
+            self.live -= self._sizes.pop(ptr, 0)
+        super()._free(ptr, nbytes, stream, ctx)
+
+
 @dataclasses.dataclass
 class RunStats:
     iterations: int
@@ -202,7 +233,8 @@ class Graph:
 
     ``src``/``dst``: numpy int32 arrays (host) or int32 CUDA tensors (device).
     ``stream``: a ``torch.cuda.Stream`` (default: torch's current stream).
-    ``allocator``: "torch" (caching allocator) or "cuda" (cudaMallocAsync).
+    ``allocator``: "torch" (caching allocator), "cuda" (cudaMallocAsync) or a
+    :class:`CountingAllocator`.
     """
 
     def __init__(self, src, dst, *, stream=None, allocator: str = "torch", member_slots: int = 0,
@@ -228,10 +260,13 @@ class Graph:
         self._allocator = None
         if allocator == "torch":
             self._allocator = _TorchAllocator(self.device)
-            opt.alloc = self._allocator.alloc
-            opt.free = self._allocator.free
+        elif isinstance(allocator, _TorchAllocator):
+            self._allocator = allocator
         elif allocator != "cuda":
             raise ValueError(allocator)
+        if self._allocator is not None:
+            opt.alloc = self._allocator.alloc
+            opt.free = self._allocator.free
         opt.member_slots = int(member_slots)
         opt.warp_max_degree = int(warp_max_degree)
         opt.use_graphs = 0 if use_graphs else -1
@@ -681,7 +716,8 @@ def lf_last_error() -> str:
 def lf_triangles_noalloc(ooff, oadj, t, vt, stream=None) -> None:
     """t(x,V) and vt(x,V) of an oriented CSR (device tensors: ooff int64[n+1],
     oadj int32[m]) into device tensors t int64[n] and vt int32[n], without any
-    device allocation (``stream``: a torch.cuda.Stream or None)."""
+    device allocation (``stream``: a torch.cuda.Stream; default torch's
+    current stream)."""
     import torch
     for a, dt in ((ooff, torch.int64), (oadj, torch.int32), (t, torch.int64), (vt, torch.int32)):
         if not isinstance(a, torch.Tensor) or a.dtype != dt or not a.is_cuda or not a.is_contiguous():
@@ -691,7 +727,9 @@ def lf_triangles_noalloc(ooff, oadj, t, vt, stream=None) -> None:
     if n < 0 or t.numel() < n or vt.numel() < n:
         raise ValueError("ooff needs n+1 entries and t, vt n each")
     L = load_library()
-    st = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    # default: torch's current stream, so that work queued there before the
+    # call (e.g. the writes of the inputs) is ordered before it
+    st = C.c_void_p((stream if stream is not None else torch.cuda.current_stream(ooff.device)).cuda_stream)
     _check(L, L.lf_triangles_noalloc(C.c_void_p(ooff.data_ptr()), C.c_void_p(oadj.data_ptr()), n, oadj.numel(),
                                      C.c_void_p(t.data_ptr()), C.c_void_p(vt.data_ptr()), st))
 

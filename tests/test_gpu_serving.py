@@ -107,3 +107,39 @@ def test_destroy_cancels_jobs_not_yet_admitted(lf):
     assert not t.is_alive()
     assert "err" in out, out
     assert out["err"].status == lf.LF_ERR_STATE and "cancelled" in str(out["err"])
+
+
+def test_admission_estimate_bounds_each_jobs_device_memory(lf):
+    """The memory the server reserves for a job (est_bytes, from its edge
+    count) is at least the device memory the same graph's run actually
+    holds at its peak (counted through the allocation callbacks); with the
+    admission rule (reserved estimates within the budget) the jobs resident
+    at any time therefore fit the budget.  Graphs of the serving workload's
+    shape (planted, average degree 10-80), a hub graph and the power-law
+    workload at 10%."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    graphs = W.serving_jobs(10, seed=7, n_hi=60000)[0]
+    graphs += [W.random_graph(n=3000, m=9000, seed=12, hubs=2, hub_degree=2600), W.dblp_like(scale=0.1)]
+    with lf.Server(max_active=2) as srv:
+        est = [srv.wait(srv.submit(el.src, el.dst, 1024, 0.01, 50))["est_bytes"] for el in graphs]
+    for el, e in zip(graphs, est):
+        a = lf.CountingAllocator(dev)
+        with lf.Graph(el.src, el.dst, allocator=a) as g:
+            g.run(1024, 0.01, 50)
+            g.communities()
+        assert 0 < a.peak <= e, (len(el.src), a.peak, e)
+
+
+def test_resident_estimates_stay_within_the_budget(lf):
+    """Jobs overlapping in time never reserve more than the budget together
+    (a job larger than the whole budget runs alone)."""
+    graphs = jobs()
+    budget = 3 * max(228 * len(el.src) + (64 << 20) for el in graphs) // 2
+    with lf.Server(hbm_budget_bytes=budget, max_active=4) as srv:
+        ids = [srv.submit(el.src, el.dst, 256, 0.01, 50) for el in graphs]
+        res = [srv.wait(j) for j in ids]
+    for r in res:
+        others = [o for o in res if o is not r and o["t_admit_ms"] < r["t_done_ms"] and r["t_admit_ms"] < o["t_done_ms"]]
+        overlapping = r["est_bytes"] + sum(o["est_bytes"] for o in others if o["t_admit_ms"] <= r["t_admit_ms"])
+        assert r["est_bytes"] > budget or overlapping <= budget, (r, budget)

@@ -30,13 +30,16 @@ def lf():
 
 @pytest.mark.parametrize("make", [lambda: W.dblp_like(seed=5, scale=0.05), lambda: W.wide_fan(seed=9)],
                          ids=["dblp_like_5pct", "wide_fan"])
-def test_noalloc_triangles_equal_the_allocating_path_twice(lf, make):
+def test_noalloc_triangles_equal_the_allocating_path_twice(lf, oracle_lib, make):
     import torch
     el = make()
     with lf.Graph(el.src, el.dst) as g:
         t_ref, vt_ref, _ = g.node_stats()
         ooff, oadj = g.oriented()
         n, m = g.n, g.m
+    # the allocating path is itself the oracle's (triangles by sorted merges)
+    ot, ovt, _ = oracle_lib.OracleGraph(el.src, el.dst).node_stats()
+    assert np.array_equal(t_ref, ot) and np.array_equal(vt_ref, ovt)
     L = lf.load_library()
     d_ooff = torch.from_numpy(ooff).cuda()
     d_oadj = torch.from_numpy(oadj).cuda()
@@ -53,6 +56,34 @@ def test_noalloc_triangles_equal_the_allocating_path_twice(lf, make):
         torch.cuda.synchronize()
         assert np.array_equal(d_t.cpu().numpy(), t_ref), f"call {call}"
         assert np.array_equal(d_vt.cpu().numpy(), vt_ref), f"call {call}"
+        assert np.array_equal(d_t.cpu().numpy(), ot) and np.array_equal(d_vt.cpu().numpy(), ovt), f"call {call}"
+
+
+def test_noalloc_rejects_a_malformed_csr(lf):
+    """Offsets that do not end at num_edges, or a neighbour id outside the
+    nodes, are rejected (LF_ERR_INVALID) before any counting kernel runs."""
+    import torch
+    L = lf.load_library()
+    n, m = 4, 3
+    t = torch.zeros(n, dtype=torch.int64, device="cuda")
+    vt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    good_off = torch.tensor([0, 2, 3, 3, 3], dtype=torch.int64, device="cuda")
+    for off, adj in ((torch.tensor([0, 2, 3, 3, 5], dtype=torch.int64, device="cuda"),
+                      torch.tensor([1, 2, 2], dtype=torch.int32, device="cuda")),
+                     (good_off, torch.tensor([1, 2, 9], dtype=torch.int32, device="cuda")),
+                     (torch.tensor([0, 3, 2, 3, 3], dtype=torch.int64, device="cuda"),
+                      torch.tensor([1, 2, 2], dtype=torch.int32, device="cuda"))):
+        st = L.lf_triangles_noalloc(C.c_void_p(off.data_ptr()), C.c_void_p(adj.data_ptr()), n, m,
+                                    C.c_void_p(t.data_ptr()), C.c_void_p(vt.data_ptr()), None)
+        assert st == lf.LF_ERR_INVALID, L.lf_last_error()
+        assert b"malformed" in L.lf_last_error()
+    # and a well-formed one still works afterwards (a triangle 0-1-2 and node 3 alone)
+    adj = torch.tensor([1, 2, 2], dtype=torch.int32, device="cuda")
+    st = L.lf_triangles_noalloc(C.c_void_p(good_off.data_ptr()), C.c_void_p(adj.data_ptr()), n, m,
+                                C.c_void_p(t.data_ptr()), C.c_void_p(vt.data_ptr()), None)
+    assert st == lf.LF_OK, L.lf_last_error()
+    torch.cuda.synchronize()
+    assert t.cpu().tolist() == [1, 1, 1, 0] and vt.cpu().tolist() == [2, 2, 2, 0]
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(lf):
