@@ -216,6 +216,7 @@ lf_status create_handle(const int32_t *src, const int32_t *dst, int64_t num_edge
             if (opt->gain_rule != 0 && opt->gain_rule != LF_GAIN_LITERAL && opt->gain_rule != LF_GAIN_MEANFIELD)
                 fail(LF_ERR_INVALID, "unknown gain_rule %d", opt->gain_rule);
             if (opt->gain_rule != 0) g->gain_rule = opt->gain_rule;
+            g->debug_checks = opt->debug_checks == 1 ? 1 : 0;
             if ((g->alloc_cb == nullptr) != (g->free_cb == nullptr))
                 fail(LF_ERR_INVALID, "alloc and free callbacks must be set together");
         }

@@ -109,6 +109,7 @@ struct lf_graph {
     int32_t warps_per_node = 0;                    // team size of the move evaluation (0: by queue size)
     int32_t hub_degree = 384;                      // above it a node takes the hub path
     int32_t gain_rule = LF_GAIN_LITERAL;           // decision rule of the move evaluation (paper's gain)
+    int32_t debug_checks = 0;                      // bounds-checked kernels
     unsigned long long launches = 0;               // kernels launched (host count)
     std::vector<std::pair<void *, size_t>> live;   // outstanding allocations
 

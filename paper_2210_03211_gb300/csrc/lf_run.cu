@@ -42,6 +42,7 @@ struct RunArgs {
     int64_t nnodes;
     int32_t warp_max_deg;
     int32_t profile;   // count algorithmic bytes of the move evaluation
+    int32_t debug;     // bounds-checked mode: every index read from device state is checked first
     // hubs: nodes of degree > huge_deg are evaluated one block each with a
     // hash table in global memory (hkeys/hvals/hub_ub/hub_lb at hub_toff[h]),
     // listed per queue: hub_pos[hub_qoff[b] .. hub_qoff[b+1]) are positions
@@ -1908,6 +1909,15 @@ __device__ inline double ssacc_round_and_clear(unsigned long long *acc) {
     return neg ? -r : r;
 }
 
+// Bounds-checked mode (lf_options.debug_checks): a value read from device
+// state that is out of its range sets DERR_CHECK and the access is skipped
+// (never a trap; the call then fails with a message).
+__device__ __forceinline__ bool dbg_ok(const RunArgs &a, bool ok) {
+    if (!a.debug || ok) return true;
+    atomicOr(&a.ds->err, DERR_CHECK);
+    return false;
+}
+
 // Position of C in a row of cnt ascending ids, -1 if absent.
 __device__ __forceinline__ int row_find(const int32_t *row, int32_t cnt, int32_t C) {
     int lo = 0, hi = cnt - 1;
@@ -2061,11 +2071,14 @@ __device__ double lit_exact_gain(const RunArgs &a, int32_t x, int32_t d, int32_t
     const int64_t xb = a.off[x], xe = a.off[x + 1];
     auto member = [&](int32_t y) {
         if (y == x) return;
+        if (!dbg_ok(a, y >= 0 && y < a.nnodes)) return;
         const int32_t cy = __ldcg(&a.nmem[y]);
+        if (!dbg_ok(a, cy >= 0 && cy <= a.K)) return;
         const int s = row_find(a.mem + (int64_t)y * a.K, cy, C);
         if (s < 0) return;   // left C earlier in this iteration
         const int64_t ky = __ldcg(&a.kmem[(int64_t)y * a.K + s]);
         const int64_t dy = a.deg[y];
+        if (!dbg_ok(a, ky >= 0 && ky <= dy)) return;
         const int64_t k1 = adj_has(a.adj, xb, xe, y) ? (own ? ky - 1 : ky + 1) : ky;
         ssacc_add(acc, wcchat_member(k1, dy, n1, m21, cc));
         ssacc_add(acc, -wcchat_member(ky, dy, n0, m20, cc));
@@ -2158,15 +2171,19 @@ __device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int3
     team_sync<T>(tm);
     for (int64_t q = ln.beg + tl; q < ln.end; q += NT) {
         const int32_t y = a.adj[q];
+        if (!dbg_ok(a, y >= 0 && y < a.nnodes)) continue;
         const int32_t cy = __ldcg(&a.nmem[y]);
+        if (!dbg_ok(a, cy >= 0 && cy <= a.K)) continue;
         const int32_t *rowy = a.mem + (int64_t)y * a.K;
         const int32_t *krow = a.kmem + (int64_t)y * a.K;
         const int64_t dy = a.deg[y];
         if (count_bytes) pb += 12ull + 8ull * (unsigned long long)cy;
         for (int s = 0; s < cy; ++s) {
             const int32_t C = __ldcg(&rowy[s]);
+            if (!dbg_ok(a, C >= 0 && C < a.nnodes)) continue;
             if (P > 1 && (int)part_of(C, P) != p) continue;
             const int64_t ky = __ldcg(&krow[s]);
+            if (!dbg_ok(a, ky >= 0 && ky <= dy)) continue;
             const int64_t n = __ldcg(&a.comm[C].n);
             const int slot = lit_insert(keys, vals, hm, C);
             if (slot < 0) {
@@ -2634,14 +2651,18 @@ __global__ void __launch_bounds__(256) k_lh_fill(RunArgs a, LitHubPlan hp, int64
     const int64_t cb = beg + (int64_t)c * LH_CHUNK, ce = min(end, cb + LH_CHUNK);
     for (int64_t q = cb + threadIdx.x; q < ce; q += blockDim.x) {
         const int32_t y = a.adj[q];
+        if (!dbg_ok(a, y >= 0 && y < a.nnodes)) continue;
         const int32_t cy = __ldcg(&a.nmem[y]);
+        if (!dbg_ok(a, cy >= 0 && cy <= a.K)) continue;
         const int32_t *rowy = a.mem + (int64_t)y * a.K;
         const int32_t *krow = a.kmem + (int64_t)y * a.K;
         const int64_t dy = a.deg[y];
         if (a.profile) pb += 12ull + 8ull * (unsigned long long)cy;
         for (int s = 0; s < cy; ++s) {
             const int32_t C = __ldcg(&rowy[s]);
+            if (!dbg_ok(a, C >= 0 && C < a.nnodes)) continue;
             const int64_t ky = __ldcg(&krow[s]);
+            if (!dbg_ok(a, ky >= 0 && ky <= dy)) continue;
             const int64_t n = __ldcg(&a.comm[C].n);
             const int slot = lit_insert(keys, vals, hm, C);
             if (slot < 0) {   // cannot happen: the table holds 2 (d+1) K slots
@@ -2819,6 +2840,7 @@ __device__ void lit_apply_node(const RunArgs &a, int64_t bstart, int32_t blen, i
     const int lane = threadIdx.x & 31;
     const int32_t j = __ldcg(&a.act[i]), l = __ldcg(&a.act[a.qcap + i]);
     if (j < 0 && l < 0) return;
+    if (!dbg_ok(a, j < a.nnodes && l < a.nnodes && (j < 0 || j != l))) return;
     const int32_t x = a.order[bstart + i];
     int jj = 0, jl = 0, ll = 0;
     for (int64_t p = a.off[x] + lane; p < a.off[x + 1]; p += 32) {
@@ -2842,6 +2864,7 @@ __device__ void lit_apply_node(const RunArgs &a, int64_t bstart, int32_t blen, i
     int32_t *row = a.mem + (int64_t)x * a.K;
     int32_t *krow = a.kmem + (int64_t)x * a.K;
     const int32_t c = __ldcg(&a.nmem[x]);
+    if (!dbg_ok(a, c >= 0 && c <= a.K && (j < 0 || (kjoin >= 0 && kjoin <= d)))) return;
     int32_t c_new = c;
     if (lane == 0) {
         int32_t cc2 = c;
@@ -2928,11 +2951,17 @@ __global__ void __launch_bounds__(AP_THREADS) k_lit_kupd(RunArgs a, int64_t bsta
         const int32_t *row = a.mem + (int64_t)y * a.K;
         if (j >= 0) {
             const int s = row_find(row, cy, j);
-            if (s >= 0) atomicAdd(&a.kmem[(int64_t)y * a.K + s], 1);
+            if (s >= 0) {
+                const int32_t was = atomicAdd(&a.kmem[(int64_t)y * a.K + s], 1);
+                dbg_ok(a, was >= 0 && was < a.deg[y]);
+            }
         }
         if (l >= 0) {
             const int s = row_find(row, cy, l);
-            if (s >= 0) atomicAdd(&a.kmem[(int64_t)y * a.K + s], -1);
+            if (s >= 0) {
+                const int32_t was = atomicAdd(&a.kmem[(int64_t)y * a.K + s], -1);
+                dbg_ok(a, was >= 1);
+            }
         }
     }
 }
@@ -2945,11 +2974,14 @@ constexpr int LIT_FSUM_WARP = 512;
 
 __device__ __forceinline__ void lit_fsum_member(const RunArgs &a, int32_t C, int64_t n, int32_t y, double &f0,
                                                 double &f1, double &f2) {
+    if (!dbg_ok(a, y >= 0 && y < a.nnodes)) return;
     const int32_t cy = __ldcg(&a.nmem[y]);
+    if (!dbg_ok(a, cy >= 0 && cy <= a.K)) return;
     const int s = row_find(a.mem + (int64_t)y * a.K, cy, C);
     if (s < 0) return;   // left C earlier in this iteration
     const int64_t ky = __ldcg(&a.kmem[(int64_t)y * a.K + s]);
     const int64_t dy = a.deg[y];
+    if (!dbg_ok(a, ky >= 0 && ky <= dy)) return;
     f0 += lit_g(ky, dy, n - 1);
     f1 += lit_g(ky, dy, n);
     f2 += lit_g(ky, dy, n + 1);
@@ -3740,6 +3772,7 @@ RunArgs make_args(lf_graph *g, Readback *rbd) {
     a.nnodes = g->n;
     a.warp_max_deg = g->warp_max_degree > 0 ? g->warp_max_degree : 0x7fffffff;
     a.profile = g->profile;
+    a.debug = g->debug_checks;
     a.qtimes = g->qtimes;
     a.huge_deg = g->hub_qoff ? g->hub_degree : 0x7fffffff;
     a.hub_pos = g->hub_pos;
@@ -5082,7 +5115,8 @@ void run_impl(lf_graph *g, int32_t q_in, double thr, int32_t max_iters, int64_t 
         const Readback rb = *g->rb;
         if (rb.err & DERR_TIMEOUT) fail(LF_ERR_TIMEOUT, "a grid-barrier wait ran out (limit %d ms)", g->barrier_timeout_ms);
         if (rb.err & DERR_CAPACITY) fail(LF_ERR_CAPACITY, "membership row overflow (internal bound violated)");
-        if (rb.err & DERR_CHECK) fail(LF_ERR_CUDA, "device consistency check failed (histogram partitioning)");
+        if (rb.err & DERR_CHECK)
+            fail(LF_ERR_CUDA, "a device-side consistency check failed (bounds-checked mode or table partitioning)");
         iters = it;
         maxcnt = rb.maxcnt;
         last_live = rb.live_comms;

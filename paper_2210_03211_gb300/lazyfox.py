@@ -53,7 +53,8 @@ class Options(C.Structure):
                 ("use_graphs", C.c_int32), ("profile", C.c_int32), ("exhaustive_fp64", C.c_int32),
                 ("per_queue_launches", C.c_int32), ("barrier_timeout_ms", C.c_int32),
                 ("inject_barrier_stall", C.c_int32), ("barrier_mode", C.c_int32),
-                ("warps_per_node", C.c_int32), ("hub_degree", C.c_int32), ("gain_rule", C.c_int32)]
+                ("warps_per_node", C.c_int32), ("hub_degree", C.c_int32), ("gain_rule", C.c_int32),
+                ("debug_checks", C.c_int32)]
 
 
 class RunStatsC(C.Structure):
@@ -241,8 +242,8 @@ class Graph:
                  warp_max_degree: int = 0, use_graphs: bool = True, profile: bool = False,
                  exhaustive_fp64: bool = False, per_queue_launches: bool | None = None,
                  barrier_timeout_ms: int = 0, inject_barrier_stall: bool = False, barrier_mode: int = 0,
-                 warps_per_node: int = 0, hub_degree: int = 0, gain_rule: str | None = None, device=None,
-                 edge_offsets=None):
+                 warps_per_node: int = 0, hub_degree: int = 0, gain_rule: str | None = None,
+                 debug_checks: bool = False, device=None, edge_offsets=None):
         import torch
         self._L = load_library()
         self._h = C.c_void_p()
@@ -282,6 +283,7 @@ class Graph:
         if gain_rule not in GAIN_RULES:
             raise ValueError(f"unknown gain_rule {gain_rule!r}")
         opt.gain_rule = GAIN_RULES[gain_rule]
+        opt.debug_checks = 1 if debug_checks else 0
         if isinstance(src, torch.Tensor):
             if src.dtype != torch.int32 or dst.dtype != torch.int32 or not src.is_cuda:
                 raise TypeError("device edge lists must be int32 CUDA tensors")

@@ -51,7 +51,7 @@ def test_null_handle_is_rejected_without_touching_the_gpu(lib):
 
 def test_struct_layouts_match_header():
     from paper_2210_03211_gb300 import lazyfox
-    # lf_options: 4 pointers + 13 int32 (+4 padding) = 88 bytes on LP64
+    # lf_options: 4 pointers + 14 int32 = 88 bytes on LP64
     assert C.sizeof(lazyfox.Options) == 4 * 8 + 14 * 4
     assert C.sizeof(lazyfox.CreateStatsC) == 3 * 8 + 5 * 8 + 8 + 8
     assert C.sizeof(lazyfox.TuneResultC) == 4 * 4 + 2 * 8

@@ -112,12 +112,14 @@ def test_literal_per_queue_parity(lf, oracle_lib, idx, q):
 
 @pytest.mark.parametrize("shape", [dict(warps_per_node=1), dict(warps_per_node=2), dict(warps_per_node=4),
                                    dict(warps_per_node=8), dict(exhaustive_fp64=True),
-                                   dict(member_slots=2), dict(use_graphs=False)],
-                         ids=["team1", "team2", "team4", "team8", "exact_all", "row_growth", "direct_launches"])
+                                   dict(member_slots=2), dict(use_graphs=False), dict(debug_checks=True)],
+                         ids=["team1", "team2", "team4", "team8", "exact_all", "row_growth", "direct_launches",
+                              "bounds_checked"])
 def test_literal_launch_shapes(lf, oracle_lib, shape):
     """Every team size, the bracket switched off (every candidate's gain
-    summed exactly), membership rows grown from capacity 2, and launches
-    without graph capture give the oracle's run."""
+    summed exactly), membership rows grown from capacity 2, launches without
+    graph capture, and the bounds-checked mode (no check fires) give the
+    oracle's run."""
     el = W.dblp_like(seed=3, scale=0.03)
     og = oracle_lib.OracleGraph(el.src, el.dst)
     check_run(lf, og, el, 64, -math.inf, 4, **shape)
@@ -235,3 +237,18 @@ def test_literal_edge_cases(lf, oracle_lib):
             g.run(0, 0.01, 5)
         with pytest.raises(lf.LazyFoxError):
             g.communities()
+
+
+def test_literal_bounds_checked_runs_with_hubs_and_batches(lf, oracle_lib):
+    """The bounds-checked mode on the hub kernels and on a batch: no check
+    fires, and the results are the oracle's."""
+    el = W.hub_of_triangles(12000, extra=2, seed=3)
+    check_run(lf, oracle_lib.OracleGraph(el.src, el.dst), el, 256, -math.inf, 2, debug_checks=True)
+    graphs = W.batched_planted(4, seed=5, n_hi=3000)
+    with lf.Batch(graphs, gain_rule=RULE, debug_checks=True) as b:
+        b.run(64, 0.01, 50)
+        comms = b.graph_communities()
+    for i, g in enumerate(graphs):
+        og = oracle_lib.OracleGraph(g.src, g.dst)
+        og.run(64, 0.01, 50, rule=RULE)
+        assert [c.tolist() for c in comms[i]] == [c.tolist() for c in og.communities()], i
