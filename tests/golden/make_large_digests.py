@@ -6,14 +6,16 @@ stored values never come from the CUDA path.  Per run (gain rule, queue
 size, threshold -inf): cc and the node order (SHA-256 of the int32 array),
 and after each recorded iteration the WCC-hat total (as a hex float), joins,
 leaves and the SHA-256 of the membership CSR (int64 offsets over dense ids,
-then int32 community ids).  The paper's gain costs a pass over each
-candidate community in the oracle, so its runs are recorded after
-iterations 1 and 2; the mean-field runs also after iteration 20.
+then int32 community ids).  The paper's gain costs the oracle a pass over
+each candidate community (hours per iteration on this graph), so its runs
+are recorded after iteration 1; the mean-field runs after iterations 1, 2
+and 20.
 
-    python tests/golden/make_large_digests.py [--out tests/golden/large_digests.json]
+    python tests/golden/make_large_digests.py [--rule literal|meanfield] [--out FILE]
 
-Runs the four (rule, queue size) jobs in parallel, one process each; hours
-of CPU time.
+Runs the (rule, queue size) jobs in parallel, one process each, and rewrites
+the output (default tests/golden/large_digests_<rule>.json) as each job
+finishes; hours of CPU time.
 """
 import argparse
 import hashlib
@@ -27,8 +29,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-JOBS = [("literal", 65536, [1, 2]), ("literal", 1024, [1, 2]),
-        ("meanfield", 65536, [1, 2, 20]), ("meanfield", 1024, [1, 2, 20])]
+JOBS = {"literal": [("literal", 65536, [1]), ("literal", 1024, [1])],
+        "meanfield": [("meanfield", 65536, [1, 2, 20]), ("meanfield", 1024, [1, 2, 20])]}
 
 
 def sha(*arrays):
@@ -65,15 +67,21 @@ def job(spec):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "large_digests.json"))
+    ap.add_argument("--rule", choices=sorted(JOBS), required=True)
+    ap.add_argument("--out", default=None)
     args = ap.parse_args()
-    with mp.get_context("spawn").Pool(len(JOBS)) as pool:
-        res = pool.map(job, JOBS, chunksize=1)
-    doc = dict(workload="large_like() -- 3.07M nodes, power law (gamma 2.2), seed 4", threshold="-inf",
-               written_by="tests/golden/make_large_digests.py (oracle only)", runs=res)
-    with open(args.out, "w") as f:
-        json.dump(doc, f, indent=1)
-    print("wrote", args.out)
+    out = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), f"large_digests_{args.rule}.json")
+    jobs = JOBS[args.rule]
+    res = []
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        for r in pool.imap_unordered(job, jobs):
+            res.append(r)
+            res.sort(key=lambda x: -x["queue_size"])
+            doc = dict(workload="large_like() -- 3.07M nodes, power law (gamma 2.2), seed 4", threshold="-inf",
+                       written_by="tests/golden/make_large_digests.py (oracle only)", runs=res)
+            with open(out, "w") as f:
+                json.dump(doc, f, indent=1)
+            print("wrote", out, "with", len(res), "run(s)", flush=True)
 
 
 if __name__ == "__main__":
