@@ -2039,6 +2039,55 @@ __device__ __forceinline__ void lit_screen(const RunArgs &a, int32_t C, uint32_t
     }
 }
 
+// The (neighbour, membership) entries of neighbours [qb, qe) of one warp:
+// 32 neighbours at a time, their entries laid end to end over the lanes
+// (lane e of a round takes entry e, found by a shuffle search over the
+// prefix sums of the neighbours' membership counts), so a warp's work does
+// not depend on how the entries spread over its neighbours.  fn(C, ky, dy,
+// n): the community, deg(y,C), deg(y) and C's size before the queue.
+// Every lane of the warp must call this with the same range.
+template <typename Fn>
+__device__ __forceinline__ void lit_warp_entries(const RunArgs &a, int64_t qb, int64_t qe, unsigned long long &pb,
+                                                 bool count_bytes, Fn &&fn) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t q0 = qb; q0 < qe; q0 += 32) {
+        const int64_t q = q0 + lane;
+        int32_t y = 0, cy = 0, dy = 0;
+        if (q < qe) {
+            y = a.adj[q];
+            if (dbg_ok(a, y >= 0 && y < a.nnodes)) {
+                cy = __ldcg(&a.nmem[y]);
+                if (!dbg_ok(a, cy >= 0 && cy <= a.K)) cy = 0;
+                dy = a.deg[y];
+                if (count_bytes) pb += 12ull + 8ull * (unsigned long long)cy;
+            }
+        }
+        int inc = cy;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += t;
+        }
+        const int total = __shfl_sync(FULL, inc, 31);
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int e = e0 + lane;
+            int j = 0;   // first lane whose inclusive prefix exceeds e
+#pragma unroll
+            for (int b = 16; b > 0; b >>= 1)
+                if (__shfl_sync(FULL, inc, j + b - 1) <= e) j += b;
+            const int32_t yj = __shfl_sync(FULL, y, j);
+            const int32_t first = __shfl_sync(FULL, inc - cy, j);
+            const int32_t dj = __shfl_sync(FULL, dy, j);
+            if (e < total) {
+                const int64_t rb = (int64_t)yj * a.K + (e - first);
+                const int32_t C = __ldcg(&a.mem[rb]);
+                const int32_t ky = __ldcg(&a.kmem[rb]);
+                if (dbg_ok(a, C >= 0 && C < a.nnodes)) fn(C, (int64_t)ky, (int64_t)dj, (int64_t)__ldcg(&a.comm[C].n));
+            }
+        }
+    }
+}
+
 // Every entry of C's member index -- the members at the iteration's start
 // and its joiners since, in C's region and, past its capacity, in C's list --
 // handed to f, entry t to thread `tid` of `nthreads` when t % nthreads == tid.
@@ -2169,30 +2218,20 @@ __device__ bool lit_pass(const RunArgs &a, const LitNode &ln, int P, int p, int3
         if (P == 1 || (int)part_of(C, P) == p) ok &= ht_insert(keys, vals, hm, C, 0u, true);
     }
     team_sync<T>(tm);
-    for (int64_t q = ln.beg + tl; q < ln.end; q += NT) {
-        const int32_t y = a.adj[q];
-        if (!dbg_ok(a, y >= 0 && y < a.nnodes)) continue;
-        const int32_t cy = __ldcg(&a.nmem[y]);
-        if (!dbg_ok(a, cy >= 0 && cy <= a.K)) continue;
-        const int32_t *rowy = a.mem + (int64_t)y * a.K;
-        const int32_t *krow = a.kmem + (int64_t)y * a.K;
-        const int64_t dy = a.deg[y];
-        if (count_bytes) pb += 12ull + 8ull * (unsigned long long)cy;
-        for (int s = 0; s < cy; ++s) {
-            const int32_t C = __ldcg(&rowy[s]);
-            if (!dbg_ok(a, C >= 0 && C < a.nnodes)) continue;
-            if (P > 1 && (int)part_of(C, P) != p) continue;
-            const int64_t ky = __ldcg(&krow[s]);
-            if (!dbg_ok(a, ky >= 0 && ky <= dy)) continue;
-            const int64_t n = __ldcg(&a.comm[C].n);
+    {   // each warp of the team takes a contiguous share of the neighbours
+        const int64_t deg = ln.end - ln.beg, per = (deg + T - 1) / T;
+        const int64_t qb = ln.beg + min(deg, (int64_t)w_in * per), qe = ln.beg + min(deg, (int64_t)(w_in + 1) * per);
+        lit_warp_entries(a, qb, qe, pb, count_bytes, [&](int32_t C, int64_t ky, int64_t dy, int64_t n) {
+            if (P > 1 && (int)part_of(C, P) != p) return;
+            if (!dbg_ok(a, ky >= 0 && ky <= dy)) return;
             const int slot = lit_insert(keys, vals, hm, C);
             if (slot < 0) {
                 ok = false;
-                continue;
+                return;
             }
             const float h = (vals[slot] & OWN_FLAG) ? lit_h_leave32(ky, dy, n) : lit_h_join32(ky, dy, n);
             if (h != 0.f) atomicAdd(&hs[slot], h);
-        }
+        });
     }
     // a full table: the whole team starts over with more parts
     if constexpr (T > 1) {
@@ -2649,29 +2688,19 @@ __global__ void __launch_bounds__(256) k_lh_fill(RunArgs a, LitHubPlan hp, int64
             if (!ht_insert(keys, vals, hm, __ldcg(&rowx[j]), 0u, true)) atomicOr(&a.ds->err, DERR_CHECK);
     unsigned long long pb = 0;
     const int64_t cb = beg + (int64_t)c * LH_CHUNK, ce = min(end, cb + LH_CHUNK);
-    for (int64_t q = cb + threadIdx.x; q < ce; q += blockDim.x) {
-        const int32_t y = a.adj[q];
-        if (!dbg_ok(a, y >= 0 && y < a.nnodes)) continue;
-        const int32_t cy = __ldcg(&a.nmem[y]);
-        if (!dbg_ok(a, cy >= 0 && cy <= a.K)) continue;
-        const int32_t *rowy = a.mem + (int64_t)y * a.K;
-        const int32_t *krow = a.kmem + (int64_t)y * a.K;
-        const int64_t dy = a.deg[y];
-        if (a.profile) pb += 12ull + 8ull * (unsigned long long)cy;
-        for (int s = 0; s < cy; ++s) {
-            const int32_t C = __ldcg(&rowy[s]);
-            if (!dbg_ok(a, C >= 0 && C < a.nnodes)) continue;
-            const int64_t ky = __ldcg(&krow[s]);
-            if (!dbg_ok(a, ky >= 0 && ky <= dy)) continue;
-            const int64_t n = __ldcg(&a.comm[C].n);
+    {   // each warp takes a contiguous eighth of the chunk
+        const int64_t per = (ce - cb + 7) / 8, w = threadIdx.x >> 5;
+        const int64_t qb = min(ce, cb + w * per), qe = min(ce, cb + (w + 1) * per);
+        lit_warp_entries(a, qb, qe, pb, a.profile != 0, [&](int32_t C, int64_t ky, int64_t dy, int64_t n) {
+            if (!dbg_ok(a, ky >= 0 && ky <= dy)) return;
             const int slot = lit_insert(keys, vals, hm, C);
             if (slot < 0) {   // cannot happen: the table holds 2 (d+1) K slots
                 atomicOr(&a.ds->err, DERR_CHECK);
-                continue;
+                return;
             }
             const float hv = row_find(rowx, cx, C) >= 0 ? lit_h_leave32(ky, dy, n) : lit_h_join32(ky, dy, n);
             if (hv != 0.f) atomicAdd(&hs[slot], hv);
-        }
+        });
     }
     if (a.profile) {
 #pragma unroll
