@@ -59,6 +59,15 @@ WORKLOADS = {
                              dict(workload="dblp", q=1024, rule="literal"),
                              dict(workload="dblp", q=64, rule="literal"),
                              dict(workload="dblp", q=1024, rule="meanfield")]),
+    # the same generator at a quarter of the nodes (767,500 nodes, ~29M
+    # edges), queue size 16384, 20 iterations: the size detailed ncu captures
+    # of the move-evaluation kernels are taken on
+    "large_quarter": dict(name="large_like_767k_nodes_quarter_scale", gen=("large_like", {"scale": 0.25}), q=16384,
+                          threshold=-math.inf, max_iters=20,
+                          cpu_sample=dict(gen=("large_like", {"scale": 0.02}), max_iters=1,
+                                          what="the same generator at 2% scale (61,400 nodes, 2.07M edges): "
+                                               "preprocessing and the first iteration at queue size 16384"),
+                          secondary=[]),
     # 335k nodes, ~0.93M edges, Chung-Lu gamma 2.5, max degree ~550, planted
     # overlapping communities (sizes 6-2,000, 1-4 per node), seed 1
     "dblp": dict(name="dblp_like_335k_nodes_0.93M_edges", gen=("dblp_like", {}), q=1024, threshold=0.01,
