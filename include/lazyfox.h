@@ -126,12 +126,17 @@ typedef struct lf_run_stats {
                                 evaluation kernel in per-queue mode, the persistent queue
                                 kernel otherwise) */
     double prof_move_ms;     /* profile mode: their summed device time */
-    int64_t prof_move_bytes; /* profile mode: their algorithmic bytes.  Evaluation: per
-                                node 28 + 4|M(x)|, per neighbour y 8 + 4|M(y)|, 16 per
-                                distinct candidate community, 16 for the actions.  Apply
-                                (persistent kernel): 8 per node, and per moving node
-                                24 + 4|M(x)| + 12 per action, plus 16 per neighbour when
-                                the neighbour scan runs */
+    int64_t prof_move_bytes; /* profile mode: their algorithmic bytes.  LF_GAIN_LITERAL
+                                (evaluation kernels of a queue): per node 44 + 8|M(x)| (its
+                                offsets, count and actions, its row with deg(x,C)), per
+                                neighbour y 12 + 8|M(y)| (id, count, degree, row with
+                                deg(y,C)), 40 per distinct candidate community (its 16-byte
+                                record, its size read with the entries, 20 bytes of member
+                                sums).  LF_GAIN_MEANFIELD evaluation: per node 28 + 4|M(x)|,
+                                per neighbour y 8 + 4|M(y)|, 16 per distinct candidate
+                                community, 16 for the actions; apply (persistent kernel): 8
+                                per node, and per moving node 24 + 4|M(x)| + 12 per action,
+                                plus 16 per neighbour when the neighbour scan runs */
     double prof_queue_us[4]; /* profile mode, persistent kernel: p50, p90, p99 and max of the
                                 time per queue (evaluate + apply + barriers), last iteration */
     int64_t prof_candidates; /* profile mode, LF_GAIN_LITERAL: candidate (node, community) pairs

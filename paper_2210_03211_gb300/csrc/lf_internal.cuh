@@ -264,7 +264,7 @@ struct lf_graph {
     int32_t *lh_pos = nullptr, *lh_nsr = nullptr, *lh_fh = nullptr, *lh_fc = nullptr, *lh_sh = nullptr,
             *lh_sr = nullptr, *lh_svc = nullptr;
     int64_t *lh_toff = nullptr, *lh_soff = nullptr;
-    uint32_t *lh_tcap = nullptr, *lh_done = nullptr, *lh_ns = nullptr, *lh_svv = nullptr;
+    uint32_t *lh_tcap = nullptr, *lh_ns = nullptr, *lh_svv = nullptr;
     int32_t *lh_lb = nullptr;
     float *lh_svl = nullptr;
     void *lh_tab = nullptr;               // tables: 16 bytes per slot

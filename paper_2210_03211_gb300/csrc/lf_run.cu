@@ -1956,29 +1956,14 @@ __device__ __forceinline__ double lit_g(int64_t k, int64_t d, int64_t nu) {
     return (bk * (double)d) / (bd * (double)den);
 }
 
-// h+ = g(n+1; k+1) - g(n+1; k) = d (k D + C(k,2)) / (C(d,2) D (D-1)), D = n + d - k
-// (a neighbour y of a joining x; y is not x, so k <= d - 1 and D - 1 >= n >= 1)
-__device__ __forceinline__ double lit_h_join(int64_t k, int64_t d, int64_t n) {
-    if (d < 2 || k < 1) return 0.0;
-    const double D = (double)(n + d - k);
-    const double bk = 0.5 * ((double)k * (double)(k - 1));
-    const double bd = 0.5 * ((double)d * (double)(d - 1));
-    return ((double)d * ((double)k * D + bk)) / (bd * (D * (D - 1.0)));
-}
-
-// h- = g(n-1; k-1) - g(n-1; k) = -d (C(k-1,2) + (k-1)(D+1)) / (C(d,2) D (D+1)),
-// D = n - 2 + d - k (used only when n - 1 >= 2, so D >= 1)
-__device__ __forceinline__ double lit_h_leave(int64_t k, int64_t d, int64_t n) {
-    if (d < 2 || k < 2 || n < 3) return 0.0;
-    const double D = (double)(n - 2 + d - k);
-    const double bk1 = 0.5 * ((double)(k - 1) * (double)(k - 2));
-    const double bd = 0.5 * ((double)d * (double)(d - 1));
-    return -((double)d * (bk1 + (double)(k - 1) * (D + 1.0))) / (bd * (D * (D + 1.0)));
-}
-
-// The same corrections and x's own g in FP32 (about ten roundings each,
-// relative error < 16 x 2^-24; a sum of k of them adds k roundings): used
-// only in the bracket, whose bound E carries a term for them.
+// The neighbours' corrections:
+//   h+ = g(n+1; k+1) - g(n+1; k) = d (k D + C(k,2)) / (C(d,2) D (D-1)), D = n + d - k
+//        (a neighbour y of a joining x; y is not x, so k <= d - 1 and D - 1 >= n >= 1),
+//   h- = g(n-1; k-1) - g(n-1; k) = -d (C(k-1,2) + (k-1)(D+1)) / (C(d,2) D (D+1)),
+//        D = n - 2 + d - k (used only when n - 1 >= 2, so D >= 1),
+// and x's own g, in FP32 (about ten roundings each, relative error
+// < 16 x 2^-24; a sum of k of them adds k roundings): used only in the
+// bracket, whose bound E carries a term for them.
 __device__ __forceinline__ float lit_h_join32(int64_t k, int64_t d, int64_t n) {
     if (d < 2 || k < 1) return 0.f;
     const float D = (float)(n + d - k), kf = (float)k, df = (float)d;
@@ -2105,12 +2090,36 @@ __device__ __forceinline__ void lit_members(const RunArgs &a, int32_t C, int tid
     }
 }
 
+// Whether y is a neighbour of x (adjacency [xb, xe), ascending): without a
+// fence a binary search in global memory; with one (fence[j] = adj[xb + j
+// step], nf entries, in shared memory) the search first finds the segment
+// between two fence entries, then searches only that segment.
+__device__ __forceinline__ bool adj_has_fenced(const int32_t *adj, int64_t xb, int64_t xe, const int32_t *fence,
+                                               int nf, int64_t step, int32_t y) {
+    if (!fence) return adj_has(adj, xb, xe, y);
+    int lo = 0, hi = nf;   // the last j with fence[j] <= y
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (fence[mid] <= y) lo = mid;
+        else hi = mid;
+    }
+    if (fence[lo] > y) return false;
+    const int64_t b = xb + (int64_t)lo * step;
+    return adj_has(adj, b, min(xe, b + step), y);
+}
+
 // The exact gain of x joining (own = false) or leaving C: every member's term
 // after and before, x's own term, added into a signed superaccumulator (acc:
-// the warp's, zero on entry and on exit).  One warp.
+// the warp's, zero on entry and on exit).  One warp (tid, nthreads = lane,
+// 32), or a whole block (threadIdx.x, blockDim.x; each warp adds into its own
+// accumulator, acc + warp x SACC_CHUNKS, and the words are summed before the
+// one rounding).
 __device__ double lit_exact_gain(const RunArgs &a, int32_t x, int32_t d, int32_t C, bool own, int64_t k,
-                                 unsigned long long *acc) {
+                                 unsigned long long *acc, const int32_t *fence = nullptr, int nf = 0,
+                                 int64_t step = 0, bool block = false, double *s_g = nullptr) {
     const int lane = threadIdx.x & 31;
+    const int tid = block ? (int)threadIdx.x : lane, nthreads = block ? (int)blockDim.x : 32;
+    unsigned long long *wacc = block ? acc + (threadIdx.x >> 5) * SACC_CHUNKS : acc;
     const int4 r = __ldcg(reinterpret_cast<const int4 *>(&a.comm[C]));
     const int64_t n0 = r.x;
     const uint32_t m20 = (uint32_t)r.y;
@@ -2128,17 +2137,35 @@ __device__ double lit_exact_gain(const RunArgs &a, int32_t x, int32_t d, int32_t
         const int64_t ky = __ldcg(&a.kmem[(int64_t)y * a.K + s]);
         const int64_t dy = a.deg[y];
         if (!dbg_ok(a, ky >= 0 && ky <= dy)) return;
-        const int64_t k1 = adj_has(a.adj, xb, xe, y) ? (own ? ky - 1 : ky + 1) : ky;
-        ssacc_add(acc, wcchat_member(k1, dy, n1, m21, cc));
-        ssacc_add(acc, -wcchat_member(ky, dy, n0, m20, cc));
+        const int64_t k1 = adj_has_fenced(a.adj, xb, xe, fence, nf, step, y) ? (own ? ky - 1 : ky + 1) : ky;
+        ssacc_add(wacc, wcchat_member(k1, dy, n1, m21, cc));
+        ssacc_add(wacc, -wcchat_member(ky, dy, n0, m20, cc));
     };
-    lit_members(a, C, lane, 32, member);
-    if (lane == 0) ssacc_add(acc, own ? -wcchat_member(k, d, n0, m20, cc) : wcchat_member(k, d, n1, m21, cc));
-    __syncwarp();
-    double g = 0.0;
-    if (lane == 0) g = ssacc_round_and_clear(acc);
-    __syncwarp();
-    return __shfl_sync(FULL, g, 0);
+    lit_members(a, C, tid, nthreads, member);
+    if (tid == 0) ssacc_add(wacc, own ? -wcchat_member(k, d, n0, m20, cc) : wcchat_member(k, d, n1, m21, cc));
+    if (!block) {
+        __syncwarp();
+        double g = 0.0;
+        if (lane == 0) g = ssacc_round_and_clear(acc);
+        __syncwarp();
+        return __shfl_sync(FULL, g, 0);
+    }
+    __syncthreads();
+    const int nw = (int)(blockDim.x >> 5);
+    for (int c = threadIdx.x; c < SACC_CHUNKS; c += blockDim.x) {
+        unsigned long long t = acc[c];
+        for (int w2 = 1; w2 < nw; ++w2) {
+            t += acc[w2 * SACC_CHUNKS + c];   // words wrap: the sum of the warps' signed sums
+            acc[w2 * SACC_CHUNKS + c] = 0ull;
+        }
+        acc[c] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *s_g = ssacc_round_and_clear(acc);
+    __syncthreads();
+    const double g = *s_g;
+    __syncthreads();
+    return g;
 }
 
 // Per-warp values a literal team exchanges.
@@ -2157,23 +2184,6 @@ struct LitNode {
     int32_t x, d, cx;
     int64_t beg, end;
 };
-
-__device__ __forceinline__ double warp_max_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
-    return v;
-}
-
-__device__ __forceinline__ int lit_find(const int32_t *keys, uint32_t hm, int32_t key) {
-    uint32_t h = hash32((uint32_t)key) & hm;
-    for (uint32_t probe = 0; probe <= hm; ++probe) {
-        const int32_t k = keys[h];
-        if (k == key) return (int)h;
-        if (k == EMPTY_KEY) return -1;
-        h = (h + 1) & hm;
-    }
-    return -1;
-}
 
 // Open-addressing insert of one neighbour entry: the slot of key (claimed if
 // new) with its count raised by one, or -1 if the table is full.
@@ -2621,8 +2631,10 @@ __global__ void __launch_bounds__(EV_THREADS, 3) k_lit_big(RunArgs a, int64_t bs
 // 1024 neighbours: counts, own flags, FP32 corrections), k_lh_bound (one
 // block per 4096 slots: brackets, the hub's best lower ends by an
 // order-preserving integer max), k_lh_mark (one block per 4096 slots:
-// survivors listed, slots cleared; the hub's last block decides, summing the
-// undecided survivors exactly).  Team and block kernels skip these nodes.
+// survivors listed, slots cleared) and k_lh_decide (one block per hub: a lone
+// survivor with a positive lower end, or the survivors' exact sums; those of
+// large communities by the whole block, with the hub's adjacency searched
+// through a fence in shared memory).  Team and block kernels skip these nodes.
 // ---------------------------------------------------------------------------
 constexpr int LIT_HUB_DEG = 1024;
 constexpr int LH_CHUNK = 1024;       // neighbours per fill block
@@ -2638,7 +2650,6 @@ struct LitHubPlan {
     const int32_t *nsr;       // per hub: its slot items (worst case)
     uint32_t *heff;           // per hub: table slots used in this queue
     int32_t *lb;              // per hub: best lower ends (join, leave), order-preserving
-    uint32_t *done;           // per hub: slot items marked
     uint32_t *ns;             // per hub: survivors listed
     int32_t *sv_c;            // survivor lists: community, count word, lower end
     uint32_t *sv_v;
@@ -2756,16 +2767,14 @@ __global__ void __launch_bounds__(256) k_lh_bound(RunArgs a, LitHubPlan hp, int6
     }
 }
 
-__global__ void __launch_bounds__(256) k_lh_mark(RunArgs a, LitHubPlan hp, int64_t bstart, int64_t first) {
-    __shared__ int s_last;
-    __shared__ unsigned long long acc_s[8 * SACC_CHUNKS];
-    __shared__ double bg[2][8];
-    __shared__ int32_t bc[2][8], bk[2][8];
+constexpr int LH_FENCE = 2048;        // fence entries of a hub's adjacency (exact sums)
+constexpr int64_t LH_BLOCK_MEMBERS = 256;   // survivors of larger communities are summed by the whole block
+
+// Survivors of a hub's bracket test listed (one block per 4096 slots), the
+// table left clean for the hub's next queue.
+__global__ void __launch_bounds__(256, 4) k_lh_mark(RunArgs a, LitHubPlan hp, int64_t bstart, int64_t first) {
     const int64_t it = first + blockIdx.x;
     const int h = hp.sh[it], r = hp.sr[it];
-    const int32_t i = hp.pos[h];
-    const int32_t x = a.order[bstart + i];
-    const int32_t d = (int32_t)(a.off[x + 1] - a.off[x]);
     const int64_t t0 = hp.toff[h], so = hp.soff[h];
     const float lbj = ord2f(__ldcg(&hp.lb[2 * h])), lbl = ord2f(__ldcg(&hp.lb[2 * h + 1]));
     const uint32_t heff = __ldcg(&hp.heff[h]);
@@ -2788,13 +2797,23 @@ __global__ void __launch_bounds__(256) k_lh_mark(RunArgs a, LitHubPlan hp, int64
         hp.vals[t0 + s] = 0u;
         hp.hs[t0 + s] = 0.f;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&hp.done[h], 1u) + 1u == heff / LH_SLOTS;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // the hub's last block: the survivors decide
+}
+
+// A hub's decision from its listed survivors (one block per hub of the
+// queue): a lone survivor with a positive lower end wins; otherwise the
+// survivors' gains are summed exactly and compared.
+__global__ void __launch_bounds__(256) k_lh_decide(RunArgs a, LitHubPlan hp, int64_t bstart, int64_t h0, int64_t nh) {
+    __shared__ unsigned long long acc_s[8 * SACC_CHUNKS];
+    __shared__ int32_t fence[LH_FENCE];
+    __shared__ double s_g;
+    __shared__ double bg[2][8];
+    __shared__ int32_t bc[2][8], bk[2][8];
+    if (blockIdx.x >= nh) return;
+    const int64_t h = h0 + blockIdx.x;
+    const int32_t i = hp.pos[h];
+    const int32_t x = a.order[bstart + i];
+    const int32_t d = (int32_t)(a.off[x + 1] - a.off[x]);
+    const int64_t so = hp.soff[h];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t ns = __ldcg(&hp.ns[h]);
     int cj = 0, cl = 0;
@@ -2823,14 +2842,36 @@ __global__ void __launch_bounds__(256) k_lh_mark(RunArgs a, LitHubPlan hp, int64
     if (do_j || do_l) {
         unsigned long long *acc = acc_s + w * SACC_CHUNKS;
         for (int c2 = lane; c2 < SACC_CHUNKS; c2 += 32) acc[c2] = 0ull;
-        __syncwarp();
+        // every step-th entry of x's adjacency, for the neighbour tests of the member passes
+        const int64_t xb = a.off[x];
+        const int64_t step = ((int64_t)d + LH_FENCE - 1) / LH_FENCE;
+        const int nf = (int)(((int64_t)d + step - 1) / step);
+        for (int j = threadIdx.x; j < nf; j += blockDim.x) fence[j] = a.adj[xb + (int64_t)j * step];
+        __syncthreads();
+        // survivors of large communities: one at a time, the whole block over the members
+        for (uint32_t e = 0; e < ns; ++e) {
+            const uint32_t v = __ldcg(&hp.sv_v[so + e]);
+            const bool own = (v & OWN_FLAG) != 0;
+            if (own ? !do_l : !do_j) continue;
+            const int32_t C = __ldcg(&hp.sv_c[so + e]);
+            if ((int64_t)__ldcg(&a.comm[C].n) <= LH_BLOCK_MEMBERS) continue;
+            const int64_t k = (int64_t)(v & CNT_MASK);
+            const double g = lit_exact_gain(a, x, d, C, own, k, acc_s, fence, nf, step, true, &s_g);
+            if (a.profile && threadIdx.x == 0) atomicAdd(&a.ds->prof_exact, 1ull);
+            if (g > 0.0) {
+                Best &b = own ? bl : bj;
+                if (better(g, C, b.g, b.c)) b = Best{g, C, (int32_t)k};
+            }
+        }
+        // the others: a warp each
         for (uint32_t e = w; e < ns; e += blockDim.x >> 5) {
             const uint32_t v = __ldcg(&hp.sv_v[so + e]);
             const bool own = (v & OWN_FLAG) != 0;
             if (own ? !do_l : !do_j) continue;
             const int32_t C = __ldcg(&hp.sv_c[so + e]);
+            if ((int64_t)__ldcg(&a.comm[C].n) > LH_BLOCK_MEMBERS) continue;
             const int64_t k = (int64_t)(v & CNT_MASK);
-            const double g = lit_exact_gain(a, x, d, C, own, k, acc);
+            const double g = lit_exact_gain(a, x, d, C, own, k, acc, fence, nf, step);
             if (a.profile && lane == 0) atomicAdd(&a.ds->prof_exact, 1ull);
             if (g > 0.0) {
                 Best &b = own ? bl : bj;
@@ -2851,8 +2892,7 @@ __global__ void __launch_bounds__(256) k_lh_mark(RunArgs a, LitHubPlan hp, int64
     if (threadIdx.x == 0) {
         write_action(a, i, bj, bl, 0ull);
         if (a.profile) atomicAdd(&a.ds->prof_bytes, 44ull + 8ull * (unsigned long long)__ldcg(&a.nmem[x]));
-        hp.done[h] = 0u;   // ready for the hub's next queue
-        hp.ns[h] = 0u;
+        hp.ns[h] = 0u;   // ready for the hub's next queue
         hp.lb[2 * h] = f2ord(-INFINITY);
         hp.lb[2 * h + 1] = f2ord(-INFINITY);
     }
@@ -3511,7 +3551,8 @@ __device__ __forceinline__ bool row_has(const int32_t *row, int32_t c, int32_t C
 }
 
 // WCC-hat(P) = sum over memberships (x, C) of WCC-hat(x, C), with
-// deg(x, C) counted over x's neighbours; exact sum, so the total does not
+// deg(x, C) read from the membership's count under the paper's gain (kept
+// exact through every apply), else counted over x's neighbours; exact sum, so the total does not
 // depend on the order of the additions.  Warps take runs of node ids from a
 // counter; a node of degree > TOT_CHUNK is counted in chunks of TOT_CHUNK
 // neighbours taken from a second counter, each chunk adding its counts to the
@@ -3694,6 +3735,37 @@ __global__ void __launch_bounds__(TOT_WARPS * 32) k_total(RunArgs a, int64_t n) 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t *row_s = s_row[w], *cnt_s = s_cnt[w];
     TotBuf buf{s_buf[w][0], s_buf[w][1], s_buf[w][2], 0};
+    if (a.kmem) {   // the paper's gain keeps deg(x, C) of every membership: no recount
+        for (;;) {
+            long long b0 = 0;
+            if (lane == 0) b0 = (long long)atomicAdd(&a.tot_next[0], 1u) * 32;
+            b0 = __shfl_sync(FULL, b0, 0);
+            if (b0 >= n) break;
+            const int64_t x = b0 + lane;   // a node per lane
+            int32_t c = 0, d = 0;
+            if (x < n) {
+                c = __ldcg(&a.nmem[x]);
+                if (!dbg_ok(a, c >= 0 && c <= a.K)) c = 0;
+                d = a.deg[x];
+            }
+            const int cmax = __reduce_max_sync(FULL, c);
+            for (int s = 0; s < cmax; ++s) {
+                int32_t C = 0, k = 0;
+                bool has = s < c;
+                if (has) {
+                    C = __ldcg(&a.mem[x * a.K + s]);
+                    k = __ldcg(&a.kmem[x * a.K + s]);
+                    has = dbg_ok(a, C >= 0 && C < a.nnodes && k >= 0 && k <= d);
+                }
+                tot_push(a, acc, buf, has, C, k, d);
+            }
+        }
+        if (buf.n > 0) tot_flush(a, acc, buf);
+        __syncthreads();
+        for (int s = threadIdx.x; s < SACC_CHUNKS; s += blockDim.x)
+            if (acc[s]) atomicAdd(&a.ds->sacc[s], acc[s]);
+        return;
+    }
     // nodes of degree <= TOT_CHUNK, whole
     for (;;) {
         long long b0 = 0;
@@ -4105,7 +4177,7 @@ void free_lit_hub_plan(lf_graph *g) {
             dfree(g, *pp);
             *pp = nullptr;
         }
-    for (uint32_t **pp : {&g->lh_tcap, &g->lh_done, &g->lh_ns, &g->lh_svv, &g->lh_heff})
+    for (uint32_t **pp : {&g->lh_tcap, &g->lh_ns, &g->lh_svv, &g->lh_heff})
         if (*pp) {
             dfree(g, *pp);
             *pp = nullptr;
@@ -4200,10 +4272,8 @@ void build_lit_hub_plan(lf_graph *g, int64_t q, int64_t nb) {
     up(g->lh_toff, toff);
     up(g->lh_soff, soff);
     up(g->lh_tcap, tcap);
-    g->lh_done = dalloc_n<uint32_t>(g, H);
     g->lh_heff = dalloc_n<uint32_t>(g, H);
     g->lh_ns = dalloc_n<uint32_t>(g, H);
-    LF_CUDA(cudaMemsetAsync(g->lh_done, 0, (size_t)H * 4, g->stream));
     LF_CUDA(cudaMemsetAsync(g->lh_ns, 0, (size_t)H * 4, g->stream));
     {
         // best lower ends start at -inf (order-preserving: -inf's bits ^ 0x7fffffff)
@@ -4236,7 +4306,6 @@ LitHubPlan lit_hub_plan(lf_graph *g) {
     hp.nsr = g->lh_nsr;
     hp.heff = g->lh_heff;
     hp.lb = g->lh_lb;
-    hp.done = g->lh_done;
     hp.ns = g->lh_ns;
     hp.sv_c = g->lh_svc;
     hp.sv_v = g->lh_svv;
@@ -4291,7 +4360,8 @@ void launch_batches_lit(lf_graph *g, const RunArgs &a, int64_t q, int64_t first,
             k_lh_fill<<<(unsigned)nf, 256, 0, g->stream>>>(ab, hp, bstart, f0);
             k_lh_bound<<<(unsigned)nsl, 256, 0, g->stream>>>(ab, hp, bstart, s0);
             k_lh_mark<<<(unsigned)nsl, 256, 0, g->stream>>>(ab, hp, bstart, s0);
-            g->launches += 4;
+            k_lh_decide<<<(unsigned)nh, 256, 0, g->stream>>>(ab, hp, bstart, h0, nh);
+            g->launches += 5;
         }
         if (prof) record_event(g, g->prof_ev[2 * b + 1], capturing);
         const unsigned ag = grid_for((int64_t)blen * 32, AP_THREADS, 1 << 30);
