@@ -87,9 +87,9 @@ typedef struct lf_options {
                                 memory, in blocks of their own (per-queue launches: on a second
                                 stream); 0 (default) = 384 */
     int32_t gain_rule;       /* decision rule of a move (LF_GAIN_*); 0 (default): LF_GAIN_LITERAL */
-    int32_t debug_checks;    /* 1: bounds-checked mode -- the move evaluation, apply and community
-                                sums of LF_GAIN_LITERAL check every node id, community id, row count
-                                and deg(x,C) they read from device state before using it; a value
+    int32_t debug_checks;    /* 1: bounds-checked mode -- the move evaluation, apply, community
+                                sums and total of LF_GAIN_LITERAL check every node id, community id,
+                                row count and deg(x,C) they read from device state before using it; a value
                                 out of range is skipped and the run fails with LF_ERR_CUDA and a
                                 message (no kernel traps).  Slower; for tests and debugging */
 } lf_options;
