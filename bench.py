@@ -134,9 +134,10 @@ def measured_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def ncu_traffic(kernel: str):
+def ncu_traffic(kernel: str, workload: str, queue_size: int):
     """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    source has not changed since it was captured."""
+    source has not changed since it was captured and the summary is for this
+    workload and queue size (a launch's traffic depends on both)."""
     import hashlib
     summ = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     if not os.path.exists(summ):
@@ -152,6 +153,8 @@ def ncu_traffic(kernel: str):
     except OSError:
         return None
     if vals.get("source_sha256_16") != sha:
+        return None
+    if vals.get("bench_workload") != workload or vals.get("bench_queue_size") != str(queue_size):
         return None
     try:
         return dict(bytes_per_launch=float(vals["dram_bytes_per_launch_scaled"]),
@@ -708,11 +711,11 @@ def main():
     if rule == "literal":
         kname = ("k_lit_eval + k_lit_big (move evaluation under the paper's gain; one launch = one queue's "
                  "evaluation kernels)")
-        traffic = ncu_traffic("k_lit_eval")
+        traffic = ncu_traffic("k_lit_eval", args.workload, q)
     else:
         kname = ("k_eval (move evaluation, one launch per queue)" if not persistent else
                  "k_iterate (persistent kernel: evaluate + apply of every queue, one launch per iteration)")
-        traffic = ncu_traffic("k_eval")
+        traffic = ncu_traffic("k_eval", args.workload, q)
     roofline = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": achieved / peak, "bytes_per_launch": ev_bytes / max(1, ev_launches),

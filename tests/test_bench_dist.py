@@ -77,8 +77,8 @@ def test_oracle_sample_runs_one_process_per_core():
 
 
 def test_traffic_is_reported_only_for_the_captured_source(tmp_path, monkeypatch):
-    """The committed ncu traffic counts for a kernel whose source changed
-    since the capture are not reported (None)."""
+    """The committed ncu traffic counts are reported only for the source,
+    workload and queue size they were captured for (else None)."""
     import hashlib
     import bench
     src_dir = tmp_path / "paper_2210_03211_gb300" / "csrc"
@@ -89,12 +89,15 @@ def test_traffic_is_reported_only_for_the_captured_source(tmp_path, monkeypatch)
     sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
     (tmp_path / "profiles" / "k_eval_traffic.txt").write_text(
         "# comment: with a colon\nsource: lf_run.cu\n"
-        f"source_sha256_16: {sha}\ndram_bytes_per_launch_scaled: 2977331\ncaptured_on: test\n")
+        f"source_sha256_16: {sha}\ndram_bytes_per_launch_scaled: 2977331\ncaptured_on: test\n"
+        "bench_workload: large\nbench_queue_size: 65536\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.ncu_traffic("k_eval") == {"bytes_per_launch": 2977331.0, "workload": "test"}
+    assert bench.ncu_traffic("k_eval", "large", 65536) == {"bytes_per_launch": 2977331.0, "workload": "test"}
+    assert bench.ncu_traffic("k_eval", "large", 1024) is None
+    assert bench.ncu_traffic("k_eval", "dblp", 65536) is None
     src.write_text("// kernel source, changed\n")
-    assert bench.ncu_traffic("k_eval") is None
-    assert bench.ncu_traffic("k_other") is None
+    assert bench.ncu_traffic("k_eval", "large", 65536) is None
+    assert bench.ncu_traffic("k_other", "large", 65536) is None
 
 
 def test_measured_peak_and_its_fallback(tmp_path, monkeypatch):
