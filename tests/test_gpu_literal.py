@@ -252,3 +252,23 @@ def test_literal_bounds_checked_runs_with_hubs_and_batches(lf, oracle_lib):
         og = oracle_lib.OracleGraph(g.src, g.dst)
         og.run(64, 0.01, 50, rule=RULE)
         assert [c.tolist() for c in comms[i]] == [c.tolist() for c in og.communities()], i
+
+
+def ring_lattice(n, k):
+    """Every node joined to its k nearest neighbours on each side: all nodes
+    have the same degree and the same clustering coefficient."""
+    return [(i, (i + j) % n) for i in range(n) for j in range(1, k + 1)]
+
+
+@pytest.mark.parametrize("q", [1, 7, 64, 1 << 30])
+def test_literal_ties_everywhere(lf, oracle_lib, q):
+    """Adversarial ties: a ring lattice (one CC and one degree for every node,
+    so the order falls back to ids and many gains tie exactly), a complete
+    bipartite graph (no triangle: cc = 0, every estimator term and total 0)
+    and disjoint copies of the same clique (equal gains in every copy)."""
+    graphs = [W.from_pairs(ring_lattice(60, 3), "ring_lattice_60_3"),
+              W.from_pairs([(a, 10 + b) for a in range(6) for b in range(7)], "k_6_7"),
+              W.from_pairs(W.clique(5) + W.clique(5, 10) + W.clique(5, 20) + [(4, 10), (14, 20)], "three_k5")]
+    for el in graphs:
+        og = oracle_lib.OracleGraph(el.src, el.dst)
+        check_run(lf, og, el, q)
