@@ -272,3 +272,20 @@ def test_literal_ties_everywhere(lf, oracle_lib, q):
     for el in graphs:
         og = oracle_lib.OracleGraph(el.src, el.dst)
         check_run(lf, og, el, q)
+
+
+def test_literal_runs_are_deterministic(lf):
+    """The FP32 corrections are summed with atomics in any order, so a
+    bracket may differ in its last bits between runs; the decisions may not.
+    Two runs of a power-law graph with hubs give the same totals (bit for
+    bit) and the same memberships, and so does a third run with the
+    bounds-checked mode on."""
+    el = W.dblp_like(seed=5, scale=0.05)
+    outs = []
+    for kw in [{}, {}, dict(debug_checks=True)]:
+        with lf.Graph(el.src, el.dst, **kw) as g:
+            st = g.run(1024, -math.inf, 6)
+            s = g.state()
+            outs.append(([float(v).hex() for v in st.wcc_history], st.joins.tolist(), st.leaves.tolist(),
+                         s["mem_off"].tolist(), s["mem_ids"].tolist()))
+    assert outs[0] == outs[1] == outs[2]
